@@ -1,0 +1,356 @@
+#!/usr/bin/env python3
+"""Benchmark of the FIDS hot path on the headline workload:
+n = 2^17 - 1 interior points, M = 4096 graded levels, gamma = 0.4 (r = 4),
+alpha = 1.6, kappa = exp(GRF) mapped onto [0.2, 5], mixed precision
+(FP32 inner PBiCGSTAB inside FP64 refinement) vs the plain FP64 path.
+
+One step = one time level of the scheme: SOE history update and
+right-hand side, Strang preconditioner for the level, Krylov solve.
+Steps are timed one by one with CUDA events on the solver's stream; L2 is
+flushed (256 MB write, outside the events) before every timed level.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
+replica on its own GPU (a single problem does not shard: its levels are
+sequential); value = levels of all ranks / max elapsed.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "steps/s & % HBM roofline at N=2^17-1, M=4096: mixed vs FP64, rel err <=1e-10"
+WORKLOAD = "fids-mixed n=131071 M=4096 gamma=0.4 r=4 alpha=1.6 kappa=GRF[0.2,5]"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None, help="timed levels (default: rest of the march)")
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=131071)
+    ap.add_argument("--M", type=int, default=4096)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison arm")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-n", type=int, default=255)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- our arm
+def run_arm(torch, pkg, prob, precision, W, K, flush, stream, e2e=False):
+    """March W untimed levels, then K timed levels (restarting the march
+    after level M).  Each timed level is bracketed by CUDA events on the
+    solver's stream, with an L2 flush before it.  Returns the solver, the
+    per-level milliseconds, the per-kernel event totals and the iteration
+    totals of the timed levels."""
+    s = pkg.Solver(prob.alpha, prob.gamma, prob.l, prob.T, prob.n, prob.M, prob.r, prob.soe_tol,
+                   precision=precision, krylov_tol=1e-12, profile=True, stream=stream)
+    s.set_problem_from(prob)
+    n = prob.n
+    dev = torch.device("cuda")
+    tot = {"its": 0, "outer": 0, "E_active_sum": 0, "status": 0}
+    if e2e:
+        kap_h = torch.from_numpy(prob.kappa0.copy()).pin_memory()
+        f_h = torch.from_numpy(prob.f_at(0.0)).pin_memory()
+        u_h = torch.empty(n, dtype=torch.float64).pin_memory()
+        kap_d = torch.empty(n, dtype=torch.float64, device=dev)
+        f_d = torch.empty(n, dtype=torch.float64, device=dev)
+        u_d = torch.empty(n, dtype=torch.float64, device=dev)
+    first_timed = [None]
+
+    def collect():
+        if first_timed[0] is not None and s.m >= first_timed[0]:
+            for rec in s.level_stats(first_timed[0], s.m):
+                tot["its"] += rec["iterations"]
+                tot["outer"] += rec["outer"]
+                tot["E_active_sum"] += rec["E_active"]
+                tot["status"] = tot["status"] or rec["status"]
+
+    def one_level(timed):
+        if s.m == prob.M:
+            collect()
+            s.reset()
+            if timed:
+                first_timed[0] = 1
+        if timed and first_timed[0] is None:
+            first_timed[0] = s.m + 1
+        if e2e:
+            kap_d.copy_(kap_h, non_blocking=True)
+            f_d.copy_(f_h, non_blocking=True)
+            s.step(kappa_m=kap_d, f_m=f_d, u_out=u_d, sync=False)
+            u_h.copy_(u_d, non_blocking=True)
+        else:
+            s.step(sync=False)
+
+    with torch.cuda.stream(stream):
+        for _ in range(W):
+            one_level(False)
+        torch.cuda.synchronize()
+        s.timing()  # discard the warm-up kernel times
+        evs = []
+        for _ in range(K):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one_level(True)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    tim = s.timing()
+    collect()
+    return s, ms, tim, tot
+
+
+def current_u(torch, s):
+    u = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    s.current_solution(u)
+    torch.cuda.synchronize()
+    return u
+
+
+def ours(args):
+    import torch
+    import paper_2002_11978_gb300 as pkg
+    import tsfde_inputs as ti
+    from paper_2002_11978_gb300 import build
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    prob = ti.config_mixed(n=args.n, M=args.M)
+    W = args.warmup
+    K = args.steps if args.steps is not None else max(1, prob.M - W)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device="cuda")
+    n = prob.n
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- mixed arm: the reported value
+    clocks = ClockSampler(torch.cuda.current_device())
+    barrier()
+    clocks.start()
+    s_mx, ms_mx, tim_mx, st_mx = run_arm(torch, pkg, prob, "mixed", W, K, flush, stream)
+    barrier()
+    clk = clocks.stop()
+    t_mx = sum(ms_mx) / 1e3
+    if world > 1:
+        t = torch.tensor([t_mx], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_mx = float(t.item())
+    u_mx = current_u(torch, s_mx)
+
+    # ---- plain FP64 arm on the same levels: the comparison
+    fp64 = None
+    if not args.no_fp64:
+        s64, ms64, tim64, st64 = run_arm(torch, pkg, prob, "fp64", W, K, flush, stream)
+        u64 = current_u(torch, s64)
+        rel = float(torch.max(torch.abs(u_mx - u64)) / torch.max(torch.abs(u64)))
+        t64 = sum(ms64) / 1e3
+        fp64 = {"steps_per_s": K / t64, "ms_per_step": 1e3 * t64 / K,
+                "iterations_per_step": st64["its"] / K, "krylov_its_per_s": st64["its"] / t64,
+                "kernel_ms": {"k_rhs": tim64["rhs_ms"] / K, "k_level64": tim64["level_ms"] / K},
+                "status": st64["status"],
+                "mixed_vs_fp64_max_rel_err_at_last_level": rel,
+                "mixed_speedup": (K / t_mx * (1 if world == 1 else 1)) / (K / t64)}
+        s64.close()
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        se, ms_e2e, _, _ = run_arm(torch, pkg, prob, "mixed", W, K, flush, stream, e2e=True)
+        se.close()
+        e2e = {"value": world * K / (sum(ms_e2e) / 1e3), "unit": "steps/s",
+               "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n,
+               "note": "per level: kappa^m and f^m copied from pinned host, tsfde_step, u^m copied back"}
+
+    # ---- rooflines from the per-kernel CUDA-event totals
+    peak, peak_kind = measured_peaks()
+    rhs_ms = tim_mx["rhs_ms"] / K
+    lvl_ms = tim_mx["level_ms"] / K
+    rhs_bytes = (16.0 * n * st_mx["E_active_sum"] + K * 8.0 * n * (3 + 1)) / K
+    lvl_bytes = (88.0 * n * st_mx["its"] + 40.0 * n * st_mx["outer"]) / K
+    rhs_gbs = rhs_bytes / (rhs_ms * 1e-3) / 1e9
+    lvl_gbs = lvl_bytes / (lvl_ms * 1e-3) / 1e9
+    dom = ("k_level_mixed", lvl_gbs) if lvl_ms >= rhs_ms else ("k_rhs", rhs_gbs)
+    roof = {"kernel": dom[0], "bound": "hbm", "achieved": dom[1], "peak": peak, "unit": "GB/s",
+            "frac": dom[1] / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(prob, args.cpu_sample_n, budget_s=20.0)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": world * K / t_mx, "unit": "steps/s", "n_gpus": world,
+            "steps": K, "warmup": W, "ms_per_step": t_mx * 1e3 / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "M": prob.M, "first_timed_level": W + 1,
+                       "precision": "mixed: FP32 inner PBiCGSTAB, FP64 refinement/residual/SOE",
+                       "krylov_tol": 1e-12, "inner_tol": 1e-2,
+                       "l2": "flushed before every timed level (256 MB write outside the events)",
+                       "parallelism": f"replicas x{world}"},
+            "status": st_mx["status"],
+            "iterations_per_step": st_mx["its"] / K, "outer_per_step": st_mx["outer"] / K,
+            "krylov_its_per_s": world * st_mx["its"] / t_mx,
+            "kernels": {"k_rhs": {"ms": rhs_ms, "bytes": rhs_bytes, "GB/s": rhs_gbs, "frac": rhs_gbs / peak},
+                        "k_level_mixed": {"ms": lvl_ms, "bytes": lvl_bytes, "GB/s": lvl_gbs,
+                                          "frac": lvl_gbs / peak}},
+            "fp64": fp64, "e2e": e2e, "gpu_launches": 2 * K, "roofline": roof,
+            "cpu_baseline": cpu, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    s_mx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------ CPU baseline
+def cpu_baseline_sample(prob, n_s, budget_s=20.0, levels=None, warmup=0):
+    """The oracle (plain C, one thread, dense LU per level, direct O(m n)
+    history sums) on the same workload generators at n_s interior points
+    and the full M-level mesh, for as many leading levels as fit the time
+    budget.  The per-level time is scaled to n = prob.n by (n/n_s)^3, the
+    growth of the dense LU that dominates at full size."""
+    import oracle
+    import tsfde_inputs as ti
+    p = ti.config_mixed(n=n_s, M=prob.M)
+    tm, tau = oracle.graded_mesh(p.T, p.M, p.r)
+    soe = oracle.soe_build(p.gamma, tau[1], p.T, p.soe_tol)
+    K = p.kappa_table(tm)
+    F = p.f_table(tm)
+    # probe the per-level cost at the start, then size the sample
+    lv = levels
+    if lv is None:
+        t0 = time.perf_counter()
+        oracle.march("FIDS", p.alpha, p.gamma, p.l, p.T, p.r, p.n, p.M, p.phi, K, F, soe=soe, levels=8)
+        per = (time.perf_counter() - t0) / 8
+        lv = int(max(8, min(p.M, budget_s / max(per, 1e-6) / 2)))
+    t_w = 0.0
+    if warmup:
+        t0 = time.perf_counter()
+        oracle.march("FIDS", p.alpha, p.gamma, p.l, p.T, p.r, p.n, p.M, p.phi, K, F, soe=soe, levels=warmup)
+        t_w = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.march("FIDS", p.alpha, p.gamma, p.l, p.T, p.r, p.n, p.M, p.phi, K, F, soe=soe, levels=warmup + lv)
+    el = time.perf_counter() - t0 - t_w
+    per_level = el / lv
+    scale = (prob.n / n_s) ** 3
+    return {"value": 1.0 / (per_level * scale), "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle FIDS (dense LU per level, direct history sums, SOE E={len(soe[0])}) on the "
+                       f"same generators at n={n_s}, levels {warmup + 1}..{warmup + lv} of M={p.M}: "
+                       f"{lv / el:.3f} levels/s measured; value = that rate scaled by (n_s/n)^3 = "
+                       f"1/{scale:.3g} to n={prob.n} (dense LU dominates at full size)"),
+            "sample_levels_per_s": lv / el, "sample_n": n_s}
+
+
+def reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import tsfde_inputs as ti
+    prob = ti.config_mixed(n=args.n, M=args.M)
+    W = args.warmup
+    K = args.steps if args.steps is not None else max(1, prob.M - W)
+    K = min(K, prob.M - W)
+    cpu = cpu_baseline_sample(prob, args.cpu_sample_n, levels=K, warmup=W)
+    line = {"metric": METRIC, "value": cpu["value"], "unit": "steps/s", "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": 1e3 / cpu["value"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "n": prob.n, "M": prob.M, "levels_timed": [W + 1, W + K],
+                       "parallelism": "one host thread"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": cpu["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        reference(a)
+    else:
+        ours(a)

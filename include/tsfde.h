@@ -1,0 +1,208 @@
+/*
+ * tsfde.h -- C ABI of the GB300 (sm_103a) implementation of the fast implicit
+ * difference scheme (FIDS) of Gu, Sun, Zhang and Zhao for the 1-D
+ * time-space fractional diffusion equation with the integral fractional
+ * Laplacian (arXiv 2002.11978):
+ *
+ *   C_0D_t^gamma u = -kappa(x,t) (-Delta)^{alpha/2} u + f   on (-l,l) x (0,T]
+ *   u = 0 outside (-l,l),  u(x,0) = phi(x)                      (Eq. (1.1))
+ *
+ * Each time level m solves (Eq. (3.16gu))
+ *   (a_m/Gamma(1-gamma) I + diag(kappa^m) A) u^m = b^m,
+ * where A is the symmetric Toeplitz IFL matrix of Eq. (3.16x) and b^m is
+ * built from the sum-of-exponentials history (Lemma 2.2, Eq. (lem2.3)), by
+ * Strang-circulant-preconditioned BiCGSTAB (Sec. 4.1, Eq. (4.3); Sec. 5).
+ *
+ * Conventions for every entry point:
+ *  - Return value: a tsfde_status (0 = TSFDE_OK).  No C++ exception crosses
+ *    the ABI.  tsfde_strerror() gives a static message.
+ *  - "dev" pointers are CUDA device pointers to contiguous IEEE doubles owned
+ *    by the caller; they must stay valid until the call's work has completed
+ *    on the context's stream.  "host" pointers are read during the call only.
+ *  - All device work is enqueued on the stream given in tsfde_opts.stream
+ *    (NULL = legacy default stream).  Calls that return per-call statistics
+ *    through an info struct synchronise that stream; others are asynchronous.
+ *  - A context owns all of its device workspaces; one context per stream.
+ *    Nothing is global.  Contexts are not thread-safe.
+ *  - n is the number of interior grid points (the paper's N - 1), so the
+ *    mesh size is h = 2l/(n+1) and x_i = -l + i h, i = 1..n.
+ */
+#ifndef TSFDE_H
+#define TSFDE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum tsfde_status {
+  TSFDE_OK = 0,
+  TSFDE_EINVAL = 1,      /* invalid argument (message names it)            */
+  TSFDE_ENOMEM = 2,      /* device or host allocation failed               */
+  TSFDE_ECUDA = 3,       /* a CUDA runtime call failed                     */
+  TSFDE_ENOCONV = 4,     /* Krylov iteration cap reached                   */
+  TSFDE_EBREAKDOWN = 5,  /* BiCGSTAB breakdown (rho, (r0,v) or (t,t) = 0)  */
+  TSFDE_ETIMEOUT = 6,    /* a device-side grid barrier gave up waiting     */
+  TSFDE_ESTATE = 7,      /* call not valid in the context's current state  */
+  TSFDE_ENONFINITE = 8,  /* NaN or Inf met in a residual or scalar         */
+  TSFDE_ENOTSUP = 9      /* option not supported by this build             */
+} tsfde_status;
+
+enum { TSFDE_FP64 = 0, TSFDE_MIXED = 1 };       /* tsfde_opts.precision */
+enum { TSFDE_STRANG = 0, TSFDE_PRECOND_NONE = 1 }; /* tsfde_opts.precond */
+
+typedef struct tsfde_opts {
+  double mu;            /* splitting parameter of Eq. (2.11), mu in (alpha,2];
+                           <= 0 selects the paper's default 1 + alpha/2     */
+  int kappa_mu;         /* 1 for mu < 2, 2 for mu = 2; 0 derives it from mu */
+  double krylov_tol;    /* FP64 path: stop when ||r_k||_2/||r_0||_2 < tol
+                           (recursive residual, x0 = 0, Sec. 5); mixed path:
+                           stop the FP64 refinement when the last correction
+                           satisfies max|e| <= tol * max|u|.  Default 1e-12 */
+  int max_it;           /* BiCGSTAB iteration cap per solve (default 2000)  */
+  int precision;        /* TSFDE_FP64 (default) or TSFDE_MIXED              */
+  int precond;          /* TSFDE_STRANG (default) or TSFDE_PRECOND_NONE     */
+  double inner_tol;     /* mixed: FP32 inner relative tolerance (def. 1e-2) */
+  int max_outer;        /* mixed: FP64 refinement cap (default 60)          */
+  int soe_E;            /* > 0: use the caller's SOE table below instead of
+                           building one (exponentials sorted ascending)     */
+  const double* soe_s;  /* host, soe_E nodes s_j > 0                        */
+  const double* soe_w;  /* host, soe_E weights w_j > 0                      */
+  int profile;          /* 1: time every launch with CUDA events on the
+                           context's stream (see tsfde_get_timing)          */
+  long long barrier_timeout_cycles; /* device barrier wait budget in SM
+                           clock cycles; 0 = default (about 2 s).  A tiny
+                           value makes every barrier give up and the call
+                           return TSFDE_ETIMEOUT: used to test that path.  */
+  void* stream;         /* cudaStream_t; NULL = default stream              */
+} tsfde_opts;
+
+typedef struct tsfde_step_info {
+  int64_t m;            /* time level just computed (1..M)                  */
+  int status;           /* tsfde_status of this level                       */
+  int iterations;       /* BiCGSTAB iterations (mixed: summed inner ones)   */
+  int outer;            /* mixed: FP64 refinement sweeps (0 for FP64 path)  */
+  int E_active;         /* exponentials still non-zero at this level        */
+  double rel_residual;  /* FP64 path: recursive ||r||/||b||; mixed: last
+                           computed FP64 ||b - M u||/||b||                  */
+} tsfde_step_info;
+
+typedef struct tsfde_solve_info {
+  int status;           /* first non-OK level status, else TSFDE_OK          */
+  int64_t failed_level; /* level of that status, 0 if none                  */
+  int64_t levels;       /* levels computed by this call                     */
+  int64_t iterations;   /* total BiCGSTAB iterations over those levels      */
+  int min_iterations, max_iterations;
+  int64_t outer;        /* total refinement sweeps (mixed)                  */
+  double max_rel_residual;
+  int E;                /* size of the SOE table                            */
+  int64_t E_active_sum; /* sum over the levels of the active exponentials   */
+} tsfde_solve_info;
+
+typedef struct tsfde_timing {
+  int64_t levels;       /* levels timed since the last tsfde_get_timing     */
+  double rhs_ms;        /* total device time of the SOE/right-hand-side
+                           kernel over those levels (CUDA events)           */
+  double level_ms;      /* total device time of the level-solve kernel      */
+} tsfde_timing;
+
+typedef struct tsfde_ctx tsfde_ctx;
+
+/* Defaults documented in tsfde_opts. */
+int tsfde_default_opts(tsfde_opts* opts);
+
+/* Build a context: graded mesh t_m = T (m/M)^r (Sec. 3.1), SOE table for
+ * t^{-gamma} on [tau_1, T] with relative tolerance soe_tol (Lemma 2.2; see
+ * tsfde_get_soe), the Toeplitz symbol of Eq. (3.16x) and its circulant
+ * embedding spectrum, the Strang eigenvalues of Sec. 4.1, and all device
+ * workspaces.  Validation: 0<alpha<2, 0<gamma<1, l>0, T>0, n>=1, M>=1, r>=1,
+ * soe_tol in (0, 1e-2], mu in (alpha, 2].  opts may be NULL (defaults).
+ * On error *out is NULL. */
+int tsfde_setup(tsfde_ctx** out, double alpha, double gamma, double l, double T,
+                int64_t n, int64_t M, double r, double soe_tol,
+                const tsfde_opts* opts);
+
+void tsfde_destroy(tsfde_ctx* ctx);
+const char* tsfde_strerror(int status);
+/* Message of the last failing call on this context ("" if none). */
+const char* tsfde_last_error(const tsfde_ctx* ctx);
+
+/* Problem data.  phi: dev n.  Diffusivity kappa(x_i, t_m) = kappa0_i +
+ * theta[m] kappa1_i (kappa1 dev n or NULL; theta host M+1 or NULL).  Source
+ * f(x_i, t_m) = sum_{q<rank} G[q*(M+1)+m] F[q][i] with rank <= 4, F a host
+ * array of rank dev pointers (n each), G host rank x (M+1).  Either part may
+ * instead be supplied per level to tsfde_step.  The context copies all of it.
+ * Resets the time level to 0. */
+int tsfde_set_problem(tsfde_ctx* ctx, const double* phi, const double* kappa0,
+                      const double* kappa1, const double* theta, int rank,
+                      const double* const* F, const double* G);
+
+/* Back to level 0 with the same problem (history cleared, u^0 = phi). */
+int tsfde_reset(tsfde_ctx* ctx);
+
+/* Advance one time level m -> m+1: SOE history update and right-hand side
+ * (Eq. (3.16gu) through the recurrence of the history sums), preconditioner
+ * for this level (Eq. (4.3)), and the Krylov solve.  kappa_m / f_m (dev n)
+ * override the separable data for this level when non-NULL.  u_out (dev n)
+ * receives u^{m+1} and rhs_out (dev n) the right-hand side b^{m+1}, when
+ * non-NULL.  info (nullable) synchronises.  TSFDE_ESTATE after level M. */
+int tsfde_step(tsfde_ctx* ctx, const double* kappa_m, const double* f_m,
+               double* u_out, double* rhs_out, tsfde_step_info* info);
+
+/* Run all remaining levels with the separable problem data.  u_final (dev n)
+ * receives u^M; u_all (dev (M+1) x n, row m = u^m, nullable) every level.
+ * info (nullable) synchronises and summarises. */
+int tsfde_solve(tsfde_ctx* ctx, double* u_final, double* u_all,
+                tsfde_solve_info* info);
+
+/* Per-level statistics of levels m0..m1 (1 <= m0 <= m1 <= current level)
+ * into out[0 .. m1-m0] (host).  Synchronises the stream. */
+int tsfde_get_level_stats(tsfde_ctx* ctx, int64_t m0, int64_t m1, tsfde_step_info* out);
+
+/* Copy the current level's solution u^m (m = 0 after set_problem/reset)
+ * into u (dev n).  Asynchronous. */
+int tsfde_get_solution(tsfde_ctx* ctx, double* u);
+
+/* Copy the SOE table (ascending s_j, Lemma 2.2) to host arrays of capacity
+ * *E (either may be NULL); *E returns the table size. */
+int tsfde_get_soe(const tsfde_ctx* ctx, int* E, double* s, double* w);
+
+/* Copy the graded mesh t_0..t_M (host, M+1). */
+int tsfde_get_times(const tsfde_ctx* ctx, double* t);
+
+/* Copy the first column t_0..t_{n-1} of A (Eq. (3.16x)) to host. */
+int tsfde_get_symbol(const tsfde_ctx* ctx, double* t);
+
+/* Device time of the kernels launched since the previous call (opts.profile
+ * must be 1).  Synchronises the stream and resets the counters. */
+int tsfde_get_timing(tsfde_ctx* ctx, tsfde_timing* out);
+
+/* ---- single operations of the hot path (used by tests and tools) ------ */
+
+/* y = A v (Toeplitz product by zero-padded FFT circulant embedding,
+ * Sec. 4.1).  v, y: dev n.  precision: TSFDE_FP64 or TSFDE_MIXED (FP32
+ * transform, FP64 in/out). */
+int tsfde_toeplitz_apply(tsfde_ctx* ctx, const double* v, double* y, int precision);
+
+/* y = (a I + diag(kappa) A) v, the matrix-free product of Sec. 4.1.
+ * kappa, v, y: dev n. */
+int tsfde_operator_apply(tsfde_ctx* ctx, double a, const double* kappa,
+                         const double* v, double* y, int precision);
+
+/* z = P^{-1} v with P = a I + kbar s(A), the Strang circulant preconditioner
+ * of Eq. (4.3) (kbar = mean of kappa).  Builds the preconditioner (circulant
+ * inverse kernel by a Bluestein length-n inverse DFT) and applies it.
+ * v, z: dev n. */
+int tsfde_precond_apply(tsfde_ctx* ctx, double a, double kbar, const double* v,
+                        double* z, int precision);
+
+/* Solve (a I + diag(kappa) A) x = b with the level solver selected by the
+ * context options (PBiCGSTAB, or mixed refinement).  kappa, b, x: dev n. */
+int tsfde_linear_solve(tsfde_ctx* ctx, double a, const double* kappa,
+                       const double* b, double* x, tsfde_step_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSFDE_H */

@@ -86,7 +86,8 @@ class OrProblem(ctypes.Structure):
                 ("mu", ctypes.c_double), ("kappa_mu", ctypes.c_int),
                 ("n", ctypes.c_int64), ("M", ctypes.c_int64),
                 ("phi", _dp), ("kappa", _dp), ("f", _dp),
-                ("soe_E", ctypes.c_int), ("soe_s", _dp), ("soe_w", _dp)]
+                ("soe_E", ctypes.c_int), ("soe_s", _dp), ("soe_w", _dp),
+                ("levels", ctypes.c_int64)]
 
 
 def _ptr(a: np.ndarray):
@@ -197,7 +198,7 @@ def strang_eigs(t: np.ndarray) -> np.ndarray:
 
 
 def _problem(alpha, gamma, l, T, r, n, M, phi, kappa, f, mu=None, kappa_mu=None,
-             soe=None):
+             soe=None, levels=0):
     if mu is None:
         mu, km = default_mu(alpha)
         kappa_mu = km if kappa_mu is None else kappa_mu
@@ -212,16 +213,17 @@ def _problem(alpha, gamma, l, T, r, n, M, phi, kappa, f, mu=None, kappa_mu=None,
                   _ptr(keep[0]), _ptr(keep[1]), _ptr(keep[2]),
                   0 if soe is None else len(keep[3]),
                   None if soe is None else _ptr(keep[3]),
-                  None if soe is None else _ptr(keep[4]))
+                  None if soe is None else _ptr(keep[4]), levels)
     return p, keep
 
 
 def march(scheme: str, alpha, gamma, l, T, r, n, M, phi, kappa, f, mu=None,
-          kappa_mu=None, soe=None) -> np.ndarray:
-    """Full time march with dense LU per level.  scheme = 'DIDS' (Eq. (3.16))
+          kappa_mu=None, soe=None, levels: int = 0) -> np.ndarray:
+    """Time march with dense LU per level.  scheme = 'DIDS' (Eq. (3.16))
     or 'FIDS' (Eq. (3.15), needs soe=(s, w)).  kappa, f: (M+1, n) tables.
-    Returns U of shape (M+1, n)."""
-    p, keep = _problem(alpha, gamma, l, T, r, n, M, phi, kappa, f, mu, kappa_mu, soe)
+    Returns U of shape (M+1, n); with levels > 0 only rows 0..levels are
+    computed (the rest stay zero)."""
+    p, keep = _problem(alpha, gamma, l, T, r, n, M, phi, kappa, f, mu, kappa_mu, soe, levels)
     if scheme == "FIDS" and soe is None:
         raise ValueError("FIDS needs an SOE table")
     U = np.zeros((M + 1, n))

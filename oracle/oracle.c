@@ -259,7 +259,8 @@ int or_march(const or_problem* p, int scheme, double* U) {
   double* rhs = (double*)malloc(sizeof(double) * (size_t)n);
   memcpy(U, p->phi, sizeof(double) * (size_t)n);
   int status = 0;
-  for (int64_t m = 1; m <= M && status == 0; ++m) {
+  const int64_t last = (p->levels > 0 && p->levels < M) ? p->levels : M;
+  for (int64_t m = 1; m <= last && status == 0; ++m) {
     level_weights(p, scheme, m, c);
     /* right-hand side of Eq. (3.16gu)/(4.1):
      * Gamma(1-g)^{-1}[ sum_{k=1}^{m-1} (c_{k+1}-c_k) u^k + c_1 u^0 ] + f^m */

@@ -97,6 +97,7 @@ typedef struct {
   int soe_E;
   const double* soe_s;
   const double* soe_w;
+  int64_t levels;  /* march levels 1..levels only (0 = all M) */
 } or_problem;
 
 int or_march(const or_problem* p, int scheme, double* U);

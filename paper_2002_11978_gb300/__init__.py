@@ -1,0 +1,313 @@
+"""Python binding of libtsfde (include/tsfde.h): the GB300 implementation of
+the fast implicit difference scheme for the time-space fractional diffusion
+equation with the integral fractional Laplacian (arXiv 2002.11978).
+
+This module only marshals arguments: every step of the solver runs in the
+CUDA library.  PyTorch provides device memory and the stream.  There is no
+CPU fallback -- without the compiled library or a CUDA device the calls
+raise.
+
+Low-level names mirror the C ABI (``tsfde_setup``, ``tsfde_step``, ...);
+``Solver`` wraps a context for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libtsfde.so")
+
+TSFDE_OK, TSFDE_EINVAL, TSFDE_ENOMEM, TSFDE_ECUDA, TSFDE_ENOCONV = 0, 1, 2, 3, 4
+TSFDE_EBREAKDOWN, TSFDE_ETIMEOUT, TSFDE_ESTATE, TSFDE_ENONFINITE, TSFDE_ENOTSUP = 5, 6, 7, 8, 9
+TSFDE_FP64, TSFDE_MIXED = 0, 1
+TSFDE_STRANG, TSFDE_PRECOND_NONE = 0, 1
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class tsfde_opts(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_double), ("kappa_mu", ctypes.c_int),
+                ("krylov_tol", ctypes.c_double), ("max_it", ctypes.c_int),
+                ("precision", ctypes.c_int), ("precond", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
+                ("soe_E", ctypes.c_int), ("soe_s", _dp), ("soe_w", _dp), ("profile", ctypes.c_int),
+                ("barrier_timeout_cycles", ctypes.c_longlong), ("stream", ctypes.c_void_p)]
+
+
+class tsfde_step_info(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("status", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("outer", ctypes.c_int), ("E_active", ctypes.c_int),
+                ("rel_residual", ctypes.c_double)]
+
+
+class tsfde_solve_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("failed_level", ctypes.c_int64),
+                ("levels", ctypes.c_int64), ("iterations", ctypes.c_int64),
+                ("min_iterations", ctypes.c_int), ("max_iterations", ctypes.c_int),
+                ("outer", ctypes.c_int64), ("max_rel_residual", ctypes.c_double),
+                ("E", ctypes.c_int), ("E_active_sum", ctypes.c_int64)]
+
+
+class tsfde_timing(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int64), ("rhs_ms", ctypes.c_double),
+                ("level_ms", ctypes.c_double)]
+
+
+# (name, restype, argtypes) of every entry point in include/tsfde.h
+_V = ctypes.c_void_p
+_SIGNATURES = [
+    ("tsfde_default_opts", ctypes.c_int, [ctypes.POINTER(tsfde_opts)]),
+    ("tsfde_setup", ctypes.c_int, [ctypes.POINTER(_V), ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                   ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                   ctypes.POINTER(tsfde_opts)]),
+    ("tsfde_destroy", None, [_V]),
+    ("tsfde_strerror", ctypes.c_char_p, [ctypes.c_int]),
+    ("tsfde_last_error", ctypes.c_char_p, [_V]),
+    ("tsfde_set_problem", ctypes.c_int, [_V, _V, _V, _V, _dp, ctypes.c_int,
+                                         ctypes.POINTER(_V), _dp]),
+    ("tsfde_reset", ctypes.c_int, [_V]),
+    ("tsfde_step", ctypes.c_int, [_V, _V, _V, _V, _V, ctypes.POINTER(tsfde_step_info)]),
+    ("tsfde_solve", ctypes.c_int, [_V, _V, _V, ctypes.POINTER(tsfde_solve_info)]),
+    ("tsfde_get_soe", ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int), _dp, _dp]),
+    ("tsfde_get_times", ctypes.c_int, [_V, _dp]),
+    ("tsfde_get_symbol", ctypes.c_int, [_V, _dp]),
+    ("tsfde_get_timing", ctypes.c_int, [_V, ctypes.POINTER(tsfde_timing)]),
+    ("tsfde_get_level_stats", ctypes.c_int, [_V, ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.POINTER(tsfde_step_info)]),
+    ("tsfde_get_solution", ctypes.c_int, [_V, _V]),
+    ("tsfde_toeplitz_apply", ctypes.c_int, [_V, _V, _V, ctypes.c_int]),
+    ("tsfde_operator_apply", ctypes.c_int, [_V, ctypes.c_double, _V, _V, _V, ctypes.c_int]),
+    ("tsfde_precond_apply", ctypes.c_int, [_V, ctypes.c_double, ctypes.c_double, _V, _V,
+                                           ctypes.c_int]),
+    ("tsfde_linear_solve", ctypes.c_int, [_V, ctypes.c_double, _V, _V, _V,
+                                          ctypes.POINTER(tsfde_step_info)]),
+]
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtsfde.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"{path} not found: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(path)
+        for name, res, args in _SIGNATURES:
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_names():
+    return [s[0] for s in _SIGNATURES]
+
+
+class TsfdeError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def _check(status: int, ctx=None):
+    if status != TSFDE_OK:
+        lib = load_library()
+        detail = lib.tsfde_last_error(ctx).decode() if ctx else ""
+        raise TsfdeError(status, f"{lib.tsfde_strerror(status).decode()}: {detail}")
+
+
+def _dev(t, n=None, name="tensor"):
+    """Device pointer of a contiguous CUDA float64 tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements, has {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def default_opts() -> tsfde_opts:
+    o = tsfde_opts()
+    _check(load_library().tsfde_default_opts(ctypes.byref(o)))
+    return o
+
+
+class Solver:
+    """One FIDS problem: tsfde_setup + tsfde_set_problem + stepping."""
+
+    def __init__(self, alpha, gamma, l, T, n, M, r, soe_tol=1e-12, *, precision="fp64",
+                 precond="strang", krylov_tol=1e-12, max_it=2000, inner_tol=1e-2,
+                 max_outer=60, mu=None, kappa_mu=None, soe=None, barrier_timeout_cycles=0,
+                 profile=False, stream=None):
+        lib = load_library()
+        o = default_opts()
+        o.krylov_tol = krylov_tol
+        o.max_it = max_it
+        o.precision = {"fp64": TSFDE_FP64, "mixed": TSFDE_MIXED}[precision]
+        o.precond = {"strang": TSFDE_STRANG, "none": TSFDE_PRECOND_NONE}[precond]
+        o.inner_tol = inner_tol
+        o.max_outer = max_outer
+        o.mu = 0.0 if mu is None else mu
+        o.kappa_mu = 0 if kappa_mu is None else kappa_mu
+        o.barrier_timeout_cycles = barrier_timeout_cycles
+        o.profile = 1 if profile else 0
+        self._keep = []
+        if soe is not None:
+            s = np.ascontiguousarray(soe[0], dtype=np.float64)
+            w = np.ascontiguousarray(soe[1], dtype=np.float64)
+            self._keep += [s, w]
+            o.soe_E = len(s)
+            o.soe_s = s.ctypes.data_as(_dp)
+            o.soe_w = w.ctypes.data_as(_dp)
+        self.stream = stream
+        o.stream = _stream_handle(stream)
+        self.n, self.M = int(n), int(M)
+        self.m = 0  # current time level
+        self.ctx = ctypes.c_void_p()
+        _check(lib.tsfde_setup(ctypes.byref(self.ctx), alpha, gamma, l, T, self.n, self.M, r,
+                               soe_tol, ctypes.byref(o)))
+        self.lib = lib
+
+    def close(self):
+        if self.ctx:
+            self.lib.tsfde_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- problem data
+    def set_problem(self, phi, kappa0, kappa1=None, theta=None, F=(), G=None):
+        n, M = self.n, self.M
+        th = None
+        if theta is not None:
+            th = np.ascontiguousarray(theta, dtype=np.float64)
+            assert th.shape == (M + 1,)
+        F = list(F)
+        rank = len(F)
+        Farr = (ctypes.c_void_p * max(rank, 1))(*[_dev(f, n, "F").value for f in F])
+        Garr = None
+        if rank:
+            Garr = np.ascontiguousarray(G, dtype=np.float64).reshape(rank, M + 1)
+        self._problem_keep = [phi, kappa0, kappa1, F, th, Garr]
+        _check(self.lib.tsfde_set_problem(
+            self.ctx, _dev(phi, n, "phi"), _dev(kappa0, n, "kappa0"), _dev(kappa1, n, "kappa1"),
+            None if th is None else th.ctypes.data_as(_dp), rank,
+            ctypes.cast(Farr, ctypes.POINTER(ctypes.c_void_p)),
+            None if Garr is None else Garr.ctypes.data_as(_dp)), self.ctx)
+        self.m = 0
+
+    def set_problem_from(self, prob):
+        """Feed a tsfde_inputs.Problem (separable form) through set_problem."""
+        import torch
+        dev = torch.device("cuda")
+        t = self.times()
+        to = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+        F = [to(f) for f in prob.F]
+        self.set_problem(to(prob.phi), to(prob.kappa0),
+                         None if prob.kappa1 is None else to(prob.kappa1),
+                         prob.theta_values(t), F, prob.G_values(t) if F else None)
+
+    def reset(self):
+        _check(self.lib.tsfde_reset(self.ctx), self.ctx)
+        self.m = 0
+
+    # ---- stepping
+    def step(self, kappa_m=None, f_m=None, u_out=None, rhs_out=None, sync=True):
+        info = tsfde_step_info()
+        _check(self.lib.tsfde_step(self.ctx, _dev(kappa_m, self.n, "kappa_m"),
+                                   _dev(f_m, self.n, "f_m"), _dev(u_out, self.n, "u_out"),
+                                   _dev(rhs_out, self.n, "rhs_out"),
+                                   ctypes.byref(info) if sync else None), self.ctx)
+        self.m += 1
+        return _info_dict(info) if sync else None
+
+    def solve(self, u_final, u_all=None, sync=True):
+        info = tsfde_solve_info()
+        _check(self.lib.tsfde_solve(self.ctx, _dev(u_final, self.n, "u_final"),
+                                    _dev(u_all, (self.M + 1) * self.n, "u_all"),
+                                    ctypes.byref(info) if sync else None), self.ctx)
+        self.m = self.M
+        return _info_dict(info) if sync else None
+
+    # ---- tables
+    def soe(self):
+        E = ctypes.c_int(0)
+        _check(self.lib.tsfde_get_soe(self.ctx, ctypes.byref(E), None, None), self.ctx)
+        s = np.zeros(E.value)
+        w = np.zeros(E.value)
+        _check(self.lib.tsfde_get_soe(self.ctx, ctypes.byref(E), s.ctypes.data_as(_dp),
+                                      w.ctypes.data_as(_dp)), self.ctx)
+        return s, w
+
+    def times(self):
+        t = np.zeros(self.M + 1)
+        _check(self.lib.tsfde_get_times(self.ctx, t.ctypes.data_as(_dp)), self.ctx)
+        return t
+
+    def timing(self):
+        t = tsfde_timing()
+        _check(self.lib.tsfde_get_timing(self.ctx, ctypes.byref(t)), self.ctx)
+        return _info_dict(t)
+
+    def level_stats(self, m0, m1):
+        out = (tsfde_step_info * (m1 - m0 + 1))()
+        _check(self.lib.tsfde_get_level_stats(self.ctx, m0, m1, out), self.ctx)
+        return [_info_dict(x) for x in out]
+
+    def current_solution(self, u):
+        _check(self.lib.tsfde_get_solution(self.ctx, _dev(u, self.n, "u")), self.ctx)
+
+    def symbol(self):
+        t = np.zeros(self.n)
+        _check(self.lib.tsfde_get_symbol(self.ctx, t.ctypes.data_as(_dp)), self.ctx)
+        return t
+
+    # ---- single operations
+    def toeplitz_apply(self, v, y, precision="fp64"):
+        _check(self.lib.tsfde_toeplitz_apply(self.ctx, _dev(v, self.n, "v"), _dev(y, self.n, "y"),
+                                             _prec(precision)), self.ctx)
+
+    def operator_apply(self, a, kappa, v, y, precision="fp64"):
+        _check(self.lib.tsfde_operator_apply(self.ctx, a, _dev(kappa, self.n, "kappa"),
+                                             _dev(v, self.n, "v"), _dev(y, self.n, "y"),
+                                             _prec(precision)), self.ctx)
+
+    def precond_apply(self, a, kbar, v, z, precision="fp64"):
+        _check(self.lib.tsfde_precond_apply(self.ctx, a, kbar, _dev(v, self.n, "v"),
+                                            _dev(z, self.n, "z"), _prec(precision)), self.ctx)
+
+    def linear_solve(self, a, kappa, b, x):
+        info = tsfde_step_info()
+        _check(self.lib.tsfde_linear_solve(self.ctx, a, _dev(kappa, self.n, "kappa"),
+                                           _dev(b, self.n, "b"), _dev(x, self.n, "x"),
+                                           ctypes.byref(info)), self.ctx)
+        return _info_dict(info)
+
+
+def _prec(p):
+    return {"fp64": TSFDE_FP64, "mixed": TSFDE_MIXED, "fp32": TSFDE_MIXED}[p]
+
+
+def _info_dict(info):
+    return {f: getattr(info, f) for f, _ in info._fields_}

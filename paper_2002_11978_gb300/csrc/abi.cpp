@@ -1,0 +1,691 @@
+// abi.cpp -- C ABI of the FIDS solver: argument validation, setup tables,
+// device workspaces and the per-level launch sequence.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/tsfde.h"
+#include "host_math.h"
+#include "plan.h"
+
+using namespace tsfde;
+
+struct tsfde_ctx {
+  double alpha = 0, gamma = 0, l = 0, T = 0, r = 0, soe_tol = 0, mu = 0;
+  int kappa_mu = 1;
+  int64_t n = 0, M = 0;
+  tsfde_opts opts{};
+  cudaStream_t stream = nullptr;
+  int64_t m = 0;
+  bool have_problem = false;
+  std::string err;
+  // host tables
+  std::vector<double> tmesh, ahat, soe_s, soe_w, symbol, theta, Gsrc, eps_h, cw_h;
+  std::vector<int> Eact;
+  int E = 0, rank = 0, ld = 0;
+  bool kap1 = false;
+  // device
+  DevPlan P{};
+  std::vector<void*> allocs;
+  double *G = nullptr, *eps = nullptr, *cw = nullptr;
+  double* u[3] = {nullptr, nullptr, nullptr};
+  double *b = nullptr, *kappa64 = nullptr, *phi = nullptr, *kap0 = nullptr, *kap1d = nullptr;
+  double* F = nullptr;
+  float* kappa32 = nullptr;
+  KVecs<double> k64{};
+  KVecs<float> k32{};
+  double* r64 = nullptr;
+  StepStat* stats = nullptr;
+  int* status = nullptr;
+  // profiling: three events per level (before rhs, after rhs, after level)
+  std::vector<cudaEvent_t> ev_free, ev_used;
+};
+
+namespace {
+
+const double kTimeoutDefault = 2.0e9;
+
+int fail(tsfde_ctx* c, int st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+int cuda_fail(tsfde_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, TSFDE_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T> bool dalloc(tsfde_ctx* c, T** p, size_t count) {
+  void* q = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) return false;
+  c->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return true;
+}
+
+template <typename T> cudaError_t upload(T* dst, const std::vector<T>& src) {
+  return cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+int ilog2(int64_t x) {
+  int k = 0;
+  while ((int64_t(1) << k) < x) ++k;
+  return k;
+}
+
+Geo make_geo(int Nfft) {
+  Geo g{};
+  const int lg = ilog2(Nfft);
+  g.Nfft = Nfft;
+  g.lgN1 = (lg + 1) / 2;
+  g.N1 = 1 << g.lgN1;
+  g.lgN2 = lg - g.lgN1;
+  g.N2 = 1 << g.lgN2;
+  g.lgct64 = std::min(1, g.lgN2);
+  g.lgct32 = std::min(1, g.lgN2);
+  return g;
+}
+
+int items(const Geo& g) {
+  return std::max((g.N2 >> std::min(g.lgct64, g.lgct32)), (g.N1 >> 1) + 1);
+}
+
+}  // namespace
+
+extern "C" {
+
+int tsfde_default_opts(tsfde_opts* o) {
+  if (!o) return TSFDE_EINVAL;
+  std::memset(o, 0, sizeof(*o));
+  o->mu = 0.0;
+  o->kappa_mu = 0;
+  o->krylov_tol = 1e-12;
+  o->max_it = 2000;
+  o->precision = TSFDE_FP64;
+  o->precond = TSFDE_STRANG;
+  o->inner_tol = 1e-2;
+  o->max_outer = 60;
+  o->soe_E = 0;
+  o->soe_s = nullptr;
+  o->soe_w = nullptr;
+  o->profile = 0;
+  o->barrier_timeout_cycles = 0;
+  o->stream = nullptr;
+  return TSFDE_OK;
+}
+
+const char* tsfde_strerror(int s) {
+  switch (s) {
+    case TSFDE_OK: return "ok";
+    case TSFDE_EINVAL: return "invalid argument";
+    case TSFDE_ENOMEM: return "out of memory";
+    case TSFDE_ECUDA: return "CUDA runtime error";
+    case TSFDE_ENOCONV: return "Krylov iteration cap reached";
+    case TSFDE_EBREAKDOWN: return "BiCGSTAB breakdown";
+    case TSFDE_ETIMEOUT: return "device barrier timed out";
+    case TSFDE_ESTATE: return "call not valid in the current state";
+    case TSFDE_ENONFINITE: return "non-finite value in the solver";
+    case TSFDE_ENOTSUP: return "unsupported option";
+    default: return "unknown status";
+  }
+}
+
+const char* tsfde_last_error(const tsfde_ctx* c) { return c ? c->err.c_str() : ""; }
+
+void tsfde_destroy(tsfde_ctx* c) {
+  if (!c) return;
+  for (cudaEvent_t e : c->ev_used) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
+  for (void* p : c->allocs) cudaFree(p);
+  delete c;
+}
+
+static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double T, int64_t n,
+                      int64_t M, double r, double soe_tol, const tsfde_opts* opts) {
+  if (opts) c->opts = *opts; else tsfde_default_opts(&c->opts);
+  tsfde_opts& o = c->opts;
+  if (!(alpha > 0.0 && alpha < 2.0)) return fail(c, TSFDE_EINVAL, "alpha must be in (0,2)");
+  if (!(gamma > 0.0 && gamma < 1.0)) return fail(c, TSFDE_EINVAL, "gamma must be in (0,1)");
+  if (!(l > 0.0) || !std::isfinite(l)) return fail(c, TSFDE_EINVAL, "l must be positive");
+  if (!(T > 0.0) || !std::isfinite(T)) return fail(c, TSFDE_EINVAL, "T must be positive");
+  if (n < 1) return fail(c, TSFDE_EINVAL, "n must be >= 1");
+  if (n > (int64_t(1) << 19)) return fail(c, TSFDE_ENOTSUP, "n > 2^19 is not supported");
+  if (M < 1) return fail(c, TSFDE_EINVAL, "M must be >= 1");
+  if (!(r >= 1.0) || !std::isfinite(r)) return fail(c, TSFDE_EINVAL, "grading r must be >= 1");
+  if (!(soe_tol > 0.0 && soe_tol <= 1e-2)) return fail(c, TSFDE_EINVAL, "soe_tol must be in (0,1e-2]");
+  double mu = o.mu > 0.0 ? o.mu : 1.0 + 0.5 * alpha;
+  if (!(mu > alpha && mu <= 2.0)) return fail(c, TSFDE_EINVAL, "mu must be in (alpha,2]");
+  int kmu = o.kappa_mu > 0 ? o.kappa_mu : (mu == 2.0 ? 2 : 1);
+  if (kmu != 1 && kmu != 2) return fail(c, TSFDE_EINVAL, "kappa_mu must be 1 or 2");
+  if (!(o.krylov_tol > 0.0)) return fail(c, TSFDE_EINVAL, "krylov_tol must be positive");
+  if (o.max_it < 1) return fail(c, TSFDE_EINVAL, "max_it must be >= 1");
+  if (o.precision != TSFDE_FP64 && o.precision != TSFDE_MIXED)
+    return fail(c, TSFDE_EINVAL, "precision must be TSFDE_FP64 or TSFDE_MIXED");
+  if (o.precond != TSFDE_STRANG && o.precond != TSFDE_PRECOND_NONE)
+    return fail(c, TSFDE_EINVAL, "precond must be TSFDE_STRANG or TSFDE_PRECOND_NONE");
+  if (o.precision == TSFDE_MIXED && (!(o.inner_tol > 0.0 && o.inner_tol < 1.0) || o.max_outer < 1))
+    return fail(c, TSFDE_EINVAL, "mixed needs inner_tol in (0,1) and max_outer >= 1");
+  if (o.barrier_timeout_cycles < 0) return fail(c, TSFDE_EINVAL, "barrier_timeout_cycles < 0");
+  c->alpha = alpha; c->gamma = gamma; c->l = l; c->T = T; c->n = n; c->M = M; c->r = r;
+  c->soe_tol = soe_tol; c->mu = mu; c->kappa_mu = kmu;
+  c->stream = static_cast<cudaStream_t>(o.stream);
+
+  // ---- mesh and per-level scalars (Sec. 3.1, Eq. (2.8))
+  c->tmesh.resize(M + 1);
+  for (int64_t m = 0; m <= M; ++m) c->tmesh[m] = mesh_t(T, M, r, m);
+  std::vector<double> tau(M + 1, 0.0);
+  for (int64_t m = 1; m <= M; ++m) tau[m] = mesh_gap(T, M, r, m, m - 1);
+  const double G2 = std::tgamma(2.0 - gamma), G1 = std::tgamma(1.0 - gamma);
+  c->ahat.assign(M + 1, 0.0);
+  for (int64_t m = 1; m <= M; ++m) c->ahat[m] = std::pow(tau[m], -gamma) / G2;
+
+  // ---- SOE table (Lemma 2.2)
+  if (o.soe_E > 0) {
+    if (!o.soe_s || !o.soe_w) return fail(c, TSFDE_EINVAL, "soe_E > 0 needs soe_s and soe_w");
+    c->soe_s.assign(o.soe_s, o.soe_s + o.soe_E);
+    c->soe_w.assign(o.soe_w, o.soe_w + o.soe_E);
+    for (int j = 0; j < o.soe_E; ++j) {
+      if (!(c->soe_s[j] > 0.0) || !(c->soe_w[j] > 0.0)) return fail(c, TSFDE_EINVAL, "SOE nodes/weights must be positive");
+      if (j > 0 && c->soe_s[j] < c->soe_s[j - 1]) return fail(c, TSFDE_EINVAL, "SOE nodes must be ascending");
+    }
+  } else {
+    std::string why;
+    if (!soe_build(gamma, tau[1], T, soe_tol, c->soe_s, c->soe_w, &why)) return fail(c, TSFDE_EINVAL, why);
+  }
+  const int E = c->E = (int)c->soe_s.size();
+  c->eps_h.assign((size_t)(M + 1) * E, 0.0);
+  c->cw_h.assign((size_t)(M + 1) * E, 0.0);
+  c->Eact.assign(M + 1, 0);
+  for (int64_t m = 2; m <= M; ++m) {
+    int act = 0;
+    for (int j = 0; j < E; ++j) {
+      const double sj = c->soe_s[j];
+      const double e = std::exp(-sj * tau[m]);
+      const double x = sj * tau[m - 1];
+      const double beta = (x == 0.0) ? 1.0 : -std::expm1(-x) / x;
+      c->eps_h[m * E + j] = e;
+      c->cw_h[m * E + j] = c->soe_w[j] * beta / G1;
+      if (e > 0.0) act = j + 1;
+    }
+    c->Eact[m] = act;
+  }
+  c->Eact[1] = 0;
+
+  // ---- IFL symbol (Eq. (3.16x)), spectra and Strang eigenvalues (Sec. 4.1)
+  c->symbol = ifl_symbol(alpha, mu, kmu, n, l);
+  int64_t L = 8;
+  while (L < 2 * n - 1) L *= 2;
+  DevPlan& P = c->P;
+  P.n = (int)n;
+  P.L = (int)L;
+  P.Nc = (int)(L / 2);
+  P.gr = make_geo(P.Nc);
+  P.gc = make_geo(P.L);
+  P.T = std::max(std::max(P.gr.N1, P.gr.N2), std::max(P.gc.N1, P.gc.N2));
+  P.W = std::max(std::max(P.gr.N1 << P.gr.lgct64, 2 * P.gr.N2),
+                 std::max(P.gc.N1 << P.gc.lgct64, 2 * P.gc.N2));
+  P.timeout = o.barrier_timeout_cycles > 0 ? o.barrier_timeout_cycles : (long long)kTimeoutDefault;
+
+  std::vector<double> S = embed_spectrum(c->symbol, L);
+  std::vector<cd> tw = twiddles(L);
+  std::vector<double> lam = strang_eigs(c->symbol, L);
+  for (double x : lam)
+    if (!(x > 0.0)) return fail(c, TSFDE_EINVAL, "Strang eigenvalue not positive (Lemma 4.1 violated)");
+  const int Nc = P.Nc, N1 = P.gr.N1, N2 = P.gr.N2;
+  std::vector<double> sig(Nc), sig32d;
+  std::vector<double2> rho(Nc);
+  for (int k1 = 0; k1 < N1; ++k1)
+    for (int k2 = 0; k2 < N2; ++k2) {
+      const int k = k1 + N1 * k2;
+      const int kp = (k == 0) ? Nc : Nc - k;
+      const double sg = 0.5 * (S[k] + S[kp]) / Nc;
+      const double dl = 0.5 * (S[k] - S[kp]) / Nc;
+      sig[k1 * N2 + k2] = sg;
+      rho[k1 * N2 + k2] = make_double2(dl * tw[k].real(), dl * tw[k].imag());
+    }
+  std::vector<double2> ch64(n), tw64(L);
+  std::vector<float2> ch32(n), tw32(L);
+  for (int64_t j = 0; j < n; ++j) {
+    cd v = chirp(j, n, +1);
+    ch64[j] = make_double2(v.real(), v.imag());
+    ch32[j] = make_float2((float)v.real(), (float)v.imag());
+  }
+  for (int64_t k = 0; k < L; ++k) {
+    tw64[k] = make_double2(tw[k].real(), tw[k].imag());
+    tw32[k] = make_float2((float)tw[k].real(), (float)tw[k].imag());
+  }
+  std::vector<cd> bk(L, cd(0, 0));
+  for (int64_t m = 0; m < n; ++m) bk[m] = std::conj(chirp(m, n, +1));
+  for (int64_t m = 1; m < n; ++m) bk[L - m] = std::conj(chirp(m, n, +1));
+  fft_inplace(bk, -1);
+  std::vector<double2> Bh64(L);
+  std::vector<float2> Bh32(L);
+  {
+    const int M1 = P.gc.N1, M2 = P.gc.N2;
+    for (int k1 = 0; k1 < M1; ++k1)
+      for (int k2 = 0; k2 < M2; ++k2) {
+        cd v = bk[k1 + (int64_t)M1 * k2] / (double)L;
+        Bh64[k1 * M2 + k2] = make_double2(v.real(), v.imag());
+        Bh32[k1 * M2 + k2] = make_float2((float)v.real(), (float)v.imag());
+      }
+  }
+  std::vector<float> sig32(Nc);
+  std::vector<float2> rho32(Nc);
+  for (int i = 0; i < Nc; ++i) {
+    sig32[i] = (float)sig[i];
+    rho32[i] = make_float2((float)rho[i].x, (float)rho[i].y);
+  }
+
+  // ---- grid size
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetDevice");
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaDeviceGetAttribute");
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop) return fail(c, TSFDE_ENOTSUP, "device lacks cooperative launch");
+  const size_t smem = plan_smem_bytes(P);
+  const int bps = coop_blocks_per_sm(smem);
+  if (bps < 1) return fail(c, TSFDE_ECUDA, "cooperative kernels do not fit on an SM");
+  const int maxG = nsm * std::min(bps, 2);
+  P.G = std::max(1, std::min(maxG, std::max(items(P.gr), items(P.gc))));
+
+  // ---- device allocations
+  const int64_t ld = ((n + 31) / 32) * 32;
+  c->ld = (int)ld;
+  bool ok = true;
+  double2 *dtw64, *drho64, *dch64, *dBh64, *drhoG64, *dS1, *dS2;
+  float2 *dtw32, *drho32, *dch32, *dBh32, *drhoG32;
+  double *dsig64, *dlam, *dsigG64, *dg64, *dpart;
+  float *dsig32, *dsigG32, *dg32;
+  GridBarrier* dbar;
+  ok &= dalloc(c, &dtw64, L) && dalloc(c, &dtw32, L);
+  ok &= dalloc(c, &dsig64, Nc) && dalloc(c, &drho64, Nc) && dalloc(c, &dsig32, Nc) && dalloc(c, &drho32, Nc);
+  ok &= dalloc(c, &dlam, n) && dalloc(c, &dch64, n) && dalloc(c, &dch32, n);
+  ok &= dalloc(c, &dBh64, L) && dalloc(c, &dBh32, L);
+  ok &= dalloc(c, &dsigG64, Nc) && dalloc(c, &drhoG64, Nc) && dalloc(c, &dsigG32, Nc) && dalloc(c, &drhoG32, Nc);
+  ok &= dalloc(c, &dg64, n) && dalloc(c, &dg32, n);
+  ok &= dalloc(c, &dS1, L) && dalloc(c, &dS2, L);
+  ok &= dalloc(c, &dpart, (size_t)kSlots * P.G) && dalloc(c, &dbar, 1);
+  ok &= dalloc(c, &c->G, (size_t)std::max(E, 1) * ld);
+  ok &= dalloc(c, &c->eps, c->eps_h.size()) && dalloc(c, &c->cw, c->cw_h.size());
+  for (int q = 0; q < 3; ++q) ok &= dalloc(c, &c->u[q], n);
+  ok &= dalloc(c, &c->b, n) && dalloc(c, &c->kappa64, n) && dalloc(c, &c->kappa32, n);
+  ok &= dalloc(c, &c->phi, n) && dalloc(c, &c->kap0, n) && dalloc(c, &c->kap1d, n);
+  ok &= dalloc(c, &c->F, 4 * n) && dalloc(c, &c->r64, n);
+  double** v64[] = {&c->k64.r, &c->k64.rh, &c->k64.p, &c->k64.v, &c->k64.s, &c->k64.t, &c->k64.ph, &c->k64.sh};
+  for (double** p : v64) ok &= dalloc(c, p, n);
+  float** v32[] = {&c->k32.x, &c->k32.r, &c->k32.rh, &c->k32.p, &c->k32.v, &c->k32.s, &c->k32.t, &c->k32.ph, &c->k32.sh};
+  for (float** p : v32) ok &= dalloc(c, p, n);
+  ok &= dalloc(c, &c->stats, M + 1) && dalloc(c, &c->status, 1);
+  if (!ok) return fail(c, TSFDE_ENOMEM, "cudaMalloc failed");
+  c->k64.x = nullptr;
+
+  if ((e = upload(dtw64, tw64)) != cudaSuccess || (e = upload(dtw32, tw32)) != cudaSuccess ||
+      (e = upload(dsig64, sig)) != cudaSuccess || (e = upload(drho64, rho)) != cudaSuccess ||
+      (e = upload(dsig32, sig32)) != cudaSuccess || (e = upload(drho32, rho32)) != cudaSuccess ||
+      (e = upload(dlam, lam)) != cudaSuccess || (e = upload(dch64, ch64)) != cudaSuccess ||
+      (e = upload(dch32, ch32)) != cudaSuccess || (e = upload(dBh64, Bh64)) != cudaSuccess ||
+      (e = upload(dBh32, Bh32)) != cudaSuccess || (e = upload(c->eps, c->eps_h)) != cudaSuccess ||
+      (e = upload(c->cw, c->cw_h)) != cudaSuccess)
+    return cuda_fail(c, e, "upload");
+  if ((e = cudaMemset(c->G, 0, sizeof(double) * (size_t)std::max(E, 1) * ld)) != cudaSuccess)
+    return cuda_fail(c, e, "cudaMemset");
+  if ((e = cudaMemset(c->stats, 0, sizeof(StepStat) * (M + 1))) != cudaSuccess) return cuda_fail(c, e, "cudaMemset");
+  P.bar = dbar; P.part = dpart;
+  P.twL64 = dtw64; P.twL32 = dtw32;
+  P.sigT64 = dsig64; P.rhoT64 = drho64; P.sigT32 = dsig32; P.rhoT32 = drho32;
+  P.lam = dlam; P.chirp64 = dch64; P.chirp32 = dch32; P.Bh64 = dBh64; P.Bh32 = dBh32;
+  P.sigG64 = dsigG64; P.rhoG64 = drhoG64; P.sigG32 = dsigG32; P.rhoG32 = drhoG32;
+  P.g64 = dg64; P.g32 = dg32; P.S1 = dS1; P.S2 = dS2;
+  return TSFDE_OK;
+}
+
+int tsfde_setup(tsfde_ctx** out, double alpha, double gamma, double l, double T, int64_t n,
+                int64_t M, double r, double soe_tol, const tsfde_opts* opts) {
+  if (!out) return TSFDE_EINVAL;
+  *out = nullptr;
+  tsfde_ctx* c = nullptr;
+  try {
+    c = new tsfde_ctx();
+    int st = setup_impl(c, alpha, gamma, l, T, n, M, r, soe_tol, opts);
+    if (st != TSFDE_OK) {
+      std::fprintf(stderr, "tsfde_setup: %s\n", c->err.c_str());
+      tsfde_destroy(c);
+      return st;
+    }
+  } catch (const std::bad_alloc&) {
+    tsfde_destroy(c);
+    return TSFDE_ENOMEM;
+  } catch (...) {
+    tsfde_destroy(c);
+    return TSFDE_EINVAL;
+  }
+  *out = c;
+  return TSFDE_OK;
+}
+
+int tsfde_set_problem(tsfde_ctx* c, const double* phi, const double* kappa0, const double* kappa1,
+                      const double* theta, int rank, const double* const* F, const double* G) {
+  if (!c) return TSFDE_EINVAL;
+  if (!phi || !kappa0) return fail(c, TSFDE_EINVAL, "phi and kappa0 are required");
+  if (kappa1 && !theta) return fail(c, TSFDE_EINVAL, "kappa1 needs theta");
+  if (rank < 0 || rank > 4) return fail(c, TSFDE_EINVAL, "source rank must be 0..4");
+  if (rank > 0 && (!F || !G)) return fail(c, TSFDE_EINVAL, "rank > 0 needs F and G");
+  const size_t nb = sizeof(double) * (size_t)c->n;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(c->phi, phi, nb, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(c->kap0, kappa0, nb, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "set_problem copy");
+  c->kap1 = kappa1 != nullptr;
+  if (kappa1 && (e = cudaMemcpyAsync(c->kap1d, kappa1, nb, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "set_problem copy");
+  c->theta.assign(c->M + 1, 0.0);
+  if (theta) c->theta.assign(theta, theta + c->M + 1);
+  c->rank = rank;
+  c->Gsrc.assign(4 * (c->M + 1), 0.0);
+  for (int q = 0; q < rank; ++q) {
+    if (!F[q]) return fail(c, TSFDE_EINVAL, "F[q] is NULL");
+    if ((e = cudaMemcpyAsync(c->F + (size_t)q * c->n, F[q], nb, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "set_problem copy");
+    for (int64_t m = 0; m <= c->M; ++m) c->Gsrc[q * (c->M + 1) + m] = G[q * (c->M + 1) + m];
+  }
+  c->have_problem = true;
+  return tsfde_reset(c);
+}
+
+int tsfde_reset(tsfde_ctx* c) {
+  if (!c) return TSFDE_EINVAL;
+  if (!c->have_problem) return fail(c, TSFDE_ESTATE, "no problem set");
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(c->u[0], c->phi, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "reset copy");
+  if ((e = cudaMemsetAsync(c->G, 0, sizeof(double) * (size_t)std::max(c->E, 1) * c->ld, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "reset memset");
+  c->m = 0;
+  return TSFDE_OK;
+}
+
+static LevelArgs level_args(tsfde_ctx* c, double ahat, const double* b, double* u, StepStat* st) {
+  LevelArgs A{};
+  A.P = c->P;
+  A.ahat = ahat;
+  A.b = b;
+  A.kappa64 = c->kappa64;
+  A.kappa32 = c->kappa32;
+  A.u = u;
+  A.precond = c->opts.precond == TSFDE_STRANG ? 1 : 0;
+  A.tol = c->opts.krylov_tol;
+  A.max_it = c->opts.max_it;
+  A.inner_tol = c->opts.inner_tol;
+  A.max_outer = c->opts.max_outer;
+  A.k64 = c->k64;
+  A.k32 = c->k32;
+  A.r64 = c->r64;
+  A.stat = st;
+  return A;
+}
+
+static cudaError_t record(tsfde_ctx* c) {
+  if (!c->opts.profile) return cudaSuccess;
+  cudaEvent_t e;
+  if (c->ev_free.empty()) {
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return err;
+  } else {
+    e = c->ev_free.back();
+    c->ev_free.pop_back();
+  }
+  c->ev_used.push_back(e);
+  return cudaEventRecord(e, c->stream);
+}
+
+// Enqueue level m = c->m + 1.
+static int enqueue_level(tsfde_ctx* c, const double* kappa_m, const double* f_m, double* rhs_out) {
+  const int64_t m = c->m + 1;
+  RhsArgs R{};
+  R.n = (int)c->n;
+  R.ld = c->ld;
+  R.Eact = (m >= 2) ? c->Eact[m] : 0;
+  R.ahat = c->ahat[m];
+  R.Gm = c->G;
+  R.eps = c->eps + m * c->E;
+  R.cw = c->cw + m * c->E;
+  R.u1 = c->u[(m - 1) % 3];
+  R.u2 = (m >= 2) ? c->u[(m - 2) % 3] : c->u[(m - 1) % 3];
+  R.kap_m = kappa_m;
+  R.kap0 = c->kap0;
+  R.kap1 = c->kap1 ? c->kap1d : nullptr;
+  R.theta = c->theta[m];
+  R.f_m = f_m;
+  R.F = c->F;
+  R.rank = c->rank;
+  for (int q = 0; q < 4; ++q) R.Gr[q] = (q < c->rank) ? c->Gsrc[q * (c->M + 1) + m] : 0.0;
+  R.b = c->b;
+  R.rhs_copy = rhs_out;
+  R.kappa64 = c->kappa64;
+  R.kappa32 = c->kappa32;
+  cudaError_t e = record(c);
+  if (e == cudaSuccess) e = launch_rhs(R, c->stream);
+  if (e == cudaSuccess) e = record(c);
+  if (e != cudaSuccess) return cuda_fail(c, e, "rhs kernel");
+  LevelArgs A = level_args(c, c->ahat[m], c->b, c->u[m % 3], c->stats + m);
+  e = launch_level(A, c->opts.precision == TSFDE_MIXED, c->stream);
+  if (e == cudaSuccess) e = record(c);
+  if (e != cudaSuccess) return cuda_fail(c, e, "level kernel");
+  c->m = m;
+  return TSFDE_OK;
+}
+
+int tsfde_step(tsfde_ctx* c, const double* kappa_m, const double* f_m, double* u_out, double* rhs_out,
+               tsfde_step_info* info) {
+  if (!c) return TSFDE_EINVAL;
+  if (!c->have_problem) return fail(c, TSFDE_ESTATE, "no problem set");
+  if (c->m >= c->M) return fail(c, TSFDE_ESTATE, "all levels already computed");
+  int st = enqueue_level(c, kappa_m, f_m, rhs_out);
+  if (st != TSFDE_OK) return st;
+  const int64_t m = c->m;
+  cudaError_t e;
+  if (u_out && (e = cudaMemcpyAsync(u_out, c->u[m % 3], sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "u copy");
+  if (info) {
+    StepStat s{};
+    if ((e = cudaMemcpyAsync(&s, c->stats + m, sizeof(s), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "step sync");
+    info->m = m;
+    info->status = s.status;
+    info->iterations = s.iterations;
+    info->outer = s.outer;
+    info->E_active = c->Eact[m];
+    info->rel_residual = s.rel_residual;
+    if (s.status != TSFDE_OK) return fail(c, s.status, std::string("level ") + std::to_string(m) + ": " + tsfde_strerror(s.status));
+  }
+  return TSFDE_OK;
+}
+
+int tsfde_solve(tsfde_ctx* c, double* u_final, double* u_all, tsfde_solve_info* info) {
+  if (!c) return TSFDE_EINVAL;
+  if (!c->have_problem) return fail(c, TSFDE_ESTATE, "no problem set");
+  const int64_t m0 = c->m;
+  const size_t nb = sizeof(double) * c->n;
+  cudaError_t e;
+  if (u_all && m0 == 0 && (e = cudaMemcpyAsync(u_all, c->u[0], nb, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "u copy");
+  while (c->m < c->M) {
+    int st = enqueue_level(c, nullptr, nullptr, nullptr);
+    if (st != TSFDE_OK) return st;
+    if (u_all && (e = cudaMemcpyAsync(u_all + c->m * c->n, c->u[c->m % 3], nb, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "u copy");
+  }
+  if (u_final && (e = cudaMemcpyAsync(u_final, c->u[c->m % 3], nb, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "u copy");
+  if (info) {
+    std::vector<StepStat> s(c->M + 1);
+    if ((e = cudaMemcpyAsync(s.data(), c->stats, sizeof(StepStat) * (c->M + 1), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "solve sync");
+    std::memset(info, 0, sizeof(*info));
+    info->E = c->E;
+    info->min_iterations = 1 << 30;
+    for (int64_t m = m0 + 1; m <= c->M; ++m) {
+      if (s[m].status != TSFDE_OK && info->status == TSFDE_OK) {
+        info->status = s[m].status;
+        info->failed_level = m;
+      }
+      info->iterations += s[m].iterations;
+      info->outer += s[m].outer;
+      info->min_iterations = std::min(info->min_iterations, s[m].iterations);
+      info->max_iterations = std::max(info->max_iterations, s[m].iterations);
+      info->max_rel_residual = std::max(info->max_rel_residual, s[m].rel_residual);
+      info->E_active_sum += c->Eact[m];
+    }
+    info->levels = c->M - m0;
+    if (info->levels == 0) info->min_iterations = 0;
+    if (info->status != TSFDE_OK)
+      return fail(c, info->status, std::string("level ") + std::to_string(info->failed_level) + ": " + tsfde_strerror(info->status));
+  }
+  return TSFDE_OK;
+}
+
+int tsfde_get_level_stats(tsfde_ctx* c, int64_t m0, int64_t m1, tsfde_step_info* out) {
+  if (!c || !out) return TSFDE_EINVAL;
+  if (m0 < 1 || m1 < m0 || m1 > c->m) return fail(c, TSFDE_EINVAL, "level range outside 1..current level");
+  std::vector<StepStat> s(m1 - m0 + 1);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(s.data(), c->stats + m0, sizeof(StepStat) * s.size(), cudaMemcpyDeviceToHost,
+                           c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "level stats");
+  for (size_t q = 0; q < s.size(); ++q) {
+    out[q].m = m0 + (int64_t)q;
+    out[q].status = s[q].status;
+    out[q].iterations = s[q].iterations;
+    out[q].outer = s[q].outer;
+    out[q].E_active = c->Eact[m0 + q];
+    out[q].rel_residual = s[q].rel_residual;
+  }
+  return TSFDE_OK;
+}
+
+int tsfde_get_solution(tsfde_ctx* c, double* u) {
+  if (!c || !u) return TSFDE_EINVAL;
+  if (!c->have_problem) return fail(c, TSFDE_ESTATE, "no problem set");
+  cudaError_t e = cudaMemcpyAsync(u, c->u[c->m % 3], sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "solution copy");
+  return TSFDE_OK;
+}
+
+int tsfde_get_timing(tsfde_ctx* c, tsfde_timing* out) {
+  if (!c || !out) return TSFDE_EINVAL;
+  if (!c->opts.profile) return fail(c, TSFDE_ESTATE, "profiling is off (opts.profile = 0)");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "timing sync");
+  std::memset(out, 0, sizeof(*out));
+  for (size_t q = 0; q + 2 < c->ev_used.size(); q += 3) {
+    float a = 0.f, b = 0.f;
+    if ((e = cudaEventElapsedTime(&a, c->ev_used[q], c->ev_used[q + 1])) != cudaSuccess ||
+        (e = cudaEventElapsedTime(&b, c->ev_used[q + 1], c->ev_used[q + 2])) != cudaSuccess)
+      return cuda_fail(c, e, "cudaEventElapsedTime");
+    out->rhs_ms += a;
+    out->level_ms += b;
+    out->levels += 1;
+  }
+  for (cudaEvent_t ev : c->ev_used) c->ev_free.push_back(ev);
+  c->ev_used.clear();
+  return TSFDE_OK;
+}
+
+int tsfde_get_soe(const tsfde_ctx* c, int* E, double* s, double* w) {
+  if (!c || !E) return TSFDE_EINVAL;
+  const int cap = *E;
+  *E = c->E;
+  if ((s || w) && cap < c->E) return TSFDE_EINVAL;
+  if (s) std::memcpy(s, c->soe_s.data(), sizeof(double) * c->E);
+  if (w) std::memcpy(w, c->soe_w.data(), sizeof(double) * c->E);
+  return TSFDE_OK;
+}
+
+int tsfde_get_times(const tsfde_ctx* c, double* t) {
+  if (!c || !t) return TSFDE_EINVAL;
+  std::memcpy(t, c->tmesh.data(), sizeof(double) * (c->M + 1));
+  return TSFDE_OK;
+}
+
+int tsfde_get_symbol(const tsfde_ctx* c, double* t) {
+  if (!c || !t) return TSFDE_EINVAL;
+  std::memcpy(t, c->symbol.data(), sizeof(double) * c->n);
+  return TSFDE_OK;
+}
+
+static int run_apply(tsfde_ctx* c, int kind, double a, double kbar, const double* kappa, const double* v,
+                     double* y, int precision) {
+  if (!c || !v || !y) return TSFDE_EINVAL;
+  if (precision != TSFDE_FP64 && precision != TSFDE_MIXED) return fail(c, TSFDE_EINVAL, "bad precision");
+  ApplyArgs A{};
+  A.P = c->P;
+  A.kind = kind;
+  A.a = a;
+  A.kbar = kbar;
+  A.kappa = kappa;
+  A.v = v;
+  A.y = y;
+  A.status = c->status;
+  cudaError_t e = launch_apply(A, precision == TSFDE_MIXED, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "apply kernel");
+  int st = 0;
+  if ((e = cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "apply sync");
+  if (st != TSFDE_OK) return fail(c, st, tsfde_strerror(st));
+  return TSFDE_OK;
+}
+
+int tsfde_toeplitz_apply(tsfde_ctx* c, const double* v, double* y, int precision) {
+  return run_apply(c, 0, 0.0, 0.0, nullptr, v, y, precision);
+}
+
+int tsfde_operator_apply(tsfde_ctx* c, double a, const double* kappa, const double* v, double* y, int precision) {
+  if (!kappa) return fail(c, TSFDE_EINVAL, "kappa is required");
+  return run_apply(c, 0, a, 0.0, kappa, v, y, precision);
+}
+
+int tsfde_precond_apply(tsfde_ctx* c, double a, double kbar, const double* v, double* z, int precision) {
+  if (!(a > 0.0) || !(kbar > 0.0)) return fail(c, TSFDE_EINVAL, "a and kbar must be positive");
+  return run_apply(c, 1, a, kbar, nullptr, v, z, precision);
+}
+
+int tsfde_linear_solve(tsfde_ctx* c, double a, const double* kappa, const double* b, double* x,
+                       tsfde_step_info* info) {
+  if (!c || !kappa || !b || !x) return TSFDE_EINVAL;
+  if (!(a > 0.0)) return fail(c, TSFDE_EINVAL, "a must be positive");
+  cudaError_t e = launch_convert(kappa, c->kappa64, c->kappa32, (int)c->n, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "convert kernel");
+  LevelArgs A = level_args(c, a, b, x, c->stats);
+  A.kappa64 = c->kappa64;
+  e = launch_level(A, c->opts.precision == TSFDE_MIXED, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "level kernel");
+  StepStat s{};
+  if ((e = cudaMemcpyAsync(&s, c->stats, sizeof(s), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "solve sync");
+  if (info) {
+    info->m = 0;
+    info->status = s.status;
+    info->iterations = s.iterations;
+    info->outer = s.outer;
+    info->E_active = 0;
+    info->rel_residual = s.rel_residual;
+  }
+  if (s.status != TSFDE_OK) return fail(c, s.status, tsfde_strerror(s.status));
+  return TSFDE_OK;
+}
+
+}  // extern "C"

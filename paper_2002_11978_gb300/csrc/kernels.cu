@@ -1,0 +1,805 @@
+// kernels.cu -- CUDA kernels of the FIDS hot path (sm_103a).
+//
+// Toeplitz and circulant products use a zero-padded real FFT of length L
+// (Sec. 4.1) computed as a complex FFT of length Nc = L/2 in three passes
+// (column FFTs, paired row FFTs with the spectral product in the middle,
+// inverse column FFTs).  The inverse column pass of one product and the
+// forward column pass of the next product share a CTA tile, so a product
+// that feeds another costs two grid barriers.  Grid barriers are bounded
+// (dev.cuh); every kernel returns a status instead of hanging or trapping.
+#include <cuda_runtime.h>
+
+#include "../../include/tsfde.h"
+#include "dev.cuh"
+#include "plan.h"
+
+namespace tsfde {
+
+constexpr int kThreads = 256;
+
+// partial-sum slots
+enum {
+  SL_BB = 0, SL_RV = 1, SL_TS = 2, SL_TT = 3, SL_RR0 = 4, SL_RR = 5,
+  SL_EMAX = 6, SL_XMAX = 7, SL_RES = 8, SL_KAP = 9
+};
+
+template <typename R> struct Smem {
+  cplx<R>* tw;  // W_T^k, k < T
+  cplx<R>* bA;  // work buffers (W complex each)
+  cplx<R>* bB;
+  double* red;  // 33 doubles
+};
+
+template <typename R> __device__ __forceinline__ const cplx<R>* twL(const DevPlan& P) {
+  if constexpr (sizeof(R) == 8) return P.twL64; else return P.twL32;
+}
+template <typename R> __device__ __forceinline__ int lgct(const Geo& g) {
+  if constexpr (sizeof(R) == 8) return g.lgct64; else return g.lgct32;
+}
+template <typename R> __device__ __forceinline__ const R* sigT(const DevPlan& P) {
+  if constexpr (sizeof(R) == 8) return P.sigT64; else return P.sigT32;
+}
+template <typename R> __device__ __forceinline__ const cplx<R>* rhoT(const DevPlan& P) {
+  if constexpr (sizeof(R) == 8) return P.rhoT64; else return P.rhoT32;
+}
+template <typename R> __device__ __forceinline__ R* sigG(const DevPlan& P) {
+  if constexpr (sizeof(R) == 8) return P.sigG64; else return P.sigG32;
+}
+template <typename R> __device__ __forceinline__ cplx<R>* rhoG(const DevPlan& P) {
+  if constexpr (sizeof(R) == 8) return P.rhoG64; else return P.rhoG32;
+}
+template <typename R> __device__ __forceinline__ const cplx<R>* chirp(const DevPlan& P) {
+  if constexpr (sizeof(R) == 8) return P.chirp64; else return P.chirp32;
+}
+template <typename R> __device__ __forceinline__ const cplx<R>* Bh(const DevPlan& P) {
+  if constexpr (sizeof(R) == 8) return P.Bh64; else return P.Bh32;
+}
+template <typename R> __device__ __forceinline__ R* gcol(const DevPlan& P) {
+  if constexpr (sizeof(R) == 8) return P.g64; else return P.g32;
+}
+
+// Shared memory: [tw64 T][tw32 T][bufA W][bufB W][red 64]
+size_t plan_smem_bytes(const DevPlan& P) {
+  return (size_t)P.T * sizeof(double2) + (size_t)P.T * sizeof(float2) +
+         2 * (size_t)P.W * sizeof(double2) + 64 * sizeof(double);
+}
+
+struct SmemAll {
+  Smem<double> d;
+  Smem<float> f;
+};
+
+__device__ SmemAll smem_setup(const DevPlan& P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  char* base = reinterpret_cast<char*>(smem_raw);
+  double2* tw64 = reinterpret_cast<double2*>(base);
+  float2* tw32 = reinterpret_cast<float2*>(base + (size_t)P.T * sizeof(double2));
+  char* wbase = base + (size_t)P.T * (sizeof(double2) + sizeof(float2));
+  double2* bA = reinterpret_cast<double2*>(wbase);
+  double2* bB = bA + P.W;
+  double* red = reinterpret_cast<double*>(bB + P.W);
+  const int stride = P.L / P.T;
+  for (int k = threadIdx.x; k < P.T; k += blockDim.x) {
+    tw64[k] = P.twL64[k * stride];
+    tw32[k] = P.twL32[k * stride];
+  }
+  __syncthreads();
+  SmemAll s;
+  s.d.tw = tw64; s.d.bA = bA; s.d.bB = bB; s.d.red = red;
+  s.f.tw = tw32; s.f.bA = reinterpret_cast<float2*>(bA); s.f.bB = reinterpret_cast<float2*>(bB);
+  s.f.red = red;
+  return s;
+}
+
+__device__ __forceinline__ void put_partial(const DevPlan& P, int slot, double v) {
+  if (threadIdx.x == 0) P.part[slot * P.G + blockIdx.x] = v;
+}
+__device__ __forceinline__ double get_sum(const DevPlan& P, int slot, double* red) {
+  return grid_reduce<false>(P.part + slot * P.G, P.G, red);
+}
+__device__ __forceinline__ double get_max(const DevPlan& P, int slot, double* red) {
+  return grid_reduce<true>(P.part + slot * P.G, P.G, red);
+}
+__device__ __forceinline__ bool gsync(const DevPlan& P) { return grid_sync(P.bar, P.timeout); }
+
+// ------------------------------------------------------------------ passes
+// Pass A, real input: x (length nin, zero beyond) -> z_j = x_{2j} + i x_{2j+1},
+// column FFTs over j1 (j = N2 j1 + j2), twiddle W_Nc^{j2 k1}, store
+// S1[k1*N2 + j2].  Without FULL only rows j1 < N1/2 can be non-zero
+// (nin <= L/2).
+template <typename R, bool FULL, class Pro>
+__device__ void passA_real(const DevPlan& P, const Smem<R>& sm, int nin, Pro& pro) {
+  typedef cplx<R> Z;
+  const Geo& g = P.gr;
+  const int lc = lgct<R>(g), ct = 1 << lc;
+  const int N1 = g.N1, N2 = g.N2;
+  const int ntiles = N2 >> lc;
+  const int rows = FULL ? N1 : (N1 >> 1);
+  const int tstride = P.L / g.Nfft;
+  Z* S1 = reinterpret_cast<Z*>(P.S1);
+  const Z* tw = twL<R>(P);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int c0 = tile << lc;
+    for (int e = threadIdx.x; e < (N1 << lc); e += blockDim.x) {
+      const int j1 = e >> lc, c = e & (ct - 1);
+      Z v = mkc<R>(R(0), R(0));
+      if (j1 < rows) {
+        const int i0 = 2 * (N2 * j1 + c0 + c);
+        const R x0 = (i0 < nin) ? pro(i0) : R(0);
+        const R x1 = (i0 + 1 < nin) ? pro(i0 + 1) : R(0);
+        v = mkc<R>(x0, x1);
+      }
+      sm.bA[e] = v;
+    }
+    __syncthreads();
+    const Z* res = fft_batch<R, false>(sm.bA, sm.bB, N1, lc, sm.tw, P.T);
+    for (int e = threadIdx.x; e < (N1 << lc); e += blockDim.x) {
+      const int k1 = e >> lc, c = e & (ct - 1);
+      const int j2 = c0 + c;
+      const int m = (j2 * k1) & (g.Nfft - 1);
+      S1[k1 * N2 + j2] = cmul(res[e], tw[m * tstride]);
+    }
+    __syncthreads();
+  }
+}
+
+// Pass A, complex input a_j (j < n, n <= L/2), geometry gc (Nfft = L).
+template <typename R, class Pro>
+__device__ void passA_cplx(const DevPlan& P, const Smem<R>& sm, Pro& pro) {
+  typedef cplx<R> Z;
+  const Geo& g = P.gc;
+  const int lc = lgct<R>(g), ct = 1 << lc;
+  const int N1 = g.N1, N2 = g.N2;
+  const int ntiles = N2 >> lc;
+  const int tstride = P.L / g.Nfft;
+  Z* S1 = reinterpret_cast<Z*>(P.S1);
+  const Z* tw = twL<R>(P);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int c0 = tile << lc;
+    for (int e = threadIdx.x; e < (N1 << lc); e += blockDim.x) {
+      const int j1 = e >> lc, c = e & (ct - 1);
+      const int j = N2 * j1 + c0 + c;
+      sm.bA[e] = (j1 < (N1 >> 1) && j < P.n) ? pro(j) : mkc<R>(R(0), R(0));
+    }
+    __syncthreads();
+    const Z* res = fft_batch<R, false>(sm.bA, sm.bB, N1, lc, sm.tw, P.T);
+    for (int e = threadIdx.x; e < (N1 << lc); e += blockDim.x) {
+      const int k1 = e >> lc, c = e & (ct - 1);
+      const int j2 = c0 + c;
+      const int m = (j2 * k1) & (g.Nfft - 1);
+      S1[k1 * N2 + j2] = cmul(res[e], tw[m * tstride]);
+    }
+    __syncthreads();
+  }
+}
+
+enum { MID_APPLY = 0, MID_SPEC = 1, MID_CONV = 2 };
+
+// Pass B: row FFTs (rows k1 and N1-k1 together), the spectral middle step,
+// inverse row FFTs, twiddle W^{-j2 k1}, store S2.
+//  MID_APPLY: real-input product with a real even spectrum (sigma, rho):
+//    E = (Z_k + conj Z_k')/2, O = -i (Z_k - conj Z_k')/2,
+//    E' = sigma E + rho O, O' = conj(rho) E + sigma O, Z'_k = E' + i O'.
+//  MID_SPEC: forward only; the real spectrum S of an even real sequence
+//    (S_k = Re(E + W_L^k O), S_k' = Re(E - W_L^k O)) stored as (sigma, rho).
+//  MID_CONV: complex product Z'_k = Z_k * conv_k (geometry gc).
+template <typename R, int MID>
+__device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__ sig,
+                      const cplx<R>* __restrict__ rho, R* sig_out, cplx<R>* rho_out,
+                      const cplx<R>* __restrict__ conv) {
+  typedef cplx<R> Z;
+  const Geo& g = (MID == MID_CONV) ? P.gc : P.gr;
+  const int N1 = g.N1, N2 = g.N2;
+  const int npairs = (N1 >> 1) + 1;
+  const int tstride = P.L / g.Nfft;
+  const Z* S1 = reinterpret_cast<const Z*>(P.S1);
+  Z* S2 = reinterpret_cast<Z*>(P.S2);
+  const Z* tw = twL<R>(P);
+  const R invNc = R(1.0) / R(P.Nc);
+  for (int it = blockIdx.x; it < npairs; it += gridDim.x) {
+    const int ka = it;
+    const int kb = (it == 0 || it == (N1 >> 1)) ? -1 : N1 - it;
+    const int lgB = (kb < 0) ? 0 : 1;
+    const int B = 1 << lgB;
+    for (int e = threadIdx.x; e < (N2 << lgB); e += blockDim.x) {
+      const int b = e & (B - 1), k2 = e >> lgB;
+      const int row = b ? kb : ka;
+      sm.bA[e] = __ldcg(S1 + row * N2 + k2);
+    }
+    __syncthreads();
+    Z* res = fft_batch<R, false>(sm.bA, sm.bB, N2, lgB, sm.tw, P.T);
+    Z* oth = (res == sm.bA) ? sm.bB : sm.bA;
+    for (int e = threadIdx.x; e < (N2 << lgB); e += blockDim.x) {
+      const int b = e & (B - 1), k2 = e >> lgB;
+      const int k1 = b ? kb : ka;
+      const Z Zk = res[e];
+      if constexpr (MID == MID_CONV) {
+        oth[e] = cmul(Zk, conv[k1 * N2 + k2]);
+      } else {
+        const int q2 = (k1 == 0) ? ((N2 - k2) & (N2 - 1)) : (N2 - 1 - k2);
+        const int qb = (B == 1) ? 0 : 1 - b;
+        const Z Zq = res[(q2 << lgB) + qb];
+        const Z E = mkc<R>(R(0.5) * (Zk.x + Zq.x), R(0.5) * (Zk.y - Zq.y));
+        const Z O = mkc<R>(R(0.5) * (Zk.y + Zq.y), R(-0.5) * (Zk.x - Zq.x));
+        if constexpr (MID == MID_APPLY) {
+          const R s = sig[k1 * N2 + k2];
+          const Z r = rho[k1 * N2 + k2];
+          const Z Ep = cadd(cscale(E, s), cmul(r, O));
+          const Z Op = cadd(cmul(cconj(r), E), cscale(O, s));
+          oth[e] = mkc<R>(Ep.x - Op.y, Ep.y + Op.x);
+        } else {
+          const int k = k1 + N1 * k2;
+          const Z Wk = tw[k];  // W_L^k (L = 2 Nc)
+          const R wo = Wk.x * O.x - Wk.y * O.y;  // Re(W O)
+          sig_out[k1 * N2 + k2] = E.x * invNc;
+          rho_out[k1 * N2 + k2] = cscale(Wk, wo * invNc);
+        }
+      }
+    }
+    __syncthreads();
+    if constexpr (MID == MID_SPEC) continue;
+    const Z* res2 = fft_batch<R, true>(oth, res, N2, lgB, sm.tw, P.T);
+    for (int e = threadIdx.x; e < (N2 << lgB); e += blockDim.x) {
+      const int b = e & (B - 1), j2 = e >> lgB;
+      const int k1 = b ? kb : ka;
+      const int m = (j2 * k1) & (g.Nfft - 1);
+      S2[k1 * N2 + j2] = cmulc(res2[e], tw[m * tstride]);
+    }
+    __syncthreads();
+  }
+}
+
+// Pass C (+ optional fused pass A): inverse column FFTs, y_{2j} = Re z_j,
+// y_{2j+1} = Im z_j for j1 < N1/2.  epi(i, y_i) consumes each output and
+// returns the next product's input x_i (used only with DO_A).
+template <typename R, bool DO_A, class Epi>
+__device__ void passCA_real(const DevPlan& P, const Smem<R>& sm, Epi& epi) {
+  typedef cplx<R> Z;
+  const Geo& g = P.gr;
+  const int lc = lgct<R>(g), ct = 1 << lc;
+  const int N1 = g.N1, N2 = g.N2, n = P.n;
+  const int ntiles = N2 >> lc;
+  const int tstride = P.L / g.Nfft;
+  const Z* S2 = reinterpret_cast<const Z*>(P.S2);
+  Z* S1 = reinterpret_cast<Z*>(P.S1);
+  const Z* tw = twL<R>(P);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int c0 = tile << lc;
+    for (int e = threadIdx.x; e < (N1 << lc); e += blockDim.x) {
+      const int k1 = e >> lc, c = e & (ct - 1);
+      sm.bA[e] = __ldcg(S2 + k1 * N2 + c0 + c);
+    }
+    __syncthreads();
+    Z* res = fft_batch<R, true>(sm.bA, sm.bB, N1, lc, sm.tw, P.T);
+    Z* oth = (res == sm.bA) ? sm.bB : sm.bA;
+    for (int e = threadIdx.x; e < (N1 << lc); e += blockDim.x) {
+      const int j1 = e >> lc, c = e & (ct - 1);
+      if (j1 < (N1 >> 1)) {
+        const int i0 = 2 * (N2 * j1 + c0 + c);
+        const Z v = res[e];
+        R x0 = R(0), x1 = R(0);
+        if (i0 < n) x0 = epi(i0, v.x);
+        if (i0 + 1 < n) x1 = epi(i0 + 1, v.y);
+        if (DO_A) oth[e] = mkc<R>(x0, x1);
+      } else if (DO_A) {
+        oth[e] = mkc<R>(R(0), R(0));
+      }
+    }
+    __syncthreads();
+    if constexpr (DO_A) {
+      const Z* res2 = fft_batch<R, false>(oth, res, N1, lc, sm.tw, P.T);
+      for (int e = threadIdx.x; e < (N1 << lc); e += blockDim.x) {
+        const int k1 = e >> lc, c = e & (ct - 1);
+        const int j2 = c0 + c;
+        const int m = (j2 * k1) & (g.Nfft - 1);
+        S1[k1 * N2 + j2] = cmul(res2[e], tw[m * tstride]);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Pass C, complex output z_j for j < n (geometry gc).
+template <typename R, class Epi>
+__device__ void passC_cplx(const DevPlan& P, const Smem<R>& sm, Epi& epi) {
+  typedef cplx<R> Z;
+  const Geo& g = P.gc;
+  const int lc = lgct<R>(g), ct = 1 << lc;
+  const int N1 = g.N1, N2 = g.N2;
+  const int ntiles = N2 >> lc;
+  const Z* S2 = reinterpret_cast<const Z*>(P.S2);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int c0 = tile << lc;
+    for (int e = threadIdx.x; e < (N1 << lc); e += blockDim.x) {
+      const int k1 = e >> lc, c = e & (ct - 1);
+      sm.bA[e] = __ldcg(S2 + k1 * N2 + c0 + c);
+    }
+    __syncthreads();
+    const Z* res = fft_batch<R, true>(sm.bA, sm.bB, N1, lc, sm.tw, P.T);
+    for (int e = threadIdx.x; e < (N1 << lc); e += blockDim.x) {
+      const int j1 = e >> lc, c = e & (ct - 1);
+      const int j = N2 * j1 + c0 + c;
+      if (j1 < (N1 >> 1) && j < P.n) epi(j, res[e]);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------- preconditioner
+// P = ahat I + kbar s(A) (Eq. (4.3)) is circulant of size n with eigenvalues
+// d_k = ahat + kbar lambda_k.  Its inverse is the symmetric circulant with
+// first column g = IDFT_n(1/d), computed by a Bluestein chirp-z transform
+// on length-L FFTs; P^{-1} v is then the symmetric Toeplitz product with
+// first column g, i.e. the same zero-padded product as A with the spectrum
+// of the even embedding of g (built here as (sigma, rho) tables).
+template <typename R>
+__device__ bool build_precond(const DevPlan& P, const Smem<R>& sm, double ahat, double kbar) {
+  typedef cplx<R> Z;
+  const double* lam = P.lam;
+  const Z* ch = chirp<R>(P);
+  auto pro = [&](int j) -> Z {
+    const R q = (R)(1.0 / (ahat + kbar * lam[j]));
+    return cscale(ch[j], q);
+  };
+  passA_cplx<R>(P, sm, pro);
+  if (!gsync(P)) return false;
+  passB<R, MID_CONV>(P, sm, nullptr, nullptr, nullptr, nullptr, Bh<R>(P));
+  if (!gsync(P)) return false;
+  R* gv = gcol<R>(P);
+  const R invn = R(1.0 / (double)P.n);
+  auto epi = [&](int j, Z z) { gv[j] = (ch[j].x * z.x - ch[j].y * z.y) * invn; };
+  passC_cplx<R>(P, sm, epi);
+  if (!gsync(P)) return false;
+  const int n = P.n, L = P.L;
+  auto proE = [&](int i) -> R {
+    if (i < n) return gv[i];
+    const int k = L - i;
+    return (k < n) ? gv[k] : R(0);
+  };
+  passA_real<R, true>(P, sm, L, proE);
+  if (!gsync(P)) return false;
+  passB<R, MID_SPEC>(P, sm, nullptr, nullptr, sigG<R>(P), rhoG<R>(P), nullptr);
+  return gsync(P);
+}
+
+// ------------------------------------------------------------- PBiCGSTAB
+struct SolveRes {
+  int status;
+  int iters;
+  double relres;
+};
+
+// Right-preconditioned BiCGSTAB (van der Vorst) for (ahat I + K A) x = b,
+// x0 = 0, stop when ||r_k||_2 / ||b||_2 < tol (Sec. 5).  binit(i) gives b_i.
+// Per iteration: P^{-1}p, A p^, P^{-1}s, A s^ as zero-padded FFT products.
+template <typename R, class BInit>
+__device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>& V,
+                             const R* __restrict__ kap, double ahat, bool prec, double tol,
+                             int max_it, BInit& binit) {
+  const int n = P.n;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gstr = gridDim.x * blockDim.x;
+  const R a = (R)ahat;
+  SolveRes out{TSFDE_OK, 0, 0.0};
+  {
+    R acc = 0;
+    for (int i = gtid; i < n; i += gstr) {
+      const R bi = binit(i);
+      V.x[i] = R(0); V.r[i] = bi; V.rh[i] = bi; V.p[i] = R(0); V.v[i] = R(0);
+      acc += bi * bi;
+    }
+    put_partial(P, SL_BB, block_sum((double)acc, sm.red));
+  }
+  if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
+  const double bb = get_sum(P, SL_BB, sm.red);
+  if (!isfinite(bb)) { out.status = TSFDE_ENONFINITE; return out; }
+  if (bb == 0.0) return out;
+  const double nb = sqrt(bb);
+  double rho = 1.0, alpha = 1.0, omega = 1.0, rho_new = bb, rr = bb;
+  int it = 0;
+  for (;;) {
+    const double relres = sqrt(rr) / nb;
+    out.relres = relres;
+    out.iters = it;
+    if (!isfinite(relres) || !isfinite(rho_new)) { out.status = TSFDE_ENONFINITE; return out; }
+    if (relres < tol) return out;
+    if (it >= max_it) { out.status = TSFDE_ENOCONV; return out; }
+    if (rho_new == 0.0 || omega == 0.0) { out.status = TSFDE_EBREAKDOWN; return out; }
+    const double beta = (rho_new / rho) * (alpha / omega);
+    rho = rho_new;
+    ++it;
+    // p = r + beta (p - omega v)
+    {
+      const R bR = (R)beta, oR = (R)omega;
+      auto pro = [&](int i) -> R {
+        const R pi = V.r[i] + bR * (V.p[i] - oR * V.v[i]);
+        V.p[i] = pi;
+        return pi;
+      };
+      passA_real<R, false>(P, sm, n, pro);
+    }
+    if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
+    if (prec) {
+      passB<R, MID_APPLY>(P, sm, sigG<R>(P), rhoG<R>(P), nullptr, nullptr, nullptr);
+      if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
+      auto epi = [&](int i, R y) -> R { V.ph[i] = y; return y; };
+      passCA_real<R, true>(P, sm, epi);
+      if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
+    }
+    passB<R, MID_APPLY>(P, sm, sigT<R>(P), rhoT<R>(P), nullptr, nullptr, nullptr);
+    if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
+    const R* ph = prec ? V.ph : V.p;
+    {
+      R acc = 0;
+      auto epi = [&](int i, R y) -> R {
+        const R vi = a * ph[i] + kap[i] * y;
+        V.v[i] = vi;
+        acc += V.rh[i] * vi;
+        return R(0);
+      };
+      passCA_real<R, false>(P, sm, epi);
+      put_partial(P, SL_RV, block_sum((double)acc, sm.red));
+    }
+    if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
+    const double rv = get_sum(P, SL_RV, sm.red);
+    if (!isfinite(rv)) { out.status = TSFDE_ENONFINITE; return out; }
+    if (rv == 0.0) { out.status = TSFDE_EBREAKDOWN; return out; }
+    alpha = rho / rv;
+    // s = r - alpha v
+    {
+      const R aR = (R)alpha;
+      auto pro = [&](int i) -> R {
+        const R si = V.r[i] - aR * V.v[i];
+        V.s[i] = si;
+        return si;
+      };
+      passA_real<R, false>(P, sm, n, pro);
+    }
+    if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
+    if (prec) {
+      passB<R, MID_APPLY>(P, sm, sigG<R>(P), rhoG<R>(P), nullptr, nullptr, nullptr);
+      if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
+      auto epi = [&](int i, R y) -> R { V.sh[i] = y; return y; };
+      passCA_real<R, true>(P, sm, epi);
+      if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
+    }
+    passB<R, MID_APPLY>(P, sm, sigT<R>(P), rhoT<R>(P), nullptr, nullptr, nullptr);
+    if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
+    const R* sh = prec ? V.sh : V.s;
+    {
+      R ats = 0, att = 0;
+      auto epi = [&](int i, R y) -> R {
+        const R ti = a * sh[i] + kap[i] * y;
+        V.t[i] = ti;
+        ats += ti * V.s[i];
+        att += ti * ti;
+        return R(0);
+      };
+      passCA_real<R, false>(P, sm, epi);
+      put_partial(P, SL_TS, block_sum((double)ats, sm.red));
+      put_partial(P, SL_TT, block_sum((double)att, sm.red));
+    }
+    if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
+    const double ts = get_sum(P, SL_TS, sm.red);
+    const double tt = get_sum(P, SL_TT, sm.red);
+    omega = (tt > 0.0) ? ts / tt : 0.0;
+    if (!isfinite(omega)) { out.status = TSFDE_ENONFINITE; return out; }
+    // x += alpha p^ + omega s^, r = s - omega t
+    {
+      const R aR = (R)alpha, oR = (R)omega;
+      R arr = 0, ar2 = 0;
+      for (int i = gtid; i < n; i += gstr) {
+        V.x[i] = V.x[i] + aR * ph[i] + oR * sh[i];
+        const R ri = V.s[i] - oR * V.t[i];
+        V.r[i] = ri;
+        arr += V.rh[i] * ri;
+        ar2 += ri * ri;
+      }
+      put_partial(P, SL_RR0, block_sum((double)arr, sm.red));
+      put_partial(P, SL_RR, block_sum((double)ar2, sm.red));
+    }
+    if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
+    rho_new = get_sum(P, SL_RR0, sm.red);
+    rr = get_sum(P, SL_RR, sm.red);
+  }
+}
+
+__device__ double mean_kappa(const DevPlan& P, const double* kap, double* red) {
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gstr = gridDim.x * blockDim.x;
+  double acc = 0.0;
+  for (int i = gtid; i < P.n; i += gstr) acc += kap[i];
+  put_partial(P, SL_KAP, block_sum(acc, red));
+  if (!gsync(P)) return -1.0;
+  return get_sum(P, SL_KAP, red) / (double)P.n;
+}
+
+__device__ void write_stat(StepStat* st, int status, int iters, int outer, double relres) {
+  if (st && blockIdx.x == 0 && threadIdx.x == 0) {
+    st->status = status;
+    st->iterations = iters;
+    st->outer = outer;
+    st->rel_residual = relres;
+  }
+}
+
+// ---------------------------------------------------------- level kernels
+// FP64 level solve: preconditioner build and PBiCGSTAB, all in FP64.
+__global__ void __launch_bounds__(kThreads) k_level64(LevelArgs A) {
+  const DevPlan& P = A.P;
+  SmemAll S = smem_setup(P);
+  const double kbar = mean_kappa(P, A.kappa64, S.d.red);
+  if (kbar < 0.0) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
+  if (A.precond && !build_precond<double>(P, S.d, A.ahat, kbar)) {
+    write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0);
+    return;
+  }
+  KVecs<double> V = A.k64;
+  V.x = A.u;
+  auto binit = [&](int i) -> double { return A.b[i]; };
+  SolveRes r = bicgstab<double>(P, S.d, V, A.kappa64, A.ahat, A.precond != 0, A.tol, A.max_it, binit);
+  write_stat(A.stat, r.status, r.iters, 0, r.relres);
+}
+
+// Mixed level solve: FP64 defect correction u += e around an FP32
+// PBiCGSTAB for (ahat I + K A) e = r; the FP64 residual r = b - M u uses the
+// FP64 product; FP32 for the inner products and the preconditioner.
+// Stops when the last correction satisfies max|e| <= tol max|u|.
+__global__ void __launch_bounds__(kThreads) k_level_mixed(LevelArgs A) {
+  const DevPlan& P = A.P;
+  SmemAll S = smem_setup(P);
+  const int n = P.n;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gstr = gridDim.x * blockDim.x;
+  const double kbar = mean_kappa(P, A.kappa64, S.d.red);
+  if (kbar < 0.0) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
+  if (A.precond && !build_precond<float>(P, S.f, A.ahat, kbar)) {
+    write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0);
+    return;
+  }
+  {
+    double acc = 0.0;
+    for (int i = gtid; i < n; i += gstr) {
+      const double bi = A.b[i];
+      A.u[i] = 0.0;
+      A.r64[i] = bi;
+      acc += bi * bi;
+    }
+    put_partial(P, SL_RES, block_sum(acc, S.d.red));
+  }
+  if (!gsync(P)) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
+  const double bb = get_sum(P, SL_RES, S.d.red);
+  if (!isfinite(bb)) { write_stat(A.stat, TSFDE_ENONFINITE, 0, 0, 0.0); return; }
+  if (bb == 0.0) { write_stat(A.stat, TSFDE_OK, 0, 0, 0.0); return; }
+  const double nb = sqrt(bb);
+  double nr = nb, relres = 1.0;
+  int inner_total = 0, outer = 0, status = TSFDE_OK;
+  for (;;) {
+    if (outer >= A.max_outer) { status = TSFDE_ENOCONV; break; }
+    const double sc = 1.0 / nr;
+    auto binit = [&](int i) -> float { return (float)(A.r64[i] * sc); };
+    SolveRes ir = bicgstab<float>(P, S.f, A.k32, A.kappa32, A.ahat, A.precond != 0,
+                                  A.inner_tol, A.max_it, binit);
+    inner_total += ir.iters;
+    if (ir.status == TSFDE_ETIMEOUT) { status = ir.status; break; }
+    ++outer;
+    // u += nr * e, then r = b - (ahat u + kappa .* A u) in FP64
+    {
+      double emax = 0.0, xmax = 0.0;
+      const float* e = A.k32.x;
+      auto pro = [&](int i) -> double {
+        const double ei = nr * (double)e[i];
+        const double xi = A.u[i] + ei;
+        A.u[i] = xi;
+        emax = fmax(emax, fabs(ei));
+        xmax = fmax(xmax, fabs(xi));
+        return xi;
+      };
+      passA_real<double, false>(P, S.d, n, pro);
+      put_partial(P, SL_EMAX, block_max(emax, S.d.red));
+      put_partial(P, SL_XMAX, block_max(xmax, S.d.red));
+    }
+    if (!gsync(P)) { status = TSFDE_ETIMEOUT; break; }
+    const double emax = get_max(P, SL_EMAX, S.d.red);
+    const double xmax = get_max(P, SL_XMAX, S.d.red);
+    if (!isfinite(emax) || !isfinite(xmax)) { status = TSFDE_ENONFINITE; break; }
+    if (emax <= A.tol * xmax) break;
+    passB<double, MID_APPLY>(P, S.d, P.sigT64, P.rhoT64, nullptr, nullptr, nullptr);
+    if (!gsync(P)) { status = TSFDE_ETIMEOUT; break; }
+    {
+      double acc = 0.0;
+      const double ah = A.ahat;
+      auto epi = [&](int i, double y) -> double {
+        const double ri = A.b[i] - ah * A.u[i] - A.kappa64[i] * y;
+        A.r64[i] = ri;
+        acc += ri * ri;
+        return 0.0;
+      };
+      passCA_real<double, false>(P, S.d, epi);
+      put_partial(P, SL_RES, block_sum(acc, S.d.red));
+    }
+    if (!gsync(P)) { status = TSFDE_ETIMEOUT; break; }
+    nr = sqrt(get_sum(P, SL_RES, S.d.red));
+    relres = nr / nb;
+    if (!isfinite(nr)) { status = TSFDE_ENONFINITE; break; }
+    if (nr == 0.0) break;
+  }
+  write_stat(A.stat, status, inner_total, outer, relres);
+}
+
+// ------------------------------------------------------ single products
+template <typename R>
+__device__ void apply_kernel_body(const ApplyArgs& A, const Smem<R>& sm) {
+  const DevPlan& P = A.P;
+  const int n = P.n;
+  if (A.kind == 1) {
+    if (!build_precond<R>(P, sm, A.a, A.kbar)) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) *A.status = TSFDE_ETIMEOUT;
+      return;
+    }
+  }
+  auto pro = [&](int i) -> R { return (R)A.v[i]; };
+  passA_real<R, false>(P, sm, n, pro);
+  if (!gsync(P)) goto fail;
+  if (A.kind == 1)
+    passB<R, MID_APPLY>(P, sm, sigG<R>(P), rhoG<R>(P), nullptr, nullptr, nullptr);
+  else
+    passB<R, MID_APPLY>(P, sm, sigT<R>(P), rhoT<R>(P), nullptr, nullptr, nullptr);
+  if (!gsync(P)) goto fail;
+  {
+    auto epi = [&](int i, R y) -> R {
+      double yi = (double)y;
+      if (A.kind == 0) yi = A.a * A.v[i] + (A.kappa ? A.kappa[i] : 1.0) * yi;
+      A.y[i] = yi;
+      return R(0);
+    };
+    passCA_real<R, false>(P, sm, epi);
+  }
+  if (!gsync(P)) goto fail;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *A.status = TSFDE_OK;
+  return;
+fail:
+  if (blockIdx.x == 0 && threadIdx.x == 0) *A.status = TSFDE_ETIMEOUT;
+}
+
+__global__ void __launch_bounds__(kThreads) k_apply64(ApplyArgs A) {
+  SmemAll S = smem_setup(A.P);
+  apply_kernel_body<double>(A, S.d);
+}
+__global__ void __launch_bounds__(kThreads) k_apply32(ApplyArgs A) {
+  SmemAll S = smem_setup(A.P);
+  apply_kernel_body<float>(A, S.f);
+}
+
+// ------------------------------------------------- SOE history and RHS
+// G_j <- e^{-s_j tau_m} (G_j + c_j d), d = u^{m-1} - u^{m-2}, for the active
+// exponentials (G_j = w_j H_j / Gamma(1-gamma), c_j = w_j beta_{j,m-1} /
+// Gamma(1-gamma)); b = ahat u^{m-1} - sum_j G_j + f^m (Eq. (3.16gu) with the
+// history sum written through the SOE recurrence).  Also materialises
+// kappa^m in FP64 and FP32.
+__global__ void __launch_bounds__(kThreads) k_rhs(RhsArgs a) {
+  extern __shared__ double sh[];
+  double* s_eps = sh;
+  double* s_cw = sh + a.Eact;
+  for (int j = threadIdx.x; j < a.Eact; j += blockDim.x) {
+    s_eps[j] = a.eps[j];
+    s_cw[j] = a.cw[j];
+  }
+  __syncthreads();
+  const int gstr = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gstr) {
+    const double u1 = a.u1[i];
+    double acc = 0.0;
+    if (a.Eact > 0) {
+      const double d = u1 - a.u2[i];
+      double* Gi = a.Gm + i;
+      const size_t ld = (size_t)a.ld;
+      int j = 0;
+      for (; j + 4 <= a.Eact; j += 4) {
+        double g0 = Gi[(j + 0) * ld], g1 = Gi[(j + 1) * ld];
+        double g2 = Gi[(j + 2) * ld], g3 = Gi[(j + 3) * ld];
+        g0 = s_eps[j + 0] * fma(s_cw[j + 0], d, g0);
+        g1 = s_eps[j + 1] * fma(s_cw[j + 1], d, g1);
+        g2 = s_eps[j + 2] * fma(s_cw[j + 2], d, g2);
+        g3 = s_eps[j + 3] * fma(s_cw[j + 3], d, g3);
+        Gi[(j + 0) * ld] = g0; Gi[(j + 1) * ld] = g1;
+        Gi[(j + 2) * ld] = g2; Gi[(j + 3) * ld] = g3;
+        acc += g0; acc += g1; acc += g2; acc += g3;
+      }
+      for (; j < a.Eact; ++j) {
+        double g0 = Gi[j * ld];
+        g0 = s_eps[j] * fma(s_cw[j], d, g0);
+        Gi[j * ld] = g0;
+        acc += g0;
+      }
+    }
+    double f;
+    if (a.f_m) {
+      f = a.f_m[i];
+    } else {
+      f = 0.0;
+      for (int q = 0; q < a.rank; ++q) f += a.Gr[q] * a.F[(size_t)q * a.n + i];
+    }
+    const double bi = a.ahat * u1 - acc + f;
+    a.b[i] = bi;
+    if (a.rhs_copy) a.rhs_copy[i] = bi;
+    double k;
+    if (a.kap_m) k = a.kap_m[i];
+    else k = a.kap0[i] + (a.kap1 ? a.theta * a.kap1[i] : 0.0);
+    a.kappa64[i] = k;
+    a.kappa32[i] = (float)k;
+  }
+}
+
+__global__ void k_convert(const double* in, double* o64, float* o32, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double v = in[i];
+    o64[i] = v;
+    o32[i] = (float)v;
+  }
+}
+
+// ------------------------------------------------------------- launchers
+// The dynamic shared-memory limit of the cooperative kernels only ever grows,
+// so a context set up earlier with a larger plan can still launch.
+static size_t g_smem_limit = 0;
+
+static cudaError_t set_attrs(size_t smem) {
+  cudaError_t e = cudaSuccess;
+  if (smem <= g_smem_limit) return e;
+  const void* ks[] = {(const void*)k_level64, (const void*)k_level_mixed, (const void*)k_apply64,
+                      (const void*)k_apply32};
+  for (const void* k : ks) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  g_smem_limit = smem;
+  return e;
+}
+
+int coop_blocks_per_sm(size_t smem) {
+  if (set_attrs(smem) != cudaSuccess) return 0;
+  int best = 1 << 30;
+  const void* ks[] = {(const void*)k_level64, (const void*)k_level_mixed, (const void*)k_apply64,
+                      (const void*)k_apply32};
+  for (const void* k : ks) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, smem) != cudaSuccess) return 0;
+    best = nb < best ? nb : best;
+  }
+  return best;
+}
+
+cudaError_t launch_rhs(const RhsArgs& a, cudaStream_t s) {
+  int grid = (a.n + kThreads - 1) / kThreads;
+  if (grid < 1) grid = 1;
+  size_t smem = 2 * (size_t)(a.Eact > 0 ? a.Eact : 1) * sizeof(double);
+  k_rhs<<<grid, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const double* in, double* o64, float* o32, int n, cudaStream_t s) {
+  int grid = (n + kThreads - 1) / kThreads;
+  k_convert<<<grid < 1 ? 1 : grid, kThreads, 0, s>>>(in, o64, o32, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_level(const LevelArgs& a, int mixed, cudaStream_t s) {
+  size_t smem = plan_smem_bytes(a.P);
+  cudaError_t e = cudaMemsetAsync(a.P.bar, 0, sizeof(GridBarrier), s);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&a};
+  return cudaLaunchCooperativeKernel(mixed ? (const void*)k_level_mixed : (const void*)k_level64,
+                                     dim3(a.P.G), dim3(kThreads), args, smem, s);
+}
+
+cudaError_t launch_apply(const ApplyArgs& a, int fp32, cudaStream_t s) {
+  size_t smem = plan_smem_bytes(a.P);
+  cudaError_t e = cudaMemsetAsync(a.P.bar, 0, sizeof(GridBarrier), s);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&a};
+  return cudaLaunchCooperativeKernel(fp32 ? (const void*)k_apply32 : (const void*)k_apply64,
+                                     dim3(a.P.G), dim3(kThreads), args, smem, s);
+}
+
+}  // namespace tsfde

@@ -1,0 +1,136 @@
+// plan.h -- plain-data structures shared by the host launcher code and the
+// CUDA kernels (no CUDA-only types beyond vector types).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tsfde {
+
+// Bounded grid barrier state (cleared by the host before each cooperative
+// launch); see grid_sync in dev.cuh.
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+  int err;
+  int pad;
+};
+
+// One factorisation Nfft = N1 * N2 of a power-of-two transform, driven by
+// three passes: column FFTs of length N1 over tiles of 2^lgct columns,
+// row FFTs of length N2 (rows k1 and N1-k1 together), column inverse FFTs.
+struct Geo {
+  int Nfft, N1, N2, lgN1, lgN2;
+  int lgct64, lgct32;  // log2 columns per tile for double / float data
+};
+
+// Everything a cooperative kernel needs to run the FIDS level solve.
+struct DevPlan {
+  int n;       // unknowns
+  int L;       // circulant embedding length (power of two, >= 2n-1, >= 8)
+  int Nc;      // L/2: complex size of the real-input transforms
+  Geo gr;      // real-mode geometry, Nfft = Nc
+  Geo gc;      // complex-mode geometry (Bluestein), Nfft = L
+  int T;       // shared twiddle table size (>= every sub-FFT length)
+  int W;       // work-buffer capacity per buffer, in double2 elements
+  int G;       // CTAs of the cooperative grid
+  long long timeout;  // barrier wait budget (SM cycles)
+  GridBarrier* bar;
+  double* part;       // [kSlots][G] per-CTA partial sums
+  const double2* twL64;  // W_L^k, k < L
+  const float2* twL32;
+  // Toeplitz symbol spectrum, (k1,k2) layout of gr: sigma = (S_k+S_k')/(2Nc),
+  // rho = (S_k - S_k') W_L^k/(2Nc), k = k1 + N1 k2, k' = Nc - k
+  const double* sigT64; const double2* rhoT64;
+  const float* sigT32;  const float2* rhoT32;
+  const double* lam;       // Strang eigenvalues (n)
+  const double2* chirp64;  // e^{+pi i j^2/n}, j < n
+  const float2* chirp32;
+  const double2* Bh64;     // spectrum of the Bluestein kernel / L, (k1,k2) layout of gc
+  const float2* Bh32;
+  // per-level preconditioner spectrum (written by the build)
+  double* sigG64; double2* rhoG64;
+  float* sigG32;  float2* rhoG32;
+  double* g64; float* g32;  // first column of the circulant inverse (n)
+  double2* S1;  // work: Nfft complex (double capacity, reused as float2)
+  double2* S2;
+};
+
+enum { kSlots = 12 };
+
+struct StepStat {
+  int status;
+  int iterations;
+  int outer;
+  int E_active;
+  double rel_residual;
+};
+
+// Krylov workspace of one precision.
+template <typename R> struct KVecs {
+  R *x, *r, *rh, *p, *v, *s, *t, *ph, *sh;
+};
+
+struct LevelArgs {
+  DevPlan P;
+  double ahat;        // a_m / Gamma(1-gamma)
+  const double* b;    // right-hand side (n)
+  const double* kappa64;  // kappa^m (n)
+  const float* kappa32;
+  double* u;          // solution (n)
+  int precond;        // 1 = Strang
+  double tol;         // FP64: recursive residual tol; mixed: correction tol
+  int max_it;
+  double inner_tol;
+  int max_outer;
+  KVecs<double> k64;
+  KVecs<float> k32;
+  double* r64;        // mixed: FP64 residual
+  StepStat* stat;
+};
+
+struct RhsArgs {
+  int n, ld, Eact;
+  double ahat;
+  double* Gm;              // E x ld scaled history w_j H_j / Gamma(1-gamma)
+  const double* eps;       // e^{-s_j tau_m}, Eact entries
+  const double* cw;        // w_j beta_{j,m-1} / Gamma(1-gamma)
+  const double* u1;        // u^{m-1}
+  const double* u2;        // u^{m-2}
+  const double* kap_m;     // explicit kappa^m or NULL
+  const double* kap0;
+  const double* kap1;      // NULL if kappa has no time factor
+  double theta;
+  const double* f_m;       // explicit f^m or NULL
+  const double* F;         // rank x n source factors
+  int rank;
+  double Gr[4];
+  double* b;
+  double* rhs_copy;        // NULL or user buffer
+  double* kappa64;
+  float* kappa32;
+};
+
+struct ApplyArgs {
+  DevPlan P;
+  int kind;         // 0: y = a v + kappa .* (A v)  (kappa NULL -> 1)
+                    // 1: z = P^{-1} v (builds the preconditioner first)
+  double a, kbar;
+  const double* kappa;
+  const double* v;
+  double* y;
+  int status_slot;
+  int* status;
+};
+
+// launchers (kernels.cu)
+cudaError_t launch_rhs(const RhsArgs& a, cudaStream_t s);
+cudaError_t launch_level(const LevelArgs& a, int mixed, cudaStream_t s);
+cudaError_t launch_apply(const ApplyArgs& a, int fp32, cudaStream_t s);
+// out64 = in, out32 = (float) in
+cudaError_t launch_convert(const double* in, double* out64, float* out32, int n, cudaStream_t s);
+// CTAs per SM that every cooperative kernel can co-schedule with `smem`
+// dynamic shared bytes; 0 on failure.
+int coop_blocks_per_sm(size_t smem);
+size_t plan_smem_bytes(const DevPlan& P);
+
+}  // namespace tsfde

@@ -1,0 +1,82 @@
+"""CPU-side checks of the C ABI: the library builds, loads without a GPU,
+exports every entry point declared in include/tsfde.h, and rejects invalid
+arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2002_11978_gb300 import build
+    build.build()
+    import paper_2002_11978_gb300 as pkg
+    return pkg.load_library()
+
+
+def declared_entry_points():
+    text = open(os.path.join(ROOT, "include", "tsfde.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tsfde_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_entry_points():
+    names = declared_entry_points()
+    assert "tsfde_setup" in names and "tsfde_step" in names and "tsfde_solve" in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_entry_points():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_declared_symbol():
+    import paper_2002_11978_gb300 as pkg
+    assert sorted(pkg.exported_names()) == declared_entry_points()
+
+
+def test_default_opts(lib):
+    import paper_2002_11978_gb300 as pkg
+    o = pkg.default_opts()
+    assert o.krylov_tol == 1e-12 and o.precision == pkg.TSFDE_FP64 and o.max_it > 0
+
+
+@pytest.mark.parametrize("args", [
+    (0.0, 0.5, 1.0, 1.0, 7, 4, 3.0, 1e-12),    # alpha
+    (2.0, 0.5, 1.0, 1.0, 7, 4, 3.0, 1e-12),
+    (1.5, 0.0, 1.0, 1.0, 7, 4, 3.0, 1e-12),    # gamma
+    (1.5, 1.0, 1.0, 1.0, 7, 4, 3.0, 1e-12),
+    (1.5, 0.5, -1.0, 1.0, 7, 4, 3.0, 1e-12),   # l
+    (1.5, 0.5, 1.0, 0.0, 7, 4, 3.0, 1e-12),    # T
+    (1.5, 0.5, 1.0, 1.0, 0, 4, 3.0, 1e-12),    # n
+    (1.5, 0.5, 1.0, 1.0, 7, 0, 3.0, 1e-12),    # M
+    (1.5, 0.5, 1.0, 1.0, 7, 4, 0.5, 1e-12),    # r
+    (1.5, 0.5, 1.0, 1.0, 7, 4, 3.0, 0.0),      # soe_tol
+])
+def test_setup_rejects_invalid_arguments(lib, args):
+    import paper_2002_11978_gb300 as pkg
+    ctx = ctypes.c_void_p()
+    o = pkg.default_opts()
+    rc = lib.tsfde_setup(ctypes.byref(ctx), *args, ctypes.byref(o))
+    assert rc == pkg.TSFDE_EINVAL
+    assert not ctx
+
+
+def test_setup_rejects_bad_mu(lib):
+    import paper_2002_11978_gb300 as pkg
+    ctx = ctypes.c_void_p()
+    o = pkg.default_opts()
+    o.mu = 1.2  # must exceed alpha = 1.5
+    assert lib.tsfde_setup(ctypes.byref(ctx), 1.5, 0.5, 1.0, 1.0, 7, 4, 3.0, 1e-12,
+                           ctypes.byref(o)) == pkg.TSFDE_EINVAL
+
+
+def test_null_context_calls_fail_cleanly(lib):
+    import paper_2002_11978_gb300 as pkg
+    assert lib.tsfde_reset(None) == pkg.TSFDE_EINVAL
+    assert lib.tsfde_step(None, None, None, None, None, None) == pkg.TSFDE_EINVAL
+    assert lib.tsfde_strerror(pkg.TSFDE_ETIMEOUT) == b"device barrier timed out"
