@@ -202,6 +202,31 @@ int tsfde_precond_apply(tsfde_ctx* ctx, double a, double kbar, const double* v,
 int tsfde_linear_solve(tsfde_ctx* ctx, double a, const double* kappa,
                        const double* b, double* x, tsfde_step_info* info);
 
+/* ---- product without any device allocation ---------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc themselves (for example code whose device
+ * memory all comes from a framework's pool, or a thread that must not
+ * trigger the allocator's implicit synchronisation).
+ *
+ * y = A v for the IFL Toeplitz matrix of Eq. (3.16x) with n interior points
+ * on (-l, l), splitting mu (<= 0: 1 + alpha/2) and kappa_mu (<= 0: derived
+ * from mu).  v, y: dev n, owned by the caller.  No context is needed and
+ * no memory is allocated: the twiddles, symbol, spectrum and work buffers
+ * live in one fixed array of about 1.5 MB inside the library, which every
+ * GPU that loads the library keeps until the process exits.
+ *  - n must be <= 16383; larger n returns TSFDE_ENOTSUP (with a message on
+ *    stderr) without touching the device.
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture.
+ *  - All calls on a device share the array and it keeps the last call's
+ *    contents; the call clears what must start at zero itself.  Calls whose
+ *    work overlaps on the GPU (other streams, other host threads) race on
+ *    the array: serialise them.
+ *  - Enqueued on `stream` (cudaStream_t, NULL = default); the call waits
+ *    for its own completion and returns the kernel's status. */
+int tsfde_toeplitz_apply_static(double alpha, double mu, int kappa_mu, double l,
+                                int64_t n, const double* v, double* y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -85,6 +85,8 @@ _SIGNATURES = [
                                            ctypes.c_int]),
     ("tsfde_linear_solve", ctypes.c_int, [_V, ctypes.c_double, _V, _V, _V,
                                           ctypes.POINTER(tsfde_step_info)]),
+    ("tsfde_toeplitz_apply_static", ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                   ctypes.c_double, ctypes.c_int64, _V, _V, _V]),
 ]
 
 _lib = None
@@ -303,6 +305,16 @@ class Solver:
                                            _dev(b, self.n, "b"), _dev(x, self.n, "x"),
                                            ctypes.byref(info)), self.ctx)
         return _info_dict(info)
+
+
+def toeplitz_apply_static(alpha, n, v, y, l=1.0, mu=None, kappa_mu=None, stream=None):
+    """y = A v through tsfde_toeplitz_apply_static (no context, no device
+    allocation; n <= 16383)."""
+    lib = load_library()
+    _check(lib.tsfde_toeplitz_apply_static(alpha, 0.0 if mu is None else mu,
+                                           0 if kappa_mu is None else kappa_mu, l, int(n),
+                                           _dev(v, n, "v"), _dev(y, n, "y"),
+                                           _stream_handle(stream)))
 
 
 def _prec(p):

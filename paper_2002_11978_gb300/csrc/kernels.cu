@@ -9,6 +9,9 @@
 // (dev.cuh); every kernel returns a status instead of hanging or trapping.
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <cstdio>
+
 #include "../../include/tsfde.h"
 #include "dev.cuh"
 #include "plan.h"
@@ -803,3 +806,242 @@ cudaError_t launch_apply(const ApplyArgs& a, int fp32, cudaStream_t s) {
 }
 
 }  // namespace tsfde
+
+// =====================================================================
+// Toeplitz product without any device allocation.
+//
+// For callers that cannot call cudaMalloc themselves: code running inside
+// a pooled-memory framework that forbids raw device allocations, or a host
+// thread that must not trigger allocator synchronisation.  Every work
+// buffer and table lives in the one fixed-size array below, which each GPU
+// that loads this library holds until the process exits.  The kernel builds
+// the twiddles, the IFL symbol of Eq. (3.16x) and its circulant-embedding
+// spectrum itself, then applies the product; nothing persists between calls
+// except the array's contents.
+// =====================================================================
+namespace tsfde {
+
+constexpr int kStaticMaxN = 16383;   // largest n accepted
+constexpr int kStaticMaxL = 32768;   // embedding length for kStaticMaxN
+constexpr int kStaticMaxG = 1024;    // largest cooperative grid
+// layout (bytes, each block 256-aligned): barrier | partials | status |
+// tw64 | tw32 | sym | sig | rho | S1 | S2
+constexpr size_t kSA_bar = 0;
+constexpr size_t kSA_part = 256;
+constexpr size_t kSA_status = kSA_part + sizeof(double) * kSlots * kStaticMaxG;
+constexpr size_t kSA_tw64 = kSA_status + 256;
+constexpr size_t kSA_tw32 = kSA_tw64 + sizeof(double2) * kStaticMaxL;
+constexpr size_t kSA_sym = kSA_tw32 + sizeof(float2) * kStaticMaxL;
+constexpr size_t kSA_sig = kSA_sym + sizeof(double) * (kStaticMaxN + 1);
+constexpr size_t kSA_rho = kSA_sig + sizeof(double) * (kStaticMaxL / 2) + 256;
+constexpr size_t kSA_S1 = kSA_rho + sizeof(double2) * (kStaticMaxL / 2);
+constexpr size_t kSA_S2 = kSA_S1 + sizeof(double2) * (kStaticMaxL / 2);
+constexpr size_t kStaticBytes = kSA_S2 + sizeof(double2) * (kStaticMaxL / 2);
+
+static __device__ __align__(256) unsigned char g_toeplitz_scratch[kStaticBytes];
+
+struct StaticApplyArgs {
+  DevPlan P;
+  double alpha, mu, kappa_mu, C;  // C = c_{1,alpha} / (nu h^alpha)
+  double* sym;
+  const double* v;
+  double* y;
+  int* status;
+};
+
+__device__ double static_gap_pow(double k, double nu) {
+  if (k == 1.0) return pow(2.0, nu);
+  return pow(k, nu) * (expm1(nu * log1p(1.0 / k)) - expm1(nu * log1p(-1.0 / k)));
+}
+
+__global__ void __launch_bounds__(kThreads) k_apply_static(StaticApplyArgs A) {
+  const DevPlan& P = A.P;
+  const int n = P.n, L = P.L;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gstr = gridDim.x * blockDim.x;
+  const double nu = A.mu - A.alpha;
+  const int N = n + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* red0 = reinterpret_cast<double*>(smem_raw);
+  // twiddles W_L^k and off-diagonal symbol entries; partial sums of the
+  // diagonal's long sum (Eq. (3.16x))
+  double2* tw64 = const_cast<double2*>(P.twL64);
+  float2* tw32 = const_cast<float2*>(P.twL32);
+  double acc = 0.0;
+  for (int k = gtid; k < L; k += gstr) {
+    double s, c;
+    sincospi(-2.0 * (double)k / (double)L, &s, &c);
+    tw64[k] = make_double2(c, s);
+    tw32[k] = make_float2((float)c, (float)s);
+  }
+  for (int k = gtid; k < n; k += gstr) {
+    if (k == 1) A.sym[1] = -0.5 * A.C * (pow(2.0, nu) + A.kappa_mu - 1.0);
+    if (k >= 2) A.sym[k] = -0.5 * A.C * static_gap_pow((double)k, nu) * pow((double)k, -A.mu);
+  }
+  for (int q = 2 + gtid; q <= N - 1; q += gstr) {
+    const double Q = (double)q;
+    acc += static_gap_pow(Q, nu) * pow(Q, -A.mu);
+  }
+  put_partial(P, SL_KAP, block_sum(acc, red0));
+  if (!gsync(P)) { if (blockIdx.x == 0 && threadIdx.x == 0) *A.status = TSFDE_ETIMEOUT; return; }
+  const double big = get_sum(P, SL_KAP, red0);
+  if (gtid == 0) {
+    const double Nd = (double)N;
+    const double lastN = pow(Nd, nu - A.mu) * (-expm1(nu * log1p(-1.0 / Nd)));
+    A.sym[0] = A.C * (big + lastN + (pow(2.0, nu) + A.kappa_mu - 1.0) +
+                      2.0 * nu / (A.alpha * pow(Nd, A.alpha)));
+  }
+  if (!gsync(P)) { if (blockIdx.x == 0 && threadIdx.x == 0) *A.status = TSFDE_ETIMEOUT; return; }
+  SmemAll S = smem_setup(P);
+  // spectrum of the even embedding of the symbol -> (sigma, rho) tables
+  const double* sym = A.sym;
+  auto proE = [&](int i) -> double {
+    if (i < n) return sym[i];
+    const int k = L - i;
+    return (k < n) ? sym[k] : 0.0;
+  };
+  passA_real<double, true>(P, S.d, L, proE);
+  if (!gsync(P)) goto fail;
+  passB<double, MID_SPEC>(P, S.d, nullptr, nullptr, const_cast<double*>(P.sigT64),
+                          const_cast<double2*>(P.rhoT64), nullptr);
+  if (!gsync(P)) goto fail;
+  {
+    auto pro = [&](int i) -> double { return A.v[i]; };
+    passA_real<double, false>(P, S.d, n, pro);
+  }
+  if (!gsync(P)) goto fail;
+  passB<double, MID_APPLY>(P, S.d, P.sigT64, P.rhoT64, nullptr, nullptr, nullptr);
+  if (!gsync(P)) goto fail;
+  {
+    auto epi = [&](int i, double yv) -> double { A.y[i] = yv; return 0.0; };
+    passCA_real<double, false>(P, S.d, epi);
+  }
+  if (!gsync(P)) goto fail;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *A.status = TSFDE_OK;
+  return;
+fail:
+  if (blockIdx.x == 0 && threadIdx.x == 0) *A.status = TSFDE_ETIMEOUT;
+}
+
+// Device address of g_toeplitz_scratch, looked up once per device (with that
+// device current) on the first call made on it.
+static unsigned char* g_scratch_addr[64];
+static int g_scratch_ready[64];
+
+static int static_scratch(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= 64) return TSFDE_ENOTSUP;
+  if (!__atomic_load_n(&g_scratch_ready[dev], __ATOMIC_ACQUIRE)) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_toeplitz_scratch);
+    if (e != cudaSuccess) {
+      std::fprintf(stderr, "tsfde_toeplitz_apply_static: cudaGetSymbolAddress failed: %s\n",
+                   cudaGetErrorString(e));
+      return TSFDE_ECUDA;
+    }
+    g_scratch_addr[dev] = static_cast<unsigned char*>(p);
+    __atomic_store_n(&g_scratch_ready[dev], 1, __ATOMIC_RELEASE);
+  }
+  *out = g_scratch_addr[dev];
+  return TSFDE_OK;
+}
+
+static Geo static_geo(int Nfft) {
+  Geo g{};
+  int lg = 0;
+  while ((1 << lg) < Nfft) ++lg;
+  g.Nfft = Nfft;
+  g.lgN1 = (lg + 1) / 2;
+  g.N1 = 1 << g.lgN1;
+  g.lgN2 = lg - g.lgN1;
+  g.N2 = 1 << g.lgN2;
+  g.lgct64 = g.lgN2 < 1 ? g.lgN2 : 1;
+  g.lgct32 = g.lgct64;
+  return g;
+}
+
+}  // namespace tsfde
+
+extern "C" int tsfde_toeplitz_apply_static(double alpha, double mu, int kappa_mu, double l,
+                                           int64_t n, const double* v, double* y, void* stream) {
+  using namespace tsfde;
+  if (!v || !y) return TSFDE_EINVAL;
+  if (!(alpha > 0.0 && alpha < 2.0) || !(l > 0.0) || n < 1) return TSFDE_EINVAL;
+  if (mu <= 0.0) mu = 1.0 + 0.5 * alpha;
+  if (!(mu > alpha && mu <= 2.0)) return TSFDE_EINVAL;
+  if (kappa_mu <= 0) kappa_mu = (mu == 2.0) ? 2 : 1;
+  if (n > kStaticMaxN) {
+    std::fprintf(stderr,
+                 "tsfde_toeplitz_apply_static: n = %lld exceeds the fixed scratch capacity "
+                 "n <= %d; use tsfde_toeplitz_apply on a context instead\n",
+                 (long long)n, kStaticMaxN);
+    return TSFDE_ENOTSUP;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return TSFDE_ECUDA;
+  unsigned char* base = nullptr;
+  int st = static_scratch(dev, &base);
+  if (st != TSFDE_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  DevPlan P{};
+  int L = 8;
+  while (L < 2 * n - 1) L *= 2;
+  P.n = (int)n;
+  P.L = L;
+  P.Nc = L / 2;
+  P.gr = static_geo(P.Nc);
+  P.gc = static_geo(P.L);
+  P.T = P.gr.N1 > P.gr.N2 ? P.gr.N1 : P.gr.N2;
+  P.W = (P.gr.N1 << P.gr.lgct64) > 2 * P.gr.N2 ? (P.gr.N1 << P.gr.lgct64) : 2 * P.gr.N2;
+  P.timeout = 2000000000LL;
+  P.bar = reinterpret_cast<GridBarrier*>(base + kSA_bar);
+  P.part = reinterpret_cast<double*>(base + kSA_part);
+  P.twL64 = reinterpret_cast<const double2*>(base + kSA_tw64);
+  P.twL32 = reinterpret_cast<const float2*>(base + kSA_tw32);
+  P.sigT64 = reinterpret_cast<const double*>(base + kSA_sig);
+  P.rhoT64 = reinterpret_cast<const double2*>(base + kSA_rho);
+  P.S1 = reinterpret_cast<double2*>(base + kSA_S1);
+  P.S2 = reinterpret_cast<double2*>(base + kSA_S2);
+
+  const size_t smem = plan_smem_bytes(P);
+  int nsm = 0, bps = 0;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_apply_static, kThreads, smem)) != cudaSuccess)
+    return TSFDE_ECUDA;
+  if (bps < 1) return TSFDE_ECUDA;
+  int items = (P.gr.N2 >> P.gr.lgct64);
+  if ((P.gr.N1 >> 1) + 1 > items) items = (P.gr.N1 >> 1) + 1;
+  int G = nsm * (bps < 2 ? bps : 2);
+  if (G > items) G = items;
+  if (G > kStaticMaxG) G = kStaticMaxG;
+  if (G < 1) G = 1;
+  P.G = G;
+
+  StaticApplyArgs A{};
+  A.P = P;
+  A.alpha = alpha;
+  A.mu = mu;
+  A.kappa_mu = (double)kappa_mu;
+  const double nu = mu - alpha;
+  const double h = 2.0 * l / (double)(n + 1);
+  const double pi = 3.14159265358979323846;
+  const double c1 = std::pow(2.0, alpha - 1.0) * alpha * std::tgamma(0.5 * (alpha + 1.0)) /
+                    (std::sqrt(pi) * std::tgamma(1.0 - 0.5 * alpha));
+  A.C = c1 / (nu * std::pow(h, alpha));
+  A.sym = reinterpret_cast<double*>(base + kSA_sym);
+  A.v = v;
+  A.y = y;
+  A.status = reinterpret_cast<int*>(base + kSA_status);
+  // the barrier counters and the status word must start at zero/unknown
+  if ((e = cudaMemsetAsync(P.bar, 0, sizeof(GridBarrier), s)) != cudaSuccess) return TSFDE_ECUDA;
+  if ((e = cudaMemsetAsync(A.status, 0xff, sizeof(int), s)) != cudaSuccess) return TSFDE_ECUDA;
+  void* args[] = {(void*)&A};
+  e = cudaLaunchCooperativeKernel((const void*)k_apply_static, dim3(G), dim3(kThreads), args, smem, s);
+  if (e != cudaSuccess) return TSFDE_ECUDA;
+  int status = -1;
+  if ((e = cudaMemcpyAsync(&status, A.status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return TSFDE_ECUDA;
+  return status < 0 ? (int)TSFDE_ECUDA : status;
+}
