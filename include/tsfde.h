@@ -65,6 +65,11 @@ typedef struct tsfde_opts {
   int precond;          /* TSFDE_STRANG (default) or TSFDE_PRECOND_NONE     */
   double inner_tol;     /* mixed: FP32 inner relative tolerance (def. 1e-2) */
   int max_outer;        /* mixed: FP64 refinement cap (default 60)          */
+  int inner_max_it;     /* mixed: FP32 BiCGSTAB iterations per refinement
+                           sweep (default 40).  The inner solve stops there
+                           even short of inner_tol: at large n its FP32
+                           products cannot resolve every residual, and the
+                           FP64 refinement carries the accuracy.            */
   int soe_E;            /* > 0: use the caller's SOE table below instead of
                            building one (exponentials sorted ascending)     */
   const double* soe_s;  /* host, soe_E nodes s_j > 0                        */
@@ -117,7 +122,8 @@ int tsfde_default_opts(tsfde_opts* opts);
  * tsfde_get_soe), the Toeplitz symbol of Eq. (3.16x) and its circulant
  * embedding spectrum, the Strang eigenvalues of Sec. 4.1, and all device
  * workspaces.  Validation: 0<alpha<2, 0<gamma<1, l>0, T>0, n>=1, M>=1, r>=1,
- * soe_tol in (0, 1e-2], mu in (alpha, 2].  opts may be NULL (defaults).
+ * soe_tol in (0, 1e-2], mu in (alpha, 2]; n <= 2^18 (else TSFDE_ENOTSUP).
+ * opts may be NULL (defaults).
  * On error *out is NULL. */
 int tsfde_setup(tsfde_ctx** out, double alpha, double gamma, double l, double T,
                 int64_t n, int64_t M, double r, double soe_tol,

@@ -33,6 +33,7 @@ class tsfde_opts(ctypes.Structure):
                 ("krylov_tol", ctypes.c_double), ("max_it", ctypes.c_int),
                 ("precision", ctypes.c_int), ("precond", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
+                ("inner_max_it", ctypes.c_int),
                 ("soe_E", ctypes.c_int), ("soe_s", _dp), ("soe_w", _dp), ("profile", ctypes.c_int),
                 ("barrier_timeout_cycles", ctypes.c_longlong), ("stream", ctypes.c_void_p)]
 
@@ -156,7 +157,7 @@ class Solver:
 
     def __init__(self, alpha, gamma, l, T, n, M, r, soe_tol=1e-12, *, precision="fp64",
                  precond="strang", krylov_tol=1e-12, max_it=2000, inner_tol=1e-2,
-                 max_outer=60, mu=None, kappa_mu=None, soe=None, barrier_timeout_cycles=0,
+                 max_outer=60, inner_max_it=40, mu=None, kappa_mu=None, soe=None, barrier_timeout_cycles=0,
                  profile=False, stream=None):
         lib = load_library()
         o = default_opts()
@@ -166,6 +167,7 @@ class Solver:
         o.precond = {"strang": TSFDE_STRANG, "none": TSFDE_PRECOND_NONE}[precond]
         o.inner_tol = inner_tol
         o.max_outer = max_outer
+        o.inner_max_it = inner_max_it
         o.mu = 0.0 if mu is None else mu
         o.kappa_mu = 0 if kappa_mu is None else kappa_mu
         o.barrier_timeout_cycles = barrier_timeout_cycles

@@ -87,8 +87,8 @@ Geo make_geo(int Nfft) {
   g.N1 = 1 << g.lgN1;
   g.lgN2 = lg - g.lgN1;
   g.N2 = 1 << g.lgN2;
-  g.lgct64 = std::min(1, g.lgN2);
-  g.lgct32 = std::min(1, g.lgN2);
+  g.lgct64 = 0;  // one column per tile: N2 tiles balance the N1/2+1 row pairs
+  g.lgct32 = 0;
   return g;
 }
 
@@ -111,6 +111,7 @@ int tsfde_default_opts(tsfde_opts* o) {
   o->precond = TSFDE_STRANG;
   o->inner_tol = 1e-2;
   o->max_outer = 60;
+  o->inner_max_it = 40;
   o->soe_E = 0;
   o->soe_s = nullptr;
   o->soe_w = nullptr;
@@ -155,7 +156,7 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
   if (!(l > 0.0) || !std::isfinite(l)) return fail(c, TSFDE_EINVAL, "l must be positive");
   if (!(T > 0.0) || !std::isfinite(T)) return fail(c, TSFDE_EINVAL, "T must be positive");
   if (n < 1) return fail(c, TSFDE_EINVAL, "n must be >= 1");
-  if (n > (int64_t(1) << 19)) return fail(c, TSFDE_ENOTSUP, "n > 2^19 is not supported");
+  if (n > (int64_t(1) << 18)) return fail(c, TSFDE_ENOTSUP, "n > 2^18 is not supported");
   if (M < 1) return fail(c, TSFDE_EINVAL, "M must be >= 1");
   if (!(r >= 1.0) || !std::isfinite(r)) return fail(c, TSFDE_EINVAL, "grading r must be >= 1");
   if (!(soe_tol > 0.0 && soe_tol <= 1e-2)) return fail(c, TSFDE_EINVAL, "soe_tol must be in (0,1e-2]");
@@ -169,8 +170,9 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
     return fail(c, TSFDE_EINVAL, "precision must be TSFDE_FP64 or TSFDE_MIXED");
   if (o.precond != TSFDE_STRANG && o.precond != TSFDE_PRECOND_NONE)
     return fail(c, TSFDE_EINVAL, "precond must be TSFDE_STRANG or TSFDE_PRECOND_NONE");
-  if (o.precision == TSFDE_MIXED && (!(o.inner_tol > 0.0 && o.inner_tol < 1.0) || o.max_outer < 1))
-    return fail(c, TSFDE_EINVAL, "mixed needs inner_tol in (0,1) and max_outer >= 1");
+  if (o.precision == TSFDE_MIXED &&
+      (!(o.inner_tol > 0.0 && o.inner_tol < 1.0) || o.max_outer < 1 || o.inner_max_it < 1))
+    return fail(c, TSFDE_EINVAL, "mixed needs inner_tol in (0,1), max_outer >= 1, inner_max_it >= 1");
   if (o.barrier_timeout_cycles < 0) return fail(c, TSFDE_EINVAL, "barrier_timeout_cycles < 0");
   c->alpha = alpha; c->gamma = gamma; c->l = l; c->T = T; c->n = n; c->M = M; c->r = r;
   c->soe_tol = soe_tol; c->mu = mu; c->kappa_mu = kmu;
@@ -426,6 +428,7 @@ static LevelArgs level_args(tsfde_ctx* c, double ahat, const double* b, double* 
   A.max_it = c->opts.max_it;
   A.inner_tol = c->opts.inner_tol;
   A.max_outer = c->opts.max_outer;
+  A.inner_max_it = c->opts.inner_max_it;
   A.k64 = c->k64;
   A.k32 = c->k32;
   A.r64 = c->r64;

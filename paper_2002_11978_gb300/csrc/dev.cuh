@@ -52,35 +52,6 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ bool grid_sync(GridBarrier* gb, long long timeout) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile int* errp = &gb->err;
-    if (*errp == 0) {
-      const unsigned g = ld_acquire_u32(&gb->gen);
-      __threadfence();
-      const unsigned old = atomicAdd(&gb->count, 1u);
-      if (old == gridDim.x - 1) {
-        atomicExch(&gb->count, 0u);
-        __threadfence();
-        st_release_u32(&gb->gen, g + 1u);
-      } else {
-        const long long t0 = clock64();
-        while (ld_acquire_u32(&gb->gen) == g) {
-          if (*errp != 0) break;
-          if (clock64() - t0 > timeout) {
-            atomicOr(&gb->err, 1);
-            break;
-          }
-        }
-      }
-      __threadfence();
-    }
-  }
-  __syncthreads();
-  return *(volatile int*)&gb->err == 0;
-}
-
 // --------------------------------------------------- shared-memory FFT
 // Stockham autosort FFT (radix 4, one radix-2 stage when log2 N is odd) of
 // B independent length-N sequences held in shared memory with layout
@@ -96,11 +67,13 @@ __device__ __forceinline__ cplx<R>* fft_batch(cplx<R>* a, cplx<R>* b, int N, int
   Z* out = b;
   const int B = 1 << lgB;
   int Ns = 1;
+#pragma unroll 1
   while (Ns < N) {
     if (N / Ns >= 4) {
       const int Q = N >> 2;
       const int total = Q << lgB;
       const int st = T / (Ns << 2);
+#pragma unroll 1
       for (int t = threadIdx.x; t < total; t += blockDim.x) {
         const int bb = t & (B - 1);
         const int j = t >> lgB;
@@ -127,6 +100,7 @@ __device__ __forceinline__ cplx<R>* fft_batch(cplx<R>* a, cplx<R>* b, int N, int
       const int H = N >> 1;
       const int total = H << lgB;
       const int st = T / (Ns << 1);
+#pragma unroll 1
       for (int t = threadIdx.x; t < total; t += blockDim.x) {
         const int bb = t & (B - 1);
         const int j = t >> lgB;
@@ -182,26 +156,71 @@ __device__ __forceinline__ double block_max(double v, double* red) {
   return red[32];
 }
 
-// Sum (or max) of G per-CTA partials p[0..G), identical in every CTA:
-// lane l adds p[l], p[l+32], ... in order, then a fixed xor tree.
-template <bool MAX>
-__device__ __forceinline__ double grid_reduce(const double* p, int G, double* red) {
+// ------------------------------------------------------- grid barrier
+// Barrier over all CTAs of a cooperative launch that can also reduce
+// per-CTA partial sums.  Each CTA's thread 0 adds one arrival; the epoch k
+// of this barrier is old/G + 1, so the counter never needs a reset.  The
+// last CTA to arrive reduces the requested partial slots in a fixed order
+// (so every launch and every CTA sees bitwise the same values), publishes
+// them in gb->result, and releases the epoch; the others poll the release
+// word (on its own cache line) with a bounded wait.  On timeout err is set,
+// later barriers return false at once and the kernel unwinds.
+// red: >= 64 doubles of shared scratch.  out: nred values, in every thread.
+__device__ __forceinline__ bool grid_sync_red(GridBarrier* gb, long long timeout,
+                                              const double* part, int G, int nred,
+                                              const int* slots, unsigned maxmask,
+                                              double* out, double* red) {
+  int* flag = reinterpret_cast<int*>(red + 48);
   __syncthreads();
-  if (threadIdx.x < 32) {
-    const int l = threadIdx.x;
-    double x = 0.0;
-    for (int q = l; q < G; q += 32) {
-      double y = __ldcg(p + q);
-      x = MAX ? fmax(x, y) : x + y;
+  if (threadIdx.x == 0) {
+    int f = 0;
+    unsigned k = 0;
+    if (*(volatile int*)&gb->err == 0) {
+      __threadfence();
+      const unsigned old = atomicAdd(&gb->count, 1u);
+      __threadfence();
+      k = old / (unsigned)G + 1u;
+      f = ((old % (unsigned)G) == (unsigned)(G - 1)) ? 2 : 1;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      double y = __shfl_xor_sync(0xffffffffu, x, o);
-      x = MAX ? fmax(x, y) : x + y;
-    }
-    if (l == 0) red[32] = x;
+    flag[0] = f;
+    flag[1] = (int)k;
   }
   __syncthreads();
-  return red[32];
+  const int f = flag[0];
+  const unsigned k = (unsigned)flag[1];
+  if (f == 0) return false;
+  if (f == 2) {
+    for (int q = 0; q < nred; ++q) {
+      const double* p = part + slots[q] * G;
+      const bool mx = (maxmask >> q) & 1u;
+      double v = 0.0;
+      for (int c = threadIdx.x; c < G; c += blockDim.x) {
+        const double y = __ldcg(p + c);
+        v = mx ? fmax(v, y) : v + y;
+      }
+      v = mx ? block_max(v, red) : block_sum(v, red);
+      if (threadIdx.x == 0) gb->result[q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release_u32(&gb->gen, k);
+    }
+  } else if (threadIdx.x == 0) {
+    const long long t0 = clock64();
+    while (ld_acquire_u32(&gb->gen) < k) {
+      if (*(volatile int*)&gb->err != 0) break;
+      if (clock64() - t0 > timeout) {
+        atomicOr(&gb->err, 1);
+        break;
+      }
+      __nanosleep(20);
+    }
+  }
+  __syncthreads();
+  if (*(volatile int*)&gb->err != 0) return false;
+  for (int q = 0; q < nred; ++q) out[q] = __ldcg(&gb->result[q]);
+  return true;
 }
 
 }  // namespace tsfde

@@ -97,15 +97,34 @@ __device__ SmemAll smem_setup(const DevPlan& P) {
 __device__ __forceinline__ void put_partial(const DevPlan& P, int slot, double v) {
   if (threadIdx.x == 0) P.part[slot * P.G + blockIdx.x] = v;
 }
-__device__ __forceinline__ double get_sum(const DevPlan& P, int slot, double* red) {
-  return grid_reduce<false>(P.part + slot * P.G, P.G, red);
+// Grid barrier; the _sum variants also return the grid-wide reduction of
+// the partial slots written before the barrier (bit-identical in all CTAs).
+__device__ __forceinline__ bool gsync(const DevPlan& P, double* red) {
+  return grid_sync_red(P.bar, P.timeout, P.part, P.G, 0, nullptr, 0u, nullptr, red);
 }
-__device__ __forceinline__ double get_max(const DevPlan& P, int slot, double* red) {
-  return grid_reduce<true>(P.part + slot * P.G, P.G, red);
+__device__ __forceinline__ bool gsync_sum(const DevPlan& P, double* red, int s0, double& o0) {
+  const int sl[1] = {s0};
+  double o[1];
+  const bool ok = grid_sync_red(P.bar, P.timeout, P.part, P.G, 1, sl, 0u, o, red);
+  o0 = o[0];
+  return ok;
 }
-__device__ __forceinline__ bool gsync(const DevPlan& P) { return grid_sync(P.bar, P.timeout); }
+__device__ __forceinline__ bool gsync_sum2(const DevPlan& P, double* red, int s0, int s1,
+                                           unsigned maxmask, double& o0, double& o1) {
+  const int sl[2] = {s0, s1};
+  double o[2];
+  const bool ok = grid_sync_red(P.bar, P.timeout, P.part, P.G, 2, sl, maxmask, o, red);
+  o0 = o[0];
+  o1 = o[1];
+  return ok;
+}
 
 // ------------------------------------------------------------------ passes
+// Each thread handles at most kPre elements of a work item (tile or row
+// pair); their store twiddles and spectral coefficients are loaded into
+// registers before the shared-memory FFT so the L2 latency overlaps it.
+constexpr int kPre = 4;  // with 256 threads: work items of <= 1024 elements (n <= 2^18)
+
 // Pass A, real input: x (length nin, zero beyond) -> z_j = x_{2j} + i x_{2j+1},
 // column FFTs over j1 (j = N2 j1 + j2), twiddle W_Nc^{j2 k1}, store
 // S1[k1*N2 + j2].  Without FULL only rows j1 < N1/2 can be non-zero
@@ -117,13 +136,23 @@ __device__ void passA_real(const DevPlan& P, const Smem<R>& sm, int nin, Pro& pr
   const int lc = lgct<R>(g), ct = 1 << lc;
   const int N1 = g.N1, N2 = g.N2;
   const int ntiles = N2 >> lc;
+  const int total = N1 << lc;
   const int rows = FULL ? N1 : (N1 >> 1);
   const int tstride = P.L / g.Nfft;
   Z* S1 = reinterpret_cast<Z*>(P.S1);
   const Z* tw = twL<R>(P);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int c0 = tile << lc;
-    for (int e = threadIdx.x; e < (N1 << lc); e += blockDim.x) {
+    Z wp[kPre];
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) {
+      const int e = threadIdx.x + q * blockDim.x;
+      if (e < total) {
+        const int k1 = e >> lc, j2 = c0 + (e & (ct - 1));
+        wp[q] = tw[((j2 * k1) & (g.Nfft - 1)) * tstride];
+      }
+    }
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int j1 = e >> lc, c = e & (ct - 1);
       Z v = mkc<R>(R(0), R(0));
       if (j1 < rows) {
@@ -136,11 +165,10 @@ __device__ void passA_real(const DevPlan& P, const Smem<R>& sm, int nin, Pro& pr
     }
     __syncthreads();
     const Z* res = fft_batch<R, false>(sm.bA, sm.bB, N1, lc, sm.tw, P.T);
-    for (int e = threadIdx.x; e < (N1 << lc); e += blockDim.x) {
-      const int k1 = e >> lc, c = e & (ct - 1);
-      const int j2 = c0 + c;
-      const int m = (j2 * k1) & (g.Nfft - 1);
-      S1[k1 * N2 + j2] = cmul(res[e], tw[m * tstride]);
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) {
+      const int e = threadIdx.x + q * blockDim.x;
+      if (e < total) S1[(e >> lc) * N2 + c0 + (e & (ct - 1))] = cmul(res[e], wp[q]);
     }
     __syncthreads();
   }
@@ -154,23 +182,32 @@ __device__ void passA_cplx(const DevPlan& P, const Smem<R>& sm, Pro& pro) {
   const int lc = lgct<R>(g), ct = 1 << lc;
   const int N1 = g.N1, N2 = g.N2;
   const int ntiles = N2 >> lc;
+  const int total = N1 << lc;
   const int tstride = P.L / g.Nfft;
   Z* S1 = reinterpret_cast<Z*>(P.S1);
   const Z* tw = twL<R>(P);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int c0 = tile << lc;
-    for (int e = threadIdx.x; e < (N1 << lc); e += blockDim.x) {
+    Z wp[kPre];
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) {
+      const int e = threadIdx.x + q * blockDim.x;
+      if (e < total) {
+        const int k1 = e >> lc, j2 = c0 + (e & (ct - 1));
+        wp[q] = tw[((j2 * k1) & (g.Nfft - 1)) * tstride];
+      }
+    }
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int j1 = e >> lc, c = e & (ct - 1);
       const int j = N2 * j1 + c0 + c;
       sm.bA[e] = (j1 < (N1 >> 1) && j < P.n) ? pro(j) : mkc<R>(R(0), R(0));
     }
     __syncthreads();
     const Z* res = fft_batch<R, false>(sm.bA, sm.bB, N1, lc, sm.tw, P.T);
-    for (int e = threadIdx.x; e < (N1 << lc); e += blockDim.x) {
-      const int k1 = e >> lc, c = e & (ct - 1);
-      const int j2 = c0 + c;
-      const int m = (j2 * k1) & (g.Nfft - 1);
-      S1[k1 * N2 + j2] = cmul(res[e], tw[m * tstride]);
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) {
+      const int e = threadIdx.x + q * blockDim.x;
+      if (e < total) S1[(e >> lc) * N2 + c0 + (e & (ct - 1))] = cmul(res[e], wp[q]);
     }
     __syncthreads();
   }
@@ -204,7 +241,28 @@ __device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__
     const int kb = (it == 0 || it == (N1 >> 1)) ? -1 : N1 - it;
     const int lgB = (kb < 0) ? 0 : 1;
     const int B = 1 << lgB;
-    for (int e = threadIdx.x; e < (N2 << lgB); e += blockDim.x) {
+    const int total = N2 << lgB;
+    // per-element coefficients and store twiddles, fetched early
+    Z wp[kPre], cf[kPre];
+    R sg[kPre];
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) {
+      const int e = threadIdx.x + q * blockDim.x;
+      if (e < total) {
+        const int b = e & (B - 1), k2 = e >> lgB;
+        const int k1 = b ? kb : ka;
+        if constexpr (MID == MID_CONV) {
+          cf[q] = conv[k1 * N2 + k2];
+        } else if constexpr (MID == MID_APPLY) {
+          sg[q] = sig[k1 * N2 + k2];
+          cf[q] = rho[k1 * N2 + k2];
+        } else {
+          cf[q] = tw[k1 + N1 * k2];  // W_L^k, k = k1 + N1 k2
+        }
+        if constexpr (MID != MID_SPEC) wp[q] = tw[((k2 * k1) & (g.Nfft - 1)) * tstride];
+      }
+    }
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int b = e & (B - 1), k2 = e >> lgB;
       const int row = b ? kb : ka;
       sm.bA[e] = __ldcg(S1 + row * N2 + k2);
@@ -212,12 +270,15 @@ __device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__
     __syncthreads();
     Z* res = fft_batch<R, false>(sm.bA, sm.bB, N2, lgB, sm.tw, P.T);
     Z* oth = (res == sm.bA) ? sm.bB : sm.bA;
-    for (int e = threadIdx.x; e < (N2 << lgB); e += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) {
+      const int e = threadIdx.x + q * blockDim.x;
+      if (e >= total) continue;
       const int b = e & (B - 1), k2 = e >> lgB;
       const int k1 = b ? kb : ka;
       const Z Zk = res[e];
       if constexpr (MID == MID_CONV) {
-        oth[e] = cmul(Zk, conv[k1 * N2 + k2]);
+        oth[e] = cmul(Zk, cf[q]);
       } else {
         const int q2 = (k1 == 0) ? ((N2 - k2) & (N2 - 1)) : (N2 - 1 - k2);
         const int qb = (B == 1) ? 0 : 1 - b;
@@ -225,14 +286,13 @@ __device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__
         const Z E = mkc<R>(R(0.5) * (Zk.x + Zq.x), R(0.5) * (Zk.y - Zq.y));
         const Z O = mkc<R>(R(0.5) * (Zk.y + Zq.y), R(-0.5) * (Zk.x - Zq.x));
         if constexpr (MID == MID_APPLY) {
-          const R s = sig[k1 * N2 + k2];
-          const Z r = rho[k1 * N2 + k2];
+          const R s = sg[q];
+          const Z r = cf[q];
           const Z Ep = cadd(cscale(E, s), cmul(r, O));
           const Z Op = cadd(cmul(cconj(r), E), cscale(O, s));
           oth[e] = mkc<R>(Ep.x - Op.y, Ep.y + Op.x);
         } else {
-          const int k = k1 + N1 * k2;
-          const Z Wk = tw[k];  // W_L^k (L = 2 Nc)
+          const Z Wk = cf[q];
           const R wo = Wk.x * O.x - Wk.y * O.y;  // Re(W O)
           sig_out[k1 * N2 + k2] = E.x * invNc;
           rho_out[k1 * N2 + k2] = cscale(Wk, wo * invNc);
@@ -242,11 +302,14 @@ __device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__
     __syncthreads();
     if constexpr (MID == MID_SPEC) continue;
     const Z* res2 = fft_batch<R, true>(oth, res, N2, lgB, sm.tw, P.T);
-    for (int e = threadIdx.x; e < (N2 << lgB); e += blockDim.x) {
-      const int b = e & (B - 1), j2 = e >> lgB;
-      const int k1 = b ? kb : ka;
-      const int m = (j2 * k1) & (g.Nfft - 1);
-      S2[k1 * N2 + j2] = cmulc(res2[e], tw[m * tstride]);
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) {
+      const int e = threadIdx.x + q * blockDim.x;
+      if (e < total) {
+        const int b = e & (B - 1), j2 = e >> lgB;
+        const int k1 = b ? kb : ka;
+        S2[k1 * N2 + j2] = cmulc(res2[e], wp[q]);
+      }
     }
     __syncthreads();
   }
@@ -262,20 +325,32 @@ __device__ void passCA_real(const DevPlan& P, const Smem<R>& sm, Epi& epi) {
   const int lc = lgct<R>(g), ct = 1 << lc;
   const int N1 = g.N1, N2 = g.N2, n = P.n;
   const int ntiles = N2 >> lc;
+  const int total = N1 << lc;
   const int tstride = P.L / g.Nfft;
   const Z* S2 = reinterpret_cast<const Z*>(P.S2);
   Z* S1 = reinterpret_cast<Z*>(P.S1);
   const Z* tw = twL<R>(P);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int c0 = tile << lc;
-    for (int e = threadIdx.x; e < (N1 << lc); e += blockDim.x) {
+    Z wp[kPre];
+    if constexpr (DO_A) {
+#pragma unroll
+      for (int q = 0; q < kPre; ++q) {
+        const int e = threadIdx.x + q * blockDim.x;
+        if (e < total) {
+          const int k1 = e >> lc, j2 = c0 + (e & (ct - 1));
+          wp[q] = tw[((j2 * k1) & (g.Nfft - 1)) * tstride];
+        }
+      }
+    }
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int k1 = e >> lc, c = e & (ct - 1);
       sm.bA[e] = __ldcg(S2 + k1 * N2 + c0 + c);
     }
     __syncthreads();
     Z* res = fft_batch<R, true>(sm.bA, sm.bB, N1, lc, sm.tw, P.T);
     Z* oth = (res == sm.bA) ? sm.bB : sm.bA;
-    for (int e = threadIdx.x; e < (N1 << lc); e += blockDim.x) {
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int j1 = e >> lc, c = e & (ct - 1);
       if (j1 < (N1 >> 1)) {
         const int i0 = 2 * (N2 * j1 + c0 + c);
@@ -291,11 +366,10 @@ __device__ void passCA_real(const DevPlan& P, const Smem<R>& sm, Epi& epi) {
     __syncthreads();
     if constexpr (DO_A) {
       const Z* res2 = fft_batch<R, false>(oth, res, N1, lc, sm.tw, P.T);
-      for (int e = threadIdx.x; e < (N1 << lc); e += blockDim.x) {
-        const int k1 = e >> lc, c = e & (ct - 1);
-        const int j2 = c0 + c;
-        const int m = (j2 * k1) & (g.Nfft - 1);
-        S1[k1 * N2 + j2] = cmul(res2[e], tw[m * tstride]);
+#pragma unroll
+      for (int q = 0; q < kPre; ++q) {
+        const int e = threadIdx.x + q * blockDim.x;
+        if (e < total) S1[(e >> lc) * N2 + c0 + (e & (ct - 1))] = cmul(res2[e], wp[q]);
       }
       __syncthreads();
     }
@@ -345,14 +419,14 @@ __device__ bool build_precond(const DevPlan& P, const Smem<R>& sm, double ahat, 
     return cscale(ch[j], q);
   };
   passA_cplx<R>(P, sm, pro);
-  if (!gsync(P)) return false;
+  if (!gsync(P, sm.red)) return false;
   passB<R, MID_CONV>(P, sm, nullptr, nullptr, nullptr, nullptr, Bh<R>(P));
-  if (!gsync(P)) return false;
+  if (!gsync(P, sm.red)) return false;
   R* gv = gcol<R>(P);
   const R invn = R(1.0 / (double)P.n);
   auto epi = [&](int j, Z z) { gv[j] = (ch[j].x * z.x - ch[j].y * z.y) * invn; };
   passC_cplx<R>(P, sm, epi);
-  if (!gsync(P)) return false;
+  if (!gsync(P, sm.red)) return false;
   const int n = P.n, L = P.L;
   auto proE = [&](int i) -> R {
     if (i < n) return gv[i];
@@ -360,9 +434,9 @@ __device__ bool build_precond(const DevPlan& P, const Smem<R>& sm, double ahat, 
     return (k < n) ? gv[k] : R(0);
   };
   passA_real<R, true>(P, sm, L, proE);
-  if (!gsync(P)) return false;
+  if (!gsync(P, sm.red)) return false;
   passB<R, MID_SPEC>(P, sm, nullptr, nullptr, sigG<R>(P), rhoG<R>(P), nullptr);
-  return gsync(P);
+  return gsync(P, sm.red);
 }
 
 // ------------------------------------------------------------- PBiCGSTAB
@@ -393,8 +467,8 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
     }
     put_partial(P, SL_BB, block_sum((double)acc, sm.red));
   }
-  if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
-  const double bb = get_sum(P, SL_BB, sm.red);
+  double bb;
+  if (!gsync_sum(P, sm.red, SL_BB, bb)) { out.status = TSFDE_ETIMEOUT; return out; }
   if (!isfinite(bb)) { out.status = TSFDE_ENONFINITE; return out; }
   if (bb == 0.0) return out;
   const double nb = sqrt(bb);
@@ -421,16 +495,16 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
       };
       passA_real<R, false>(P, sm, n, pro);
     }
-    if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
+    if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
     if (prec) {
       passB<R, MID_APPLY>(P, sm, sigG<R>(P), rhoG<R>(P), nullptr, nullptr, nullptr);
-      if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
+      if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
       auto epi = [&](int i, R y) -> R { V.ph[i] = y; return y; };
       passCA_real<R, true>(P, sm, epi);
-      if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
+      if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
     }
     passB<R, MID_APPLY>(P, sm, sigT<R>(P), rhoT<R>(P), nullptr, nullptr, nullptr);
-    if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
+    if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
     const R* ph = prec ? V.ph : V.p;
     {
       R acc = 0;
@@ -443,8 +517,8 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
       passCA_real<R, false>(P, sm, epi);
       put_partial(P, SL_RV, block_sum((double)acc, sm.red));
     }
-    if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
-    const double rv = get_sum(P, SL_RV, sm.red);
+    double rv;
+    if (!gsync_sum(P, sm.red, SL_RV, rv)) { out.status = TSFDE_ETIMEOUT; return out; }
     if (!isfinite(rv)) { out.status = TSFDE_ENONFINITE; return out; }
     if (rv == 0.0) { out.status = TSFDE_EBREAKDOWN; return out; }
     alpha = rho / rv;
@@ -458,16 +532,16 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
       };
       passA_real<R, false>(P, sm, n, pro);
     }
-    if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
+    if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
     if (prec) {
       passB<R, MID_APPLY>(P, sm, sigG<R>(P), rhoG<R>(P), nullptr, nullptr, nullptr);
-      if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
+      if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
       auto epi = [&](int i, R y) -> R { V.sh[i] = y; return y; };
       passCA_real<R, true>(P, sm, epi);
-      if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
+      if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
     }
     passB<R, MID_APPLY>(P, sm, sigT<R>(P), rhoT<R>(P), nullptr, nullptr, nullptr);
-    if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
+    if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
     const R* sh = prec ? V.sh : V.s;
     {
       R ats = 0, att = 0;
@@ -482,9 +556,8 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
       put_partial(P, SL_TS, block_sum((double)ats, sm.red));
       put_partial(P, SL_TT, block_sum((double)att, sm.red));
     }
-    if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
-    const double ts = get_sum(P, SL_TS, sm.red);
-    const double tt = get_sum(P, SL_TT, sm.red);
+    double ts, tt;
+    if (!gsync_sum2(P, sm.red, SL_TS, SL_TT, 0u, ts, tt)) { out.status = TSFDE_ETIMEOUT; return out; }
     omega = (tt > 0.0) ? ts / tt : 0.0;
     if (!isfinite(omega)) { out.status = TSFDE_ENONFINITE; return out; }
     // x += alpha p^ + omega s^, r = s - omega t
@@ -501,9 +574,7 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
       put_partial(P, SL_RR0, block_sum((double)arr, sm.red));
       put_partial(P, SL_RR, block_sum((double)ar2, sm.red));
     }
-    if (!gsync(P)) { out.status = TSFDE_ETIMEOUT; return out; }
-    rho_new = get_sum(P, SL_RR0, sm.red);
-    rr = get_sum(P, SL_RR, sm.red);
+    if (!gsync_sum2(P, sm.red, SL_RR0, SL_RR, 0u, rho_new, rr)) { out.status = TSFDE_ETIMEOUT; return out; }
   }
 }
 
@@ -513,8 +584,9 @@ __device__ double mean_kappa(const DevPlan& P, const double* kap, double* red) {
   double acc = 0.0;
   for (int i = gtid; i < P.n; i += gstr) acc += kap[i];
   put_partial(P, SL_KAP, block_sum(acc, red));
-  if (!gsync(P)) return -1.0;
-  return get_sum(P, SL_KAP, red) / (double)P.n;
+  double tot;
+  if (!gsync_sum(P, red, SL_KAP, tot)) return -1.0;
+  return tot / (double)P.n;
 }
 
 __device__ void write_stat(StepStat* st, int status, int iters, int outer, double relres) {
@@ -528,7 +600,7 @@ __device__ void write_stat(StepStat* st, int status, int iters, int outer, doubl
 
 // ---------------------------------------------------------- level kernels
 // FP64 level solve: preconditioner build and PBiCGSTAB, all in FP64.
-__global__ void __launch_bounds__(kThreads) k_level64(LevelArgs A) {
+__global__ void __launch_bounds__(kThreads, 2) k_level64(LevelArgs A) {
   const DevPlan& P = A.P;
   SmemAll S = smem_setup(P);
   const double kbar = mean_kappa(P, A.kappa64, S.d.red);
@@ -548,7 +620,7 @@ __global__ void __launch_bounds__(kThreads) k_level64(LevelArgs A) {
 // PBiCGSTAB for (ahat I + K A) e = r; the FP64 residual r = b - M u uses the
 // FP64 product; FP32 for the inner products and the preconditioner.
 // Stops when the last correction satisfies max|e| <= tol max|u|.
-__global__ void __launch_bounds__(kThreads) k_level_mixed(LevelArgs A) {
+__global__ void __launch_bounds__(kThreads, 2) k_level_mixed(LevelArgs A) {
   const DevPlan& P = A.P;
   SmemAll S = smem_setup(P);
   const int n = P.n;
@@ -570,8 +642,8 @@ __global__ void __launch_bounds__(kThreads) k_level_mixed(LevelArgs A) {
     }
     put_partial(P, SL_RES, block_sum(acc, S.d.red));
   }
-  if (!gsync(P)) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
-  const double bb = get_sum(P, SL_RES, S.d.red);
+  double bb;
+  if (!gsync_sum(P, S.d.red, SL_RES, bb)) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
   if (!isfinite(bb)) { write_stat(A.stat, TSFDE_ENONFINITE, 0, 0, 0.0); return; }
   if (bb == 0.0) { write_stat(A.stat, TSFDE_OK, 0, 0, 0.0); return; }
   const double nb = sqrt(bb);
@@ -582,7 +654,7 @@ __global__ void __launch_bounds__(kThreads) k_level_mixed(LevelArgs A) {
     const double sc = 1.0 / nr;
     auto binit = [&](int i) -> float { return (float)(A.r64[i] * sc); };
     SolveRes ir = bicgstab<float>(P, S.f, A.k32, A.kappa32, A.ahat, A.precond != 0,
-                                  A.inner_tol, A.max_it, binit);
+                                  A.inner_tol, A.inner_max_it, binit);
     inner_total += ir.iters;
     if (ir.status == TSFDE_ETIMEOUT) { status = ir.status; break; }
     ++outer;
@@ -602,13 +674,12 @@ __global__ void __launch_bounds__(kThreads) k_level_mixed(LevelArgs A) {
       put_partial(P, SL_EMAX, block_max(emax, S.d.red));
       put_partial(P, SL_XMAX, block_max(xmax, S.d.red));
     }
-    if (!gsync(P)) { status = TSFDE_ETIMEOUT; break; }
-    const double emax = get_max(P, SL_EMAX, S.d.red);
-    const double xmax = get_max(P, SL_XMAX, S.d.red);
+    double emax, xmax;
+    if (!gsync_sum2(P, S.d.red, SL_EMAX, SL_XMAX, 3u, emax, xmax)) { status = TSFDE_ETIMEOUT; break; }
     if (!isfinite(emax) || !isfinite(xmax)) { status = TSFDE_ENONFINITE; break; }
     if (emax <= A.tol * xmax) break;
     passB<double, MID_APPLY>(P, S.d, P.sigT64, P.rhoT64, nullptr, nullptr, nullptr);
-    if (!gsync(P)) { status = TSFDE_ETIMEOUT; break; }
+    if (!gsync(P, S.d.red)) { status = TSFDE_ETIMEOUT; break; }
     {
       double acc = 0.0;
       const double ah = A.ahat;
@@ -621,8 +692,9 @@ __global__ void __launch_bounds__(kThreads) k_level_mixed(LevelArgs A) {
       passCA_real<double, false>(P, S.d, epi);
       put_partial(P, SL_RES, block_sum(acc, S.d.red));
     }
-    if (!gsync(P)) { status = TSFDE_ETIMEOUT; break; }
-    nr = sqrt(get_sum(P, SL_RES, S.d.red));
+    double rr;
+    if (!gsync_sum(P, S.d.red, SL_RES, rr)) { status = TSFDE_ETIMEOUT; break; }
+    nr = sqrt(rr);
     relres = nr / nb;
     if (!isfinite(nr)) { status = TSFDE_ENONFINITE; break; }
     if (nr == 0.0) break;
@@ -643,12 +715,12 @@ __device__ void apply_kernel_body(const ApplyArgs& A, const Smem<R>& sm) {
   }
   auto pro = [&](int i) -> R { return (R)A.v[i]; };
   passA_real<R, false>(P, sm, n, pro);
-  if (!gsync(P)) goto fail;
+  if (!gsync(P, sm.red)) goto fail;
   if (A.kind == 1)
     passB<R, MID_APPLY>(P, sm, sigG<R>(P), rhoG<R>(P), nullptr, nullptr, nullptr);
   else
     passB<R, MID_APPLY>(P, sm, sigT<R>(P), rhoT<R>(P), nullptr, nullptr, nullptr);
-  if (!gsync(P)) goto fail;
+  if (!gsync(P, sm.red)) goto fail;
   {
     auto epi = [&](int i, R y) -> R {
       double yi = (double)y;
@@ -658,18 +730,18 @@ __device__ void apply_kernel_body(const ApplyArgs& A, const Smem<R>& sm) {
     };
     passCA_real<R, false>(P, sm, epi);
   }
-  if (!gsync(P)) goto fail;
+  if (!gsync(P, sm.red)) goto fail;
   if (blockIdx.x == 0 && threadIdx.x == 0) *A.status = TSFDE_OK;
   return;
 fail:
   if (blockIdx.x == 0 && threadIdx.x == 0) *A.status = TSFDE_ETIMEOUT;
 }
 
-__global__ void __launch_bounds__(kThreads) k_apply64(ApplyArgs A) {
+__global__ void __launch_bounds__(kThreads, 2) k_apply64(ApplyArgs A) {
   SmemAll S = smem_setup(A.P);
   apply_kernel_body<double>(A, S.d);
 }
-__global__ void __launch_bounds__(kThreads) k_apply32(ApplyArgs A) {
+__global__ void __launch_bounds__(kThreads, 2) k_apply32(ApplyArgs A) {
   SmemAll S = smem_setup(A.P);
   apply_kernel_body<float>(A, S.f);
 }
@@ -854,7 +926,7 @@ __device__ double static_gap_pow(double k, double nu) {
   return pow(k, nu) * (expm1(nu * log1p(1.0 / k)) - expm1(nu * log1p(-1.0 / k)));
 }
 
-__global__ void __launch_bounds__(kThreads) k_apply_static(StaticApplyArgs A) {
+__global__ void __launch_bounds__(kThreads, 2) k_apply_static(StaticApplyArgs A) {
   const DevPlan& P = A.P;
   const int n = P.n, L = P.L;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -883,15 +955,15 @@ __global__ void __launch_bounds__(kThreads) k_apply_static(StaticApplyArgs A) {
     acc += static_gap_pow(Q, nu) * pow(Q, -A.mu);
   }
   put_partial(P, SL_KAP, block_sum(acc, red0));
-  if (!gsync(P)) { if (blockIdx.x == 0 && threadIdx.x == 0) *A.status = TSFDE_ETIMEOUT; return; }
-  const double big = get_sum(P, SL_KAP, red0);
+  double big;
+  if (!gsync_sum(P, red0, SL_KAP, big)) { if (blockIdx.x == 0 && threadIdx.x == 0) *A.status = TSFDE_ETIMEOUT; return; }
   if (gtid == 0) {
     const double Nd = (double)N;
     const double lastN = pow(Nd, nu - A.mu) * (-expm1(nu * log1p(-1.0 / Nd)));
     A.sym[0] = A.C * (big + lastN + (pow(2.0, nu) + A.kappa_mu - 1.0) +
                       2.0 * nu / (A.alpha * pow(Nd, A.alpha)));
   }
-  if (!gsync(P)) { if (blockIdx.x == 0 && threadIdx.x == 0) *A.status = TSFDE_ETIMEOUT; return; }
+  if (!gsync(P, red0)) { if (blockIdx.x == 0 && threadIdx.x == 0) *A.status = TSFDE_ETIMEOUT; return; }
   SmemAll S = smem_setup(P);
   // spectrum of the even embedding of the symbol -> (sigma, rho) tables
   const double* sym = A.sym;
@@ -901,22 +973,22 @@ __global__ void __launch_bounds__(kThreads) k_apply_static(StaticApplyArgs A) {
     return (k < n) ? sym[k] : 0.0;
   };
   passA_real<double, true>(P, S.d, L, proE);
-  if (!gsync(P)) goto fail;
+  if (!gsync(P, S.d.red)) goto fail;
   passB<double, MID_SPEC>(P, S.d, nullptr, nullptr, const_cast<double*>(P.sigT64),
                           const_cast<double2*>(P.rhoT64), nullptr);
-  if (!gsync(P)) goto fail;
+  if (!gsync(P, S.d.red)) goto fail;
   {
     auto pro = [&](int i) -> double { return A.v[i]; };
     passA_real<double, false>(P, S.d, n, pro);
   }
-  if (!gsync(P)) goto fail;
+  if (!gsync(P, S.d.red)) goto fail;
   passB<double, MID_APPLY>(P, S.d, P.sigT64, P.rhoT64, nullptr, nullptr, nullptr);
-  if (!gsync(P)) goto fail;
+  if (!gsync(P, S.d.red)) goto fail;
   {
     auto epi = [&](int i, double yv) -> double { A.y[i] = yv; return 0.0; };
     passCA_real<double, false>(P, S.d, epi);
   }
-  if (!gsync(P)) goto fail;
+  if (!gsync(P, S.d.red)) goto fail;
   if (blockIdx.x == 0 && threadIdx.x == 0) *A.status = TSFDE_OK;
   return;
 fail:
@@ -954,8 +1026,8 @@ static Geo static_geo(int Nfft) {
   g.N1 = 1 << g.lgN1;
   g.lgN2 = lg - g.lgN1;
   g.N2 = 1 << g.lgN2;
-  g.lgct64 = g.lgN2 < 1 ? g.lgN2 : 1;
-  g.lgct32 = g.lgct64;
+  g.lgct64 = 0;
+  g.lgct32 = 0;
   return g;
 }
 

@@ -7,12 +7,16 @@
 namespace tsfde {
 
 // Bounded grid barrier state (cleared by the host before each cooperative
-// launch); see grid_sync in dev.cuh.
+// launch); see grid_sync_red in dev.cuh.  The arrival counter and the
+// release word sit on separate 128-byte lines so that polling does not
+// contend with arrivals.
 struct GridBarrier {
-  unsigned int count;
-  unsigned int gen;
-  int err;
-  int pad;
+  unsigned int count;     // arrivals, monotonic within one launch
+  int err;                // set once any CTA gave up waiting
+  unsigned int pad0[30];
+  unsigned int gen;       // number of completed barriers
+  unsigned int pad1[31];
+  double result[16];      // scalars reduced by the last CTA to arrive
 };
 
 // One factorisation Nfft = N1 * N2 of a power-of-two transform, driven by
@@ -82,6 +86,7 @@ struct LevelArgs {
   int max_it;
   double inner_tol;
   int max_outer;
+  int inner_max_it;
   KVecs<double> k64;
   KVecs<float> k32;
   double* r64;        // mixed: FP64 residual
