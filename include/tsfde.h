@@ -59,7 +59,9 @@ typedef struct tsfde_opts {
   double krylov_tol;    /* FP64 path: stop when ||r_k||_2/||r_0||_2 < tol
                            (recursive residual, x0 = 0, Sec. 5); mixed path:
                            stop the FP64 refinement when the last correction
-                           satisfies max|e| <= tol * max|u|.  Default 1e-12 */
+                           satisfies max|e| <= tol * max|u|, or when a sweep
+                           no longer halves the FP64 residual (it has reached
+                           its rounding floor).  Default 1e-12              */
   int max_it;           /* BiCGSTAB iteration cap per solve (default 2000)  */
   int precision;        /* TSFDE_FP64 (default) or TSFDE_MIXED              */
   int precond;          /* TSFDE_STRANG (default) or TSFDE_PRECOND_NONE     */

@@ -239,11 +239,13 @@ class Solver:
     # ---- stepping
     def step(self, kappa_m=None, f_m=None, u_out=None, rhs_out=None, sync=True):
         info = tsfde_step_info()
-        _check(self.lib.tsfde_step(self.ctx, _dev(kappa_m, self.n, "kappa_m"),
-                                   _dev(f_m, self.n, "f_m"), _dev(u_out, self.n, "u_out"),
-                                   _dev(rhs_out, self.n, "rhs_out"),
-                                   ctypes.byref(info) if sync else None), self.ctx)
-        self.m += 1
+        rc = self.lib.tsfde_step(self.ctx, _dev(kappa_m, self.n, "kappa_m"),
+                                 _dev(f_m, self.n, "f_m"), _dev(u_out, self.n, "u_out"),
+                                 _dev(rhs_out, self.n, "rhs_out"),
+                                 ctypes.byref(info) if sync else None)
+        if rc == TSFDE_OK or (sync and info.m == self.m + 1):
+            self.m += 1  # the level was computed even if its solve failed
+        _check(rc, self.ctx)
         return _info_dict(info) if sync else None
 
     def solve(self, u_final, u_all=None, sync=True):

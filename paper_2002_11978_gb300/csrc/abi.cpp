@@ -240,16 +240,13 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
   for (double x : lam)
     if (!(x > 0.0)) return fail(c, TSFDE_EINVAL, "Strang eigenvalue not positive (Lemma 4.1 violated)");
   const int Nc = P.Nc, N1 = P.gr.N1, N2 = P.gr.N2;
-  std::vector<double> sig(Nc), sig32d;
-  std::vector<double2> rho(Nc);
+  std::vector<double> sa(Nc), sb(Nc);
   for (int k1 = 0; k1 < N1; ++k1)
     for (int k2 = 0; k2 < N2; ++k2) {
       const int k = k1 + N1 * k2;
       const int kp = (k == 0) ? Nc : Nc - k;
-      const double sg = 0.5 * (S[k] + S[kp]) / Nc;
-      const double dl = 0.5 * (S[k] - S[kp]) / Nc;
-      sig[k1 * N2 + k2] = sg;
-      rho[k1 * N2 + k2] = make_double2(dl * tw[k].real(), dl * tw[k].imag());
+      sa[k1 * N2 + k2] = S[k] / Nc;
+      sb[k1 * N2 + k2] = S[kp] / Nc;
     }
   std::vector<double2> ch64(n), tw64(L);
   std::vector<float2> ch32(n), tw32(L);
@@ -277,11 +274,10 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
         Bh32[k1 * M2 + k2] = make_float2((float)v.real(), (float)v.imag());
       }
   }
-  std::vector<float> sig32(Nc);
-  std::vector<float2> rho32(Nc);
+  std::vector<float> sa32(Nc), sb32(Nc);
   for (int i = 0; i < Nc; ++i) {
-    sig32[i] = (float)sig[i];
-    rho32[i] = make_float2((float)rho[i].x, (float)rho[i].y);
+    sa32[i] = (float)sa[i];
+    sb32[i] = (float)sb[i];
   }
 
   // ---- grid size
@@ -303,16 +299,16 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
   const int64_t ld = ((n + 31) / 32) * 32;
   c->ld = (int)ld;
   bool ok = true;
-  double2 *dtw64, *drho64, *dch64, *dBh64, *drhoG64, *dS1, *dS2;
-  float2 *dtw32, *drho32, *dch32, *dBh32, *drhoG32;
-  double *dsig64, *dlam, *dsigG64, *dg64, *dpart;
-  float *dsig32, *dsigG32, *dg32;
+  double2 *dtw64, *dch64, *dBh64, *dS1, *dS2;
+  float2 *dtw32, *dch32, *dBh32;
+  double *dsa64, *dsb64, *dlam, *dsaG64, *dsbG64, *dg64, *dpart;
+  float *dsa32, *dsb32, *dsaG32, *dsbG32, *dg32;
   GridBarrier* dbar;
   ok &= dalloc(c, &dtw64, L) && dalloc(c, &dtw32, L);
-  ok &= dalloc(c, &dsig64, Nc) && dalloc(c, &drho64, Nc) && dalloc(c, &dsig32, Nc) && dalloc(c, &drho32, Nc);
+  ok &= dalloc(c, &dsa64, Nc) && dalloc(c, &dsb64, Nc) && dalloc(c, &dsa32, Nc) && dalloc(c, &dsb32, Nc);
   ok &= dalloc(c, &dlam, n) && dalloc(c, &dch64, n) && dalloc(c, &dch32, n);
   ok &= dalloc(c, &dBh64, L) && dalloc(c, &dBh32, L);
-  ok &= dalloc(c, &dsigG64, Nc) && dalloc(c, &drhoG64, Nc) && dalloc(c, &dsigG32, Nc) && dalloc(c, &drhoG32, Nc);
+  ok &= dalloc(c, &dsaG64, Nc) && dalloc(c, &dsbG64, Nc) && dalloc(c, &dsaG32, Nc) && dalloc(c, &dsbG32, Nc);
   ok &= dalloc(c, &dg64, n) && dalloc(c, &dg32, n);
   ok &= dalloc(c, &dS1, L) && dalloc(c, &dS2, L);
   ok &= dalloc(c, &dpart, (size_t)kSlots * P.G) && dalloc(c, &dbar, 1);
@@ -331,8 +327,8 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
   c->k64.x = nullptr;
 
   if ((e = upload(dtw64, tw64)) != cudaSuccess || (e = upload(dtw32, tw32)) != cudaSuccess ||
-      (e = upload(dsig64, sig)) != cudaSuccess || (e = upload(drho64, rho)) != cudaSuccess ||
-      (e = upload(dsig32, sig32)) != cudaSuccess || (e = upload(drho32, rho32)) != cudaSuccess ||
+      (e = upload(dsa64, sa)) != cudaSuccess || (e = upload(dsb64, sb)) != cudaSuccess ||
+      (e = upload(dsa32, sa32)) != cudaSuccess || (e = upload(dsb32, sb32)) != cudaSuccess ||
       (e = upload(dlam, lam)) != cudaSuccess || (e = upload(dch64, ch64)) != cudaSuccess ||
       (e = upload(dch32, ch32)) != cudaSuccess || (e = upload(dBh64, Bh64)) != cudaSuccess ||
       (e = upload(dBh32, Bh32)) != cudaSuccess || (e = upload(c->eps, c->eps_h)) != cudaSuccess ||
@@ -343,9 +339,9 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
   if ((e = cudaMemset(c->stats, 0, sizeof(StepStat) * (M + 1))) != cudaSuccess) return cuda_fail(c, e, "cudaMemset");
   P.bar = dbar; P.part = dpart;
   P.twL64 = dtw64; P.twL32 = dtw32;
-  P.sigT64 = dsig64; P.rhoT64 = drho64; P.sigT32 = dsig32; P.rhoT32 = drho32;
+  P.saT64 = dsa64; P.sbT64 = dsb64; P.saT32 = dsa32; P.sbT32 = dsb32;
   P.lam = dlam; P.chirp64 = dch64; P.chirp32 = dch32; P.Bh64 = dBh64; P.Bh32 = dBh32;
-  P.sigG64 = dsigG64; P.rhoG64 = drhoG64; P.sigG32 = dsigG32; P.rhoG32 = drhoG32;
+  P.saG64 = dsaG64; P.sbG64 = dsbG64; P.saG32 = dsaG32; P.sbG32 = dsbG32;
   P.g64 = dg64; P.g32 = dg32; P.S1 = dS1; P.S2 = dS2;
   return TSFDE_OK;
 }

@@ -39,17 +39,17 @@ template <typename R> __device__ __forceinline__ const cplx<R>* twL(const DevPla
 template <typename R> __device__ __forceinline__ int lgct(const Geo& g) {
   if constexpr (sizeof(R) == 8) return g.lgct64; else return g.lgct32;
 }
-template <typename R> __device__ __forceinline__ const R* sigT(const DevPlan& P) {
-  if constexpr (sizeof(R) == 8) return P.sigT64; else return P.sigT32;
+template <typename R> __device__ __forceinline__ const R* saT(const DevPlan& P) {
+  if constexpr (sizeof(R) == 8) return P.saT64; else return P.saT32;
 }
-template <typename R> __device__ __forceinline__ const cplx<R>* rhoT(const DevPlan& P) {
-  if constexpr (sizeof(R) == 8) return P.rhoT64; else return P.rhoT32;
+template <typename R> __device__ __forceinline__ const R* sbT(const DevPlan& P) {
+  if constexpr (sizeof(R) == 8) return P.sbT64; else return P.sbT32;
 }
-template <typename R> __device__ __forceinline__ R* sigG(const DevPlan& P) {
-  if constexpr (sizeof(R) == 8) return P.sigG64; else return P.sigG32;
+template <typename R> __device__ __forceinline__ R* saG(const DevPlan& P) {
+  if constexpr (sizeof(R) == 8) return P.saG64; else return P.saG32;
 }
-template <typename R> __device__ __forceinline__ cplx<R>* rhoG(const DevPlan& P) {
-  if constexpr (sizeof(R) == 8) return P.rhoG64; else return P.rhoG32;
+template <typename R> __device__ __forceinline__ R* sbG(const DevPlan& P) {
+  if constexpr (sizeof(R) == 8) return P.sbG64; else return P.sbG32;
 }
 template <typename R> __device__ __forceinline__ const cplx<R>* chirp(const DevPlan& P) {
   if constexpr (sizeof(R) == 8) return P.chirp64; else return P.chirp32;
@@ -216,16 +216,23 @@ __device__ void passA_cplx(const DevPlan& P, const Smem<R>& sm, Pro& pro) {
 enum { MID_APPLY = 0, MID_SPEC = 1, MID_CONV = 2 };
 
 // Pass B: row FFTs (rows k1 and N1-k1 together), the spectral middle step,
-// inverse row FFTs, twiddle W^{-j2 k1}, store S2.
-//  MID_APPLY: real-input product with a real even spectrum (sigma, rho):
-//    E = (Z_k + conj Z_k')/2, O = -i (Z_k - conj Z_k')/2,
-//    E' = sigma E + rho O, O' = conj(rho) E + sigma O, Z'_k = E' + i O'.
-//  MID_SPEC: forward only; the real spectrum S of an even real sequence
-//    (S_k = Re(E + W_L^k O), S_k' = Re(E - W_L^k O)) stored as (sigma, rho).
+// inverse row FFTs, twiddle W^{-j2 k1}, store S2.  With Z the complex FFT of
+// the packed real input and k' = Nc - k, E = (Z_k + conj Z_k')/2 and
+// O = -i (Z_k - conj Z_k')/2 give the real-input spectrum
+// X_k = E + W_L^k O and conj(X_k') = E - W_L^k O.
+//  MID_APPLY: Y = S X for a real even spectrum S (tables sa = S_k/Nc,
+//    sb = S_k'/Nc), repacked as Z'_k = E' + i O' with
+//    E' = (sa X_k + sb conj X_k')/2, O' = conj(W_L^k) (sa X_k - sb conj X_k')/2.
+//    Each multiplier meets only its own frequency: the split into E and O
+//    is never weighted by the partner's S, which for the IFL symbol can be
+//    ~1e8 times larger (low against high frequencies) and would swamp the
+//    low-frequency result in rounding.
+//  MID_SPEC: forward only; stores sa = Re X_k / Nc, sb = Re conj X_k' / Nc
+//    (the spectrum of an even real sequence is real).
 //  MID_CONV: complex product Z'_k = Z_k * conv_k (geometry gc).
 template <typename R, int MID>
-__device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__ sig,
-                      const cplx<R>* __restrict__ rho, R* sig_out, cplx<R>* rho_out,
+__device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__ sa,
+                      const R* __restrict__ sb, R* sa_out, R* sb_out,
                       const cplx<R>* __restrict__ conv) {
   typedef cplx<R> Z;
   const Geo& g = (MID == MID_CONV) ? P.gc : P.gr;
@@ -244,7 +251,7 @@ __device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__
     const int total = N2 << lgB;
     // per-element coefficients and store twiddles, fetched early
     Z wp[kPre], cf[kPre];
-    R sg[kPre];
+    R s1[kPre], s2[kPre];
 #pragma unroll
     for (int q = 0; q < kPre; ++q) {
       const int e = threadIdx.x + q * blockDim.x;
@@ -253,11 +260,12 @@ __device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__
         const int k1 = b ? kb : ka;
         if constexpr (MID == MID_CONV) {
           cf[q] = conv[k1 * N2 + k2];
-        } else if constexpr (MID == MID_APPLY) {
-          sg[q] = sig[k1 * N2 + k2];
-          cf[q] = rho[k1 * N2 + k2];
         } else {
           cf[q] = tw[k1 + N1 * k2];  // W_L^k, k = k1 + N1 k2
+          if constexpr (MID == MID_APPLY) {
+            s1[q] = sa[k1 * N2 + k2];
+            s2[q] = sb[k1 * N2 + k2];
+          }
         }
         if constexpr (MID != MID_SPEC) wp[q] = tw[((k2 * k1) & (g.Nfft - 1)) * tstride];
       }
@@ -285,17 +293,19 @@ __device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__
         const Z Zq = res[(q2 << lgB) + qb];
         const Z E = mkc<R>(R(0.5) * (Zk.x + Zq.x), R(0.5) * (Zk.y - Zq.y));
         const Z O = mkc<R>(R(0.5) * (Zk.y + Zq.y), R(-0.5) * (Zk.x - Zq.x));
+        const Z Wk = cf[q];
+        const Z WO = cmul(Wk, O);
+        const Z X = cadd(E, WO);   // X_k
+        const Z Xc = csub(E, WO);  // conj(X_k')
         if constexpr (MID == MID_APPLY) {
-          const R s = sg[q];
-          const Z r = cf[q];
-          const Z Ep = cadd(cscale(E, s), cmul(r, O));
-          const Z Op = cadd(cmul(cconj(r), E), cscale(O, s));
+          const Z Ya = cscale(X, s1[q]);
+          const Z Yb = cscale(Xc, s2[q]);
+          const Z Ep = cscale(cadd(Ya, Yb), R(0.5));
+          const Z Op = cscale(cmulc(csub(Ya, Yb), Wk), R(0.5));
           oth[e] = mkc<R>(Ep.x - Op.y, Ep.y + Op.x);
         } else {
-          const Z Wk = cf[q];
-          const R wo = Wk.x * O.x - Wk.y * O.y;  // Re(W O)
-          sig_out[k1 * N2 + k2] = E.x * invNc;
-          rho_out[k1 * N2 + k2] = cscale(Wk, wo * invNc);
+          sa_out[k1 * N2 + k2] = X.x * invNc;
+          sb_out[k1 * N2 + k2] = Xc.x * invNc;
         }
       }
     }
@@ -435,7 +445,7 @@ __device__ bool build_precond(const DevPlan& P, const Smem<R>& sm, double ahat, 
   };
   passA_real<R, true>(P, sm, L, proE);
   if (!gsync(P, sm.red)) return false;
-  passB<R, MID_SPEC>(P, sm, nullptr, nullptr, sigG<R>(P), rhoG<R>(P), nullptr);
+  passB<R, MID_SPEC>(P, sm, nullptr, nullptr, saG<R>(P), sbG<R>(P), nullptr);
   return gsync(P, sm.red);
 }
 
@@ -497,13 +507,13 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
     }
     if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
     if (prec) {
-      passB<R, MID_APPLY>(P, sm, sigG<R>(P), rhoG<R>(P), nullptr, nullptr, nullptr);
+      passB<R, MID_APPLY>(P, sm, saG<R>(P), sbG<R>(P), nullptr, nullptr, nullptr);
       if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
       auto epi = [&](int i, R y) -> R { V.ph[i] = y; return y; };
       passCA_real<R, true>(P, sm, epi);
       if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
     }
-    passB<R, MID_APPLY>(P, sm, sigT<R>(P), rhoT<R>(P), nullptr, nullptr, nullptr);
+    passB<R, MID_APPLY>(P, sm, saT<R>(P), sbT<R>(P), nullptr, nullptr, nullptr);
     if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
     const R* ph = prec ? V.ph : V.p;
     {
@@ -534,13 +544,13 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
     }
     if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
     if (prec) {
-      passB<R, MID_APPLY>(P, sm, sigG<R>(P), rhoG<R>(P), nullptr, nullptr, nullptr);
+      passB<R, MID_APPLY>(P, sm, saG<R>(P), sbG<R>(P), nullptr, nullptr, nullptr);
       if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
       auto epi = [&](int i, R y) -> R { V.sh[i] = y; return y; };
       passCA_real<R, true>(P, sm, epi);
       if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
     }
-    passB<R, MID_APPLY>(P, sm, sigT<R>(P), rhoT<R>(P), nullptr, nullptr, nullptr);
+    passB<R, MID_APPLY>(P, sm, saT<R>(P), sbT<R>(P), nullptr, nullptr, nullptr);
     if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
     const R* sh = prec ? V.sh : V.s;
     {
@@ -619,7 +629,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_level64(LevelArgs A) {
 // Mixed level solve: FP64 defect correction u += e around an FP32
 // PBiCGSTAB for (ahat I + K A) e = r; the FP64 residual r = b - M u uses the
 // FP64 product; FP32 for the inner products and the preconditioner.
-// Stops when the last correction satisfies max|e| <= tol max|u|.
+// Stops when the last correction satisfies max|e| <= tol max|u|, or when a
+// sweep no longer halves the FP64 residual (its rounding floor).
 __global__ void __launch_bounds__(kThreads, 2) k_level_mixed(LevelArgs A) {
   const DevPlan& P = A.P;
   SmemAll S = smem_setup(P);
@@ -628,12 +639,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_level_mixed(LevelArgs A) {
   const int gstr = gridDim.x * blockDim.x;
   const double kbar = mean_kappa(P, A.kappa64, S.d.red);
   if (kbar < 0.0) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
-  if (A.precond && !build_precond<float>(P, S.f, A.ahat, kbar)) {
+  // The preconditioner is built in FP64 and rounded to FP32: built in FP32,
+  // the rounding of its first column (~1e-7 of its largest entries) would
+  // swamp its smallest eigenvalues (1/(ahat + kbar lambda_max), ~1e-8 of the
+  // largest at n = 2^17-1) and the FP32 inner solve would diverge.
+  if (A.precond && !build_precond<double>(P, S.d, A.ahat, kbar)) {
     write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0);
     return;
   }
   {
     double acc = 0.0;
+    if (A.precond)
+      for (int k = gtid; k < P.Nc; k += gstr) {
+        P.saG32[k] = (float)P.saG64[k];
+        P.sbG32[k] = (float)P.sbG64[k];
+      }
     for (int i = gtid; i < n; i += gstr) {
       const double bi = A.b[i];
       A.u[i] = 0.0;
@@ -678,7 +698,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_level_mixed(LevelArgs A) {
     if (!gsync_sum2(P, S.d.red, SL_EMAX, SL_XMAX, 3u, emax, xmax)) { status = TSFDE_ETIMEOUT; break; }
     if (!isfinite(emax) || !isfinite(xmax)) { status = TSFDE_ENONFINITE; break; }
     if (emax <= A.tol * xmax) break;
-    passB<double, MID_APPLY>(P, S.d, P.sigT64, P.rhoT64, nullptr, nullptr, nullptr);
+    passB<double, MID_APPLY>(P, S.d, P.saT64, P.sbT64, nullptr, nullptr, nullptr);
     if (!gsync(P, S.d.red)) { status = TSFDE_ETIMEOUT; break; }
     {
       double acc = 0.0;
@@ -694,10 +714,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_level_mixed(LevelArgs A) {
     }
     double rr;
     if (!gsync_sum(P, S.d.red, SL_RES, rr)) { status = TSFDE_ETIMEOUT; break; }
+    const double nr_prev = nr;
     nr = sqrt(rr);
-    relres = nr / nb;
     if (!isfinite(nr)) { status = TSFDE_ENONFINITE; break; }
-    if (nr == 0.0) break;
+    if (nr == 0.0) { relres = 0.0; break; }
+    if (nr > nr_prev) {
+      // the correction made the residual worse: take it back and stop; this
+      // is only acceptable once the residual is near its rounding floor
+      const float* e = A.k32.x;
+      for (int i = gtid; i < n; i += gstr) A.u[i] -= nr_prev * (double)e[i];
+      relres = nr_prev / nb;
+      if (relres > 1e-8) status = TSFDE_ENOCONV;
+      if (!gsync(P, S.d.red)) status = TSFDE_ETIMEOUT;
+      break;
+    }
+    relres = nr / nb;
+    // The FP64 residual has reached its rounding floor when a sweep no
+    // longer halves it; further FP32 corrections only add noise.
+    if (outer >= 2 && nr > 0.5 * nr_prev) break;
   }
   write_stat(A.stat, status, inner_total, outer, relres);
 }
@@ -717,9 +751,9 @@ __device__ void apply_kernel_body(const ApplyArgs& A, const Smem<R>& sm) {
   passA_real<R, false>(P, sm, n, pro);
   if (!gsync(P, sm.red)) goto fail;
   if (A.kind == 1)
-    passB<R, MID_APPLY>(P, sm, sigG<R>(P), rhoG<R>(P), nullptr, nullptr, nullptr);
+    passB<R, MID_APPLY>(P, sm, saG<R>(P), sbG<R>(P), nullptr, nullptr, nullptr);
   else
-    passB<R, MID_APPLY>(P, sm, sigT<R>(P), rhoT<R>(P), nullptr, nullptr, nullptr);
+    passB<R, MID_APPLY>(P, sm, saT<R>(P), sbT<R>(P), nullptr, nullptr, nullptr);
   if (!gsync(P, sm.red)) goto fail;
   {
     auto epi = [&](int i, R y) -> R {
@@ -974,15 +1008,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_apply_static(StaticApplyArgs A)
   };
   passA_real<double, true>(P, S.d, L, proE);
   if (!gsync(P, S.d.red)) goto fail;
-  passB<double, MID_SPEC>(P, S.d, nullptr, nullptr, const_cast<double*>(P.sigT64),
-                          const_cast<double2*>(P.rhoT64), nullptr);
+  passB<double, MID_SPEC>(P, S.d, nullptr, nullptr, const_cast<double*>(P.saT64),
+                          const_cast<double*>(P.sbT64), nullptr);
   if (!gsync(P, S.d.red)) goto fail;
   {
     auto pro = [&](int i) -> double { return A.v[i]; };
     passA_real<double, false>(P, S.d, n, pro);
   }
   if (!gsync(P, S.d.red)) goto fail;
-  passB<double, MID_APPLY>(P, S.d, P.sigT64, P.rhoT64, nullptr, nullptr, nullptr);
+  passB<double, MID_APPLY>(P, S.d, P.saT64, P.sbT64, nullptr, nullptr, nullptr);
   if (!gsync(P, S.d.red)) goto fail;
   {
     auto epi = [&](int i, double yv) -> double { A.y[i] = yv; return 0.0; };
@@ -1071,8 +1105,8 @@ extern "C" int tsfde_toeplitz_apply_static(double alpha, double mu, int kappa_mu
   P.part = reinterpret_cast<double*>(base + kSA_part);
   P.twL64 = reinterpret_cast<const double2*>(base + kSA_tw64);
   P.twL32 = reinterpret_cast<const float2*>(base + kSA_tw32);
-  P.sigT64 = reinterpret_cast<const double*>(base + kSA_sig);
-  P.rhoT64 = reinterpret_cast<const double2*>(base + kSA_rho);
+  P.saT64 = reinterpret_cast<const double*>(base + kSA_sig);
+  P.sbT64 = reinterpret_cast<const double*>(base + kSA_rho);
   P.S1 = reinterpret_cast<double2*>(base + kSA_S1);
   P.S2 = reinterpret_cast<double2*>(base + kSA_S2);
 

@@ -42,18 +42,19 @@ struct DevPlan {
   double* part;       // [kSlots][G] per-CTA partial sums
   const double2* twL64;  // W_L^k, k < L
   const float2* twL32;
-  // Toeplitz symbol spectrum, (k1,k2) layout of gr: sigma = (S_k+S_k')/(2Nc),
-  // rho = (S_k - S_k') W_L^k/(2Nc), k = k1 + N1 k2, k' = Nc - k
-  const double* sigT64; const double2* rhoT64;
-  const float* sigT32;  const float2* rhoT32;
+  // Toeplitz symbol spectrum S (DFT_L of the even embedding), in the (k1,k2)
+  // layout of gr and scaled by 1/Nc: sa = S_k / Nc, sb = S_{k'} / Nc with
+  // k = k1 + N1 k2 and k' = Nc - k (k' = Nc for k = 0)
+  const double* saT64; const double* sbT64;
+  const float* saT32;  const float* sbT32;
   const double* lam;       // Strang eigenvalues (n)
   const double2* chirp64;  // e^{+pi i j^2/n}, j < n
   const float2* chirp32;
   const double2* Bh64;     // spectrum of the Bluestein kernel / L, (k1,k2) layout of gc
   const float2* Bh32;
-  // per-level preconditioner spectrum (written by the build)
-  double* sigG64; double2* rhoG64;
-  float* sigG32;  float2* rhoG32;
+  // per-level preconditioner spectrum, same format (written by the build)
+  double* saG64; double* sbG64;
+  float* saG32;  float* sbG32;
   double* g64; float* g32;  // first column of the circulant inverse (n)
   double2* S1;  // work: Nfft complex (double capacity, reused as float2)
   double2* S2;
