@@ -124,7 +124,7 @@ def run_arm(torch, pkg, prob, precision, W, K, flush, stream, e2e=False):
     s.set_problem_from(prob)
     n = prob.n
     dev = torch.device("cuda")
-    tot = {"its": 0, "outer": 0, "E_active_sum": 0, "status": 0}
+    tot = {"its": 0, "outer": 0, "E_active_sum": 0, "status": 0, "fallback": 0}
     if e2e:
         kap_h = torch.from_numpy(prob.kappa0.copy()).pin_memory()
         f_h = torch.from_numpy(prob.f_at(0.0)).pin_memory()
@@ -138,7 +138,8 @@ def run_arm(torch, pkg, prob, precision, W, K, flush, stream, e2e=False):
         if first_timed[0] is not None and s.m >= first_timed[0]:
             for rec in s.level_stats(first_timed[0], s.m):
                 tot["its"] += rec["iterations"]
-                tot["outer"] += rec["outer"]
+                tot["outer"] += abs(rec["outer"])  # negative: finished by the FP64 fallback
+                tot["fallback"] += rec["outer"] < 0
                 tot["E_active_sum"] += rec["E_active"]
                 tot["status"] = tot["status"] or rec["status"]
 
@@ -275,7 +276,7 @@ def ours(args):
                        "l2": "flushed before every timed level (256 MB write outside the events)",
                        "parallelism": f"replicas x{world}"},
             "status": st_mx["status"],
-            "iterations_per_step": st_mx["its"] / K, "outer_per_step": st_mx["outer"] / K,
+            "iterations_per_step": st_mx["its"] / K, "outer_per_step": st_mx["outer"] / K, "fp64_fallback_levels": st_mx.get("fallback", 0),
             "krylov_its_per_s": world * st_mx["its"] / t_mx,
             "kernels": {"k_rhs": {"ms": rhs_ms, "bytes": rhs_bytes, "GB/s": rhs_gbs, "frac": rhs_gbs / peak},
                         "k_level_mixed": {"ms": lvl_ms, "bytes": lvl_bytes, "GB/s": lvl_gbs,

@@ -323,8 +323,8 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
   float** v32[] = {&c->k32.x, &c->k32.r, &c->k32.rh, &c->k32.p, &c->k32.v, &c->k32.s, &c->k32.t, &c->k32.ph, &c->k32.sh};
   for (float** p : v32) ok &= dalloc(c, p, n);
   ok &= dalloc(c, &c->stats, M + 1) && dalloc(c, &c->status, 1);
+  ok &= dalloc(c, &c->k64.x, n);  // FP64 correction of the mixed fallback
   if (!ok) return fail(c, TSFDE_ENOMEM, "cudaMalloc failed");
-  c->k64.x = nullptr;
 
   if ((e = upload(dtw64, tw64)) != cudaSuccess || (e = upload(dtw32, tw32)) != cudaSuccess ||
       (e = upload(dsa64, sa)) != cudaSuccess || (e = upload(dsb64, sb)) != cudaSuccess ||

@@ -119,6 +119,17 @@ __device__ __forceinline__ bool gsync_sum2(const DevPlan& P, double* red, int s0
   return ok;
 }
 
+__device__ __forceinline__ bool gsync_sum3(const DevPlan& P, double* red, int s0, int s1, int s2,
+                                           unsigned maxmask, double& o0, double& o1, double& o2) {
+  const int sl[3] = {s0, s1, s2};
+  double o[3];
+  const bool ok = grid_sync_red(P.bar, P.timeout, P.part, P.G, 3, sl, maxmask, o, red);
+  o0 = o[0];
+  o1 = o[1];
+  o2 = o[2];
+  return ok;
+}
+
 // ------------------------------------------------------------------ passes
 // Each thread handles at most kPre elements of a work item (tile or row
 // pair); their store twiddles and spectral coefficients are loaded into
@@ -626,11 +637,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_level64(LevelArgs A) {
   write_stat(A.stat, r.status, r.iters, 0, r.relres);
 }
 
-// Mixed level solve: FP64 defect correction u += e around an FP32
-// PBiCGSTAB for (ahat I + K A) e = r; the FP64 residual r = b - M u uses the
-// FP64 product; FP32 for the inner products and the preconditioner.
-// Stops when the last correction satisfies max|e| <= tol max|u|, or when a
-// sweep no longer halves the FP64 residual (its rounding floor).
+// Mixed level solve.  FP64 refinement around an FP32 PBiCGSTAB: each sweep
+// solves (ahat I + K A) e = r / ||r|| in FP32 (at most inner_max_it
+// iterations), forms w = M e in FP64 and updates u += theta e,
+// r -= theta w with theta = 1, or the minimal-residual
+// theta = (r, w)/(w, w) when the full step would raise ||r||, so the FP64
+// residual never grows.  Stops when the last step satisfies
+// max|theta e| <= tol max|u|, or when a sweep no longer halves ||r|| with
+// ||r||/||b|| <= 1e-9 (its rounding floor at large n).  After three sweeps
+// without progress above that, or at max_outer, the level is finished by
+// FP64 PBiCGSTAB on the remaining residual, so a level never returns an
+// unconverged answer.
 __global__ void __launch_bounds__(kThreads, 2) k_level_mixed(LevelArgs A) {
   const DevPlan& P = A.P;
   SmemAll S = smem_setup(P);
@@ -639,10 +656,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_level_mixed(LevelArgs A) {
   const int gstr = gridDim.x * blockDim.x;
   const double kbar = mean_kappa(P, A.kappa64, S.d.red);
   if (kbar < 0.0) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
-  // The preconditioner is built in FP64 and rounded to FP32: built in FP32,
-  // the rounding of its first column (~1e-7 of its largest entries) would
-  // swamp its smallest eigenvalues (1/(ahat + kbar lambda_max), ~1e-8 of the
-  // largest at n = 2^17-1) and the FP32 inner solve would diverge.
+  // The preconditioner is built in FP64 and rounded to FP32; building it in
+  // FP32 would bury its smallest eigenvalues (1/(ahat + kbar lambda_max),
+  // ~1e-8 of the largest at n = 2^17-1) under rounding.
   if (A.precond && !build_precond<double>(P, S.d, A.ahat, kbar)) {
     write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0);
     return;
@@ -668,9 +684,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_level_mixed(LevelArgs A) {
   if (bb == 0.0) { write_stat(A.stat, TSFDE_OK, 0, 0, 0.0); return; }
   const double nb = sqrt(bb);
   double nr = nb, relres = 1.0;
-  int inner_total = 0, outer = 0, status = TSFDE_OK;
+  int inner_total = 0, outer = 0, status = TSFDE_OK, stalls = 0;
+  bool fallback = false;
+  double* w = A.k64.v;  // FP64 scratch for M e
+  const float* e = A.k32.x;
   for (;;) {
-    if (outer >= A.max_outer) { status = TSFDE_ENOCONV; break; }
+    if (outer >= A.max_outer) { fallback = true; break; }
     const double sc = 1.0 / nr;
     auto binit = [&](int i) -> float { return (float)(A.r64[i] * sc); };
     SolveRes ir = bicgstab<float>(P, S.f, A.k32, A.kappa32, A.ahat, A.precond != 0,
@@ -678,60 +697,81 @@ __global__ void __launch_bounds__(kThreads, 2) k_level_mixed(LevelArgs A) {
     inner_total += ir.iters;
     if (ir.status == TSFDE_ETIMEOUT) { status = ir.status; break; }
     ++outer;
-    // u += nr * e, then r = b - (ahat u + kappa .* A u) in FP64
-    {
-      double emax = 0.0, xmax = 0.0;
-      const float* e = A.k32.x;
-      auto pro = [&](int i) -> double {
-        const double ei = nr * (double)e[i];
-        const double xi = A.u[i] + ei;
-        A.u[i] = xi;
-        emax = fmax(emax, fabs(ei));
-        xmax = fmax(xmax, fabs(xi));
-        return xi;
-      };
-      passA_real<double, false>(P, S.d, n, pro);
-      put_partial(P, SL_EMAX, block_max(emax, S.d.red));
-      put_partial(P, SL_XMAX, block_max(xmax, S.d.red));
-    }
-    double emax, xmax;
-    if (!gsync_sum2(P, S.d.red, SL_EMAX, SL_XMAX, 3u, emax, xmax)) { status = TSFDE_ETIMEOUT; break; }
-    if (!isfinite(emax) || !isfinite(xmax)) { status = TSFDE_ENONFINITE; break; }
-    if (emax <= A.tol * xmax) break;
+    // w = M (nr e) in FP64
+    const double ah = A.ahat;
+    auto pro = [&](int i) -> double { return nr * (double)e[i]; };
+    passA_real<double, false>(P, S.d, n, pro);
+    if (!gsync(P, S.d.red)) { status = TSFDE_ETIMEOUT; break; }
     passB<double, MID_APPLY>(P, S.d, P.saT64, P.sbT64, nullptr, nullptr, nullptr);
     if (!gsync(P, S.d.red)) { status = TSFDE_ETIMEOUT; break; }
     {
-      double acc = 0.0;
-      const double ah = A.ahat;
+      double rw = 0.0, ww = 0.0;
       auto epi = [&](int i, double y) -> double {
-        const double ri = A.b[i] - ah * A.u[i] - A.kappa64[i] * y;
-        A.r64[i] = ri;
-        acc += ri * ri;
+        const double wi = ah * nr * (double)e[i] + A.kappa64[i] * y;
+        w[i] = wi;
+        rw += A.r64[i] * wi;
+        ww += wi * wi;
         return 0.0;
       };
       passCA_real<double, false>(P, S.d, epi);
-      put_partial(P, SL_RES, block_sum(acc, S.d.red));
+      put_partial(P, SL_RV, block_sum(rw, S.d.red));
+      put_partial(P, SL_TT, block_sum(ww, S.d.red));
     }
-    double rr;
-    if (!gsync_sum(P, S.d.red, SL_RES, rr)) { status = TSFDE_ETIMEOUT; break; }
-    const double nr_prev = nr;
-    nr = sqrt(rr);
-    if (!isfinite(nr)) { status = TSFDE_ENONFINITE; break; }
-    if (nr == 0.0) { relres = 0.0; break; }
-    if (nr > nr_prev) {
-      // the correction made the residual worse: take it back and stop; this
-      // is only acceptable once the residual is near its rounding floor
-      const float* e = A.k32.x;
-      for (int i = gtid; i < n; i += gstr) A.u[i] -= nr_prev * (double)e[i];
-      relres = nr_prev / nb;
-      if (relres > 1e-8) status = TSFDE_ENOCONV;
-      if (!gsync(P, S.d.red)) status = TSFDE_ETIMEOUT;
+    double rw, ww;
+    if (!gsync_sum2(P, S.d.red, SL_RV, SL_TT, 0u, rw, ww)) { status = TSFDE_ETIMEOUT; break; }
+    // full step unless it would raise ||r||: ||r - w||^2 = ||r||^2 - 2 (r,w) + (w,w)
+    double theta = 1.0;
+    if (ww - 2.0 * rw > 0.0) theta = (ww > 0.0) ? rw / ww : 0.0;
+    if (!isfinite(theta) || !(theta > 0.0)) { fallback = true; break; }
+    {
+      double rr = 0.0, emax = 0.0, xmax = 0.0;
+      const double step = theta * nr;
+      for (int i = gtid; i < n; i += gstr) {
+        const double di = step * (double)e[i];
+        const double xi = A.u[i] + di;
+        A.u[i] = xi;
+        const double ri = A.r64[i] - theta * w[i];
+        A.r64[i] = ri;
+        rr += ri * ri;
+        emax = fmax(emax, fabs(di));
+        xmax = fmax(xmax, fabs(xi));
+      }
+      put_partial(P, SL_RES, block_sum(rr, S.d.red));
+      put_partial(P, SL_EMAX, block_max(emax, S.d.red));
+      put_partial(P, SL_XMAX, block_max(xmax, S.d.red));
+    }
+    double rr, emax, xmax;
+    if (!gsync_sum3(P, S.d.red, SL_RES, SL_EMAX, SL_XMAX, 6u, rr, emax, xmax)) {
+      status = TSFDE_ETIMEOUT;
       break;
     }
+    const double nr_prev = nr;
+    nr = sqrt(rr);
+    if (!isfinite(nr) || !isfinite(xmax)) { status = TSFDE_ENONFINITE; break; }
     relres = nr / nb;
-    // The FP64 residual has reached its rounding floor when a sweep no
-    // longer halves it; further FP32 corrections only add noise.
-    if (outer >= 2 && nr > 0.5 * nr_prev) break;
+    if (nr == 0.0 || emax <= A.tol * xmax) break;
+    if (outer >= 2 && nr > 0.5 * nr_prev) {
+      if (relres <= 1e-9) break;  // rounding floor of the FP64 residual
+      if (++stalls >= 3) { fallback = true; break; }
+    } else {
+      stalls = 0;
+    }
+  }
+  if (fallback && status == TSFDE_OK) {
+    // finish in FP64: solve M d = r to the requested overall tolerance
+    KVecs<double> V = A.k64;
+    auto binit = [&](int i) -> double { return A.r64[i]; };
+    const double tol_d = fmax(A.tol * nb / nr, 1e-14);
+    SolveRes fr = bicgstab<double>(P, S.d, V, A.kappa64, A.ahat, A.precond != 0, tol_d,
+                                   A.max_it, binit);
+    if (fr.status == TSFDE_OK) {
+      for (int i = gtid; i < n; i += gstr) A.u[i] += V.x[i];
+      relres = fr.relres * nr / nb;
+      if (!gsync(P, S.d.red)) fr.status = TSFDE_ETIMEOUT;
+    }
+    status = fr.status;
+    inner_total += fr.iters;
+    outer = -outer;  // a negative count marks a level finished in FP64
   }
   write_stat(A.stat, status, inner_total, outer, relres);
 }
