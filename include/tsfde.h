@@ -51,6 +51,15 @@ typedef enum tsfde_status {
 
 enum { TSFDE_FP64 = 0, TSFDE_MIXED = 1 };       /* tsfde_opts.precision */
 enum { TSFDE_STRANG = 0, TSFDE_PRECOND_NONE = 1 }; /* tsfde_opts.precond */
+/* tsfde_opts.engine: how a mixed level solve runs its FP32 inner solves.
+ * GRID: spread over the whole cooperative grid (grid barriers between the
+ * FFT passes).  CLUSTER: on one thread-block cluster of up to 16 CTAs that
+ * keeps each FFT in distributed shared memory (cluster barriers), while the
+ * grid runs the FP64 parts.  AUTO takes GRID for a single problem: at the
+ * sizes where the cluster engine fits (n <= 2^17 - 1) one cluster of 16 SMs
+ * has less FFT throughput than the whole grid loses to grid barriers.
+ * FP64 level solves always use the grid. */
+enum { TSFDE_ENGINE_AUTO = 0, TSFDE_ENGINE_GRID = 1, TSFDE_ENGINE_CLUSTER = 2 };
 
 typedef struct tsfde_opts {
   double mu;            /* splitting parameter of Eq. (2.11), mu in (alpha,2];
@@ -83,6 +92,8 @@ typedef struct tsfde_opts {
                            value makes every barrier give up and the call
                            return TSFDE_ETIMEOUT: used to test that path.  */
   void* stream;         /* cudaStream_t; NULL = default stream              */
+  int engine;           /* TSFDE_ENGINE_* (default AUTO); CLUSTER where it
+                           cannot run fails tsfde_setup with TSFDE_ENOTSUP  */
 } tsfde_opts;
 
 typedef struct tsfde_step_info {
@@ -181,6 +192,10 @@ int tsfde_get_times(const tsfde_ctx* ctx, double* t);
 
 /* Copy the first column t_0..t_{n-1} of A (Eq. (3.16x)) to host. */
 int tsfde_get_symbol(const tsfde_ctx* ctx, double* t);
+
+/* Engine the context's mixed level solves use: TSFDE_ENGINE_GRID or
+ * TSFDE_ENGINE_CLUSTER (never AUTO); -1 if ctx is NULL. */
+int tsfde_get_engine(const tsfde_ctx* ctx);
 
 /* Device time of the kernels launched since the previous call (opts.profile
  * must be 1).  Synchronises the stream and resets the counters. */

@@ -24,6 +24,7 @@ TSFDE_OK, TSFDE_EINVAL, TSFDE_ENOMEM, TSFDE_ECUDA, TSFDE_ENOCONV = 0, 1, 2, 3, 4
 TSFDE_EBREAKDOWN, TSFDE_ETIMEOUT, TSFDE_ESTATE, TSFDE_ENONFINITE, TSFDE_ENOTSUP = 5, 6, 7, 8, 9
 TSFDE_FP64, TSFDE_MIXED = 0, 1
 TSFDE_STRANG, TSFDE_PRECOND_NONE = 0, 1
+TSFDE_ENGINE_AUTO, TSFDE_ENGINE_GRID, TSFDE_ENGINE_CLUSTER = 0, 1, 2
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -35,7 +36,8 @@ class tsfde_opts(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("inner_max_it", ctypes.c_int),
                 ("soe_E", ctypes.c_int), ("soe_s", _dp), ("soe_w", _dp), ("profile", ctypes.c_int),
-                ("barrier_timeout_cycles", ctypes.c_longlong), ("stream", ctypes.c_void_p)]
+                ("barrier_timeout_cycles", ctypes.c_longlong), ("stream", ctypes.c_void_p),
+                ("engine", ctypes.c_int)]
 
 
 class tsfde_step_info(ctypes.Structure):
@@ -77,6 +79,7 @@ _SIGNATURES = [
     ("tsfde_get_times", ctypes.c_int, [_V, _dp]),
     ("tsfde_get_symbol", ctypes.c_int, [_V, _dp]),
     ("tsfde_get_timing", ctypes.c_int, [_V, ctypes.POINTER(tsfde_timing)]),
+    ("tsfde_get_engine", ctypes.c_int, [_V]),
     ("tsfde_get_level_stats", ctypes.c_int, [_V, ctypes.c_int64, ctypes.c_int64,
                                              ctypes.POINTER(tsfde_step_info)]),
     ("tsfde_get_solution", ctypes.c_int, [_V, _V]),
@@ -158,9 +161,11 @@ class Solver:
     def __init__(self, alpha, gamma, l, T, n, M, r, soe_tol=1e-12, *, precision="fp64",
                  precond="strang", krylov_tol=1e-12, max_it=2000, inner_tol=1e-2,
                  max_outer=60, inner_max_it=40, mu=None, kappa_mu=None, soe=None, barrier_timeout_cycles=0,
-                 profile=False, stream=None):
+                 profile=False, stream=None, engine="auto"):
         lib = load_library()
         o = default_opts()
+        o.engine = {"auto": TSFDE_ENGINE_AUTO, "grid": TSFDE_ENGINE_GRID,
+                    "cluster": TSFDE_ENGINE_CLUSTER}[engine]
         o.krylov_tol = krylov_tol
         o.max_it = max_it
         o.precision = {"fp64": TSFDE_FP64, "mixed": TSFDE_MIXED}[precision]
@@ -270,6 +275,12 @@ class Solver:
         t = np.zeros(self.M + 1)
         _check(self.lib.tsfde_get_times(self.ctx, t.ctypes.data_as(_dp)), self.ctx)
         return t
+
+    @property
+    def engine(self) -> str:
+        """'grid' or 'cluster': where the mixed level solves run their FP32 inner solves."""
+        return {TSFDE_ENGINE_GRID: "grid", TSFDE_ENGINE_CLUSTER: "cluster"}[
+            self.lib.tsfde_get_engine(self.ctx)]
 
     def timing(self):
         t = tsfde_timing()

@@ -43,6 +43,7 @@ struct tsfde_ctx {
   double* r64 = nullptr;
   StepStat* stats = nullptr;
   int* status = nullptr;
+  int engine = TSFDE_ENGINE_GRID;  // engine of the mixed level solves
   // profiling: three events per level (before rhs, after rhs, after level)
   std::vector<cudaEvent_t> ev_free, ev_used;
 };
@@ -118,6 +119,7 @@ int tsfde_default_opts(tsfde_opts* o) {
   o->profile = 0;
   o->barrier_timeout_cycles = 0;
   o->stream = nullptr;
+  o->engine = TSFDE_ENGINE_AUTO;
   return TSFDE_OK;
 }
 
@@ -174,6 +176,8 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
       (!(o.inner_tol > 0.0 && o.inner_tol < 1.0) || o.max_outer < 1 || o.inner_max_it < 1))
     return fail(c, TSFDE_EINVAL, "mixed needs inner_tol in (0,1), max_outer >= 1, inner_max_it >= 1");
   if (o.barrier_timeout_cycles < 0) return fail(c, TSFDE_EINVAL, "barrier_timeout_cycles < 0");
+  if (o.engine != TSFDE_ENGINE_AUTO && o.engine != TSFDE_ENGINE_GRID && o.engine != TSFDE_ENGINE_CLUSTER)
+    return fail(c, TSFDE_EINVAL, "engine must be TSFDE_ENGINE_AUTO, _GRID or _CLUSTER");
   c->alpha = alpha; c->gamma = gamma; c->l = l; c->T = T; c->n = n; c->M = M; c->r = r;
   c->soe_tol = soe_tol; c->mu = mu; c->kappa_mu = kmu;
   c->stream = static_cast<cudaStream_t>(o.stream);
@@ -295,6 +299,22 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
   const int maxG = nsm * std::min(bps, 2);
   P.G = std::max(1, std::min(maxG, std::max(items(P.gr), items(P.gc))));
 
+  // ---- cluster engine (mixed level solves only): one cooperative launch of
+  // whole clusters; cluster 0 runs the FP32 inner solves
+  bool use_cluster = false;
+  if (o.precision == TSFDE_MIXED && o.engine == TSFDE_ENGINE_CLUSTER && cluster_geometry(P)) {
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t csmem = std::max(plan_smem_bytes(P), cluster_smem_bytes(P));
+    const int gmax = (csmem <= (size_t)optin) ? cluster_max_grid(P, csmem) : 0;
+    if (gmax >= P.cl.Q) {
+      P.cl.G = gmax;
+      use_cluster = true;
+    }
+  }
+  if (o.engine == TSFDE_ENGINE_CLUSTER && !use_cluster)
+    return fail(c, TSFDE_ENOTSUP, "cluster engine unavailable for this size or device");
+
   // ---- device allocations
   const int64_t ld = ((n + 31) / 32) * 32;
   c->ld = (int)ld;
@@ -311,17 +331,22 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
   ok &= dalloc(c, &dsaG64, Nc) && dalloc(c, &dsbG64, Nc) && dalloc(c, &dsaG32, Nc) && dalloc(c, &dsbG32, Nc);
   ok &= dalloc(c, &dg64, n) && dalloc(c, &dg32, n);
   ok &= dalloc(c, &dS1, L) && dalloc(c, &dS2, L);
-  ok &= dalloc(c, &dpart, (size_t)kSlots * P.G) && dalloc(c, &dbar, 1);
+  ok &= dalloc(c, &dpart, (size_t)kSlots * std::max(P.G, P.cl.G)) && dalloc(c, &dbar, 1);
+  float2* dspT = nullptr;
+  float2* dspG = nullptr;
+  if (use_cluster) ok &= dalloc(c, &dspT, Nc) && dalloc(c, &dspG, Nc);
   ok &= dalloc(c, &c->G, (size_t)std::max(E, 1) * ld);
   ok &= dalloc(c, &c->eps, c->eps_h.size()) && dalloc(c, &c->cw, c->cw_h.size());
   for (int q = 0; q < 3; ++q) ok &= dalloc(c, &c->u[q], n);
-  ok &= dalloc(c, &c->b, n) && dalloc(c, &c->kappa64, n) && dalloc(c, &c->kappa32, n);
+  // FP32 vectors: length ld (even, zero-padded) -- the cluster engine moves
+  // entries in aligned pairs
+  ok &= dalloc(c, &c->b, n) && dalloc(c, &c->kappa64, n) && dalloc(c, &c->kappa32, ld);
   ok &= dalloc(c, &c->phi, n) && dalloc(c, &c->kap0, n) && dalloc(c, &c->kap1d, n);
   ok &= dalloc(c, &c->F, 4 * n) && dalloc(c, &c->r64, n);
   double** v64[] = {&c->k64.r, &c->k64.rh, &c->k64.p, &c->k64.v, &c->k64.s, &c->k64.t, &c->k64.ph, &c->k64.sh};
   for (double** p : v64) ok &= dalloc(c, p, n);
   float** v32[] = {&c->k32.x, &c->k32.r, &c->k32.rh, &c->k32.p, &c->k32.v, &c->k32.s, &c->k32.t, &c->k32.ph, &c->k32.sh};
-  for (float** p : v32) ok &= dalloc(c, p, n);
+  for (float** p : v32) ok &= dalloc(c, p, ld);
   ok &= dalloc(c, &c->stats, M + 1) && dalloc(c, &c->status, 1);
   ok &= dalloc(c, &c->k64.x, n);  // FP64 correction of the mixed fallback
   if (!ok) return fail(c, TSFDE_ENOMEM, "cudaMalloc failed");
@@ -337,12 +362,46 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
   if ((e = cudaMemset(c->G, 0, sizeof(double) * (size_t)std::max(E, 1) * ld)) != cudaSuccess)
     return cuda_fail(c, e, "cudaMemset");
   if ((e = cudaMemset(c->stats, 0, sizeof(StepStat) * (M + 1))) != cudaSuccess) return cuda_fail(c, e, "cudaMemset");
+  for (float* p : {c->kappa32, c->k32.x, c->k32.r, c->k32.rh, c->k32.p, c->k32.v, c->k32.s, c->k32.t,
+                   c->k32.ph, c->k32.sh})
+    if ((e = cudaMemset(p, 0, sizeof(float) * ld)) != cudaSuccess) return cuda_fail(c, e, "cudaMemset");
   P.bar = dbar; P.part = dpart;
   P.twL64 = dtw64; P.twL32 = dtw32;
   P.saT64 = dsa64; P.sbT64 = dsb64; P.saT32 = dsa32; P.sbT32 = dsb32;
   P.lam = dlam; P.chirp64 = dch64; P.chirp32 = dch32; P.Bh64 = dBh64; P.Bh32 = dBh32;
   P.saG64 = dsaG64; P.sbG64 = dsbG64; P.saG32 = dsaG32; P.sbG32 = dsbG32;
   P.g64 = dg64; P.g32 = dg32; P.S1 = dS1; P.S2 = dS2;
+  if (use_cluster) {
+    // Toeplitz spectrum in the cluster engine's row-pass order
+    const CGeo& g = P.cl;
+    std::vector<float2> spT(Nc);
+    for (int k1 = 0; k1 < N1; ++k1) {
+      const int h = N1 / 2;
+      const int u = (k1 == 0 || k1 == h) ? 0 : (k1 < h ? k1 : N1 - k1);
+      const int b = (k1 == 0) ? 0 : (k1 == h ? 1 : (k1 < h ? 0 : 1));
+      const int q = u / g.U, slot = 2 * (u % g.U) + b;
+      for (int k2 = 0; k2 < N2; ++k2)
+        spT[(size_t)q * g.nbuf + (size_t)k2 * g.Bq + slot] =
+            make_float2(sa32[k1 * N2 + k2], sb32[k1 * N2 + k2]);
+    }
+    if ((e = upload(dspT, spT)) != cudaSuccess) return cuda_fail(c, e, "upload");
+    P.spT_cl = dspT;
+    P.spG_cl = dspG;
+    // the launch itself must be accepted (cooperative launch of clusters)
+    LevelArgs probe{};
+    probe.P = P;
+    probe.P.G = P.cl.G;
+    probe.probe = 1;
+    e = launch_level_cluster(probe, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (o.engine == TSFDE_ENGINE_CLUSTER)
+        return fail(c, TSFDE_ENOTSUP, std::string("cluster engine launch refused: ") + cudaGetErrorString(e));
+      use_cluster = false;
+    }
+  }
+  c->engine = use_cluster ? TSFDE_ENGINE_CLUSTER : TSFDE_ENGINE_GRID;
   return TSFDE_OK;
 }
 
@@ -446,6 +505,14 @@ static cudaError_t record(tsfde_ctx* c) {
   return cudaEventRecord(e, c->stream);
 }
 
+static cudaError_t launch_level_ctx(tsfde_ctx* c, LevelArgs& A) {
+  if (c->opts.precision == TSFDE_MIXED && c->engine == TSFDE_ENGINE_CLUSTER) {
+    A.P.G = A.P.cl.G;
+    return launch_level_cluster(A, c->stream);
+  }
+  return launch_level(A, c->opts.precision == TSFDE_MIXED, c->stream);
+}
+
 // Enqueue level m = c->m + 1.
 static int enqueue_level(tsfde_ctx* c, const double* kappa_m, const double* f_m, double* rhs_out) {
   const int64_t m = c->m + 1;
@@ -476,7 +543,7 @@ static int enqueue_level(tsfde_ctx* c, const double* kappa_m, const double* f_m,
   if (e == cudaSuccess) e = record(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "rhs kernel");
   LevelArgs A = level_args(c, c->ahat[m], c->b, c->u[m % 3], c->stats + m);
-  e = launch_level(A, c->opts.precision == TSFDE_MIXED, c->stream);
+  e = launch_level_ctx(c, A);
   if (e == cudaSuccess) e = record(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "level kernel");
   c->m = m;
@@ -661,6 +728,8 @@ int tsfde_precond_apply(tsfde_ctx* c, double a, double kbar, const double* v, do
   return run_apply(c, 1, a, kbar, nullptr, v, z, precision);
 }
 
+int tsfde_get_engine(const tsfde_ctx* c) { return c ? c->engine : -1; }
+
 int tsfde_linear_solve(tsfde_ctx* c, double a, const double* kappa, const double* b, double* x,
                        tsfde_step_info* info) {
   if (!c || !kappa || !b || !x) return TSFDE_EINVAL;
@@ -669,7 +738,7 @@ int tsfde_linear_solve(tsfde_ctx* c, double a, const double* kappa, const double
   if (e != cudaSuccess) return cuda_fail(c, e, "convert kernel");
   LevelArgs A = level_args(c, a, b, x, c->stats);
   A.kappa64 = c->kappa64;
-  e = launch_level(A, c->opts.precision == TSFDE_MIXED, c->stream);
+  e = launch_level_ctx(c, A);
   if (e != cudaSuccess) return cuda_fail(c, e, "level kernel");
   StepStat s{};
   if ((e = cudaMemcpyAsync(&s, c->stats, sizeof(s), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||

@@ -124,6 +124,170 @@ __device__ __forceinline__ cplx<R>* fft_batch(cplx<R>* a, cplx<R>* b, int N, int
   return in;
 }
 
+// ------------------------------------------- register-blocked FFT stages
+// W_16^m = e^{-2 pi i m/16}; m is a compile-time constant after unrolling,
+// so the switch folds to literals (cos/sin of multiples of pi/8).
+template <typename R> __device__ __forceinline__ cplx<R> w16(int m) {
+  const R c1 = R(0.92387953251128674), s1 = R(0.38268343236508977), c2 = R(0.70710678118654752);
+  switch (m & 15) {
+    case 0: return mkc<R>(R(1), R(0));
+    case 1: return mkc<R>(c1, -s1);
+    case 2: return mkc<R>(c2, -c2);
+    case 3: return mkc<R>(s1, -c1);
+    case 4: return mkc<R>(R(0), R(-1));
+    case 5: return mkc<R>(-s1, -c1);
+    case 6: return mkc<R>(-c2, -c2);
+    case 7: return mkc<R>(-c1, -s1);
+    case 8: return mkc<R>(R(-1), R(0));
+    case 9: return mkc<R>(-c1, s1);
+    case 10: return mkc<R>(-c2, c2);
+    case 11: return mkc<R>(-s1, c1);
+    case 12: return mkc<R>(R(0), R(1));
+    case 13: return mkc<R>(s1, c1);
+    case 14: return mkc<R>(c2, c2);
+    default: return mkc<R>(c1, s1);
+  }
+}
+
+// x * W_16^m (conjugate twiddle when INV), with the trivial multipliers
+// (1, -1, -i, +i) done as swaps.
+template <typename R, bool INV> __device__ __forceinline__ cplx<R> mul_w16(cplx<R> x, int m) {
+  m &= 15;
+  if (INV) m = (16 - m) & 15;
+  if (m == 0) return x;
+  if (m == 8) return mkc<R>(-x.x, -x.y);
+  if (m == 4) return mkc<R>(x.y, -x.x);
+  if (m == 12) return mkc<R>(-x.y, x.x);
+  return cmul(x, w16<R>(m));
+}
+
+// In-register DFT of RAD (2..16, power of two) points in natural order:
+// Stockham radix-2 steps over the register array, fully unrolled.
+template <typename R, int RAD, bool INV> __device__ __forceinline__ void dft_reg(cplx<R>* v) {
+  typedef cplx<R> Z;
+  Z a[RAD], b[RAD];
+#pragma unroll
+  for (int r = 0; r < RAD; ++r) a[r] = v[r];
+#pragma unroll
+  for (int ns = 1; ns < RAD; ns <<= 1) {
+#pragma unroll
+    for (int j = 0; j < RAD / 2; ++j) {
+      const int k = j & (ns - 1);
+      const Z x0 = a[j];
+      const Z x1 = mul_w16<R, INV>(a[j + RAD / 2], k * (16 / (2 * ns)));
+      const int base = ((j - k) << 1) + k;
+      b[base] = cadd(x0, x1);
+      b[base + ns] = csub(x0, x1);
+    }
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) a[r] = b[r];
+  }
+#pragma unroll
+  for (int r = 0; r < RAD; ++r) v[r] = a[r];
+}
+
+// Accessors of a batch held in shared memory with layout [k][b].
+template <typename R> struct BufIn {
+  const cplx<R>* p;
+  int lgB;
+  __device__ __forceinline__ cplx<R> operator()(int k, int b) const { return p[(k << lgB) + b]; }
+};
+template <typename R> struct BufOut {
+  cplx<R>* p;
+  int lgB;
+  __device__ __forceinline__ void operator()(int k, int b, cplx<R> z) const { p[(k << lgB) + b] = z; }
+};
+
+// One radix-RAD Stockham stage over B = 2^lgB sequences of length N; Ns is
+// the length of the sub-transforms already done.  in(k, b) fetches element k
+// of sequence b, out(k, b, z) stores it; each is called once per element.
+// tw[k] = e^{-2 pi i k/T}, T >= N a power of two.
+template <typename R, bool INV, int RAD, class In, class Out>
+__device__ __forceinline__ void fft_stage_f(In& in, Out& out, int N, int Ns, int lgB,
+                                            const cplx<R>* __restrict__ tw, int T) {
+  typedef cplx<R> Z;
+  const int Q = N / RAD;
+  const int B = 1 << lgB;
+  const int total = Q << lgB;
+  const int st = T / (Ns * RAD);
+#pragma unroll 1
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int bb = t & (B - 1);
+    const int j = t >> lgB;
+    const int k = j & (Ns - 1);
+    Z v[RAD];
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) v[r] = in(j + r * Q, bb);
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) {
+        Z w = tw[r * k * st];
+        if (INV) w = cconj(w);
+        v[r] = cmul(v[r], w);
+      }
+    }
+    dft_reg<R, RAD, INV>(v);
+    const int base = (j - k) * RAD + k;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) out(base + r * Ns, bb, v[r]);
+  }
+}
+
+template <typename R, bool INV, class In, class Out>
+__device__ __forceinline__ void fft_stage_any(int rad, In& in, Out& out, int N, int Ns, int lgB,
+                                              const cplx<R>* __restrict__ tw, int T) {
+  switch (rad) {
+    case 16: fft_stage_f<R, INV, 16>(in, out, N, Ns, lgB, tw, T); break;
+    case 8: fft_stage_f<R, INV, 8>(in, out, N, Ns, lgB, tw, T); break;
+    case 4: fft_stage_f<R, INV, 4>(in, out, N, Ns, lgB, tw, T); break;
+    default: fft_stage_f<R, INV, 2>(in, out, N, Ns, lgB, tw, T); break;
+  }
+}
+
+// Number of stages fft_pipe takes for a length-2^lgN transform.
+__host__ __device__ __forceinline__ int pipe_stages(int lgN) { return (lgN + 3) >> 2; }
+
+// Batched FFT of length N = 2^lgN (>= 2) in radix-16 Stockham stages, the
+// last one of radix 2^(lgN mod 4) when 4 does not divide lgN.  The first
+// stage reads through ld, the last writes through st, and the stages in
+// between alternate between shared buffers first, second, first, ... (each
+// N << lgB elements).  ld must not read `first`, and st must not write the
+// buffer the last stage reads (stage s >= 1 writes `first` for odd s).
+// Ends with __syncthreads().
+template <typename R, bool INV, class Ld, class St>
+__device__ __forceinline__ void fft_pipe(int lgN, int lgB, Ld& ld, St& st, cplx<R>* first,
+                                         cplx<R>* second, const cplx<R>* __restrict__ tw, int T) {
+  const int N = 1 << lgN;
+  const int ns = pipe_stages(lgN);
+  if (ns == 1) {
+    fft_stage_any<R, INV>(N, ld, st, N, 1, lgB, tw, T);
+    __syncthreads();
+    return;
+  }
+  {
+    BufOut<R> o{first, lgB};
+    fft_stage_f<R, INV, 16>(ld, o, N, 1, lgB, tw, T);
+    __syncthreads();
+  }
+  cplx<R>* cur = first;
+  cplx<R>* nxt = second;
+  int Ns = 16;
+#pragma unroll 1
+  for (int s = 1; s < ns - 1; ++s) {
+    BufIn<R> i{cur, lgB};
+    BufOut<R> o{nxt, lgB};
+    fft_stage_f<R, INV, 16>(i, o, N, Ns, lgB, tw, T);
+    __syncthreads();
+    cplx<R>* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+    Ns <<= 4;
+  }
+  BufIn<R> i{cur, lgB};
+  fft_stage_any<R, INV>(N / Ns, i, st, N, Ns, lgB, tw, T);
+  __syncthreads();
+}
+
 // ------------------------------------------------------------ reductions
 // Block sum of one double per thread; result valid in every thread.
 // red: 33 doubles of shared scratch.  Fixed order -> deterministic.

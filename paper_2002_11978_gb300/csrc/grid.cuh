@@ -1,0 +1,757 @@
+// grid.cuh -- device code of the grid-wide (cooperative) FIDS solver, shared
+// by the grid engine and the cluster engine: the three-pass zero-padded FFT
+// products (Sec. 4.1), the Strang preconditioner build, PBiCGSTAB on the
+// whole grid, and the mixed-precision refinement loop around an inner solver.
+//
+// Toeplitz and circulant products use a zero-padded real FFT of length L
+// computed as a complex FFT of length Nc = L/2 in three passes (column FFTs,
+// paired row FFTs with the spectral product in the middle, inverse column
+// FFTs).  The inverse column pass of one product and the forward column pass
+// of the next product share a CTA tile, so a product that feeds another costs
+// two grid barriers.  Grid barriers are bounded (dev.cuh); every kernel
+// returns a status instead of hanging or trapping.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "../../include/tsfde.h"
+#include "dev.cuh"
+#include "plan.h"
+
+namespace tsfde {
+
+constexpr int kThreads = 256;
+
+// partial-sum slots
+enum {
+  SL_BB = 0, SL_RV = 1, SL_TS = 2, SL_TT = 3, SL_RR0 = 4, SL_RR = 5,
+  SL_EMAX = 6, SL_XMAX = 7, SL_RES = 8, SL_KAP = 9
+};
+
+template <typename R> struct Smem {
+  cplx<R>* tw;  // W_T^k, k < T
+  cplx<R>* bA;  // work buffers (W complex each)
+  cplx<R>* bB;
+  double* red;  // 33 doubles
+};
+
+template <typename R> __device__ __forceinline__ const cplx<R>* twL(const DevPlan& P) {
+  if constexpr (sizeof(R) == 8) return P.twL64; else return P.twL32;
+}
+template <typename R> __device__ __forceinline__ int lgct(const Geo& g) {
+  if constexpr (sizeof(R) == 8) return g.lgct64; else return g.lgct32;
+}
+template <typename R> __device__ __forceinline__ const R* saT(const DevPlan& P) {
+  if constexpr (sizeof(R) == 8) return P.saT64; else return P.saT32;
+}
+template <typename R> __device__ __forceinline__ const R* sbT(const DevPlan& P) {
+  if constexpr (sizeof(R) == 8) return P.sbT64; else return P.sbT32;
+}
+template <typename R> __device__ __forceinline__ R* saG(const DevPlan& P) {
+  if constexpr (sizeof(R) == 8) return P.saG64; else return P.saG32;
+}
+template <typename R> __device__ __forceinline__ R* sbG(const DevPlan& P) {
+  if constexpr (sizeof(R) == 8) return P.sbG64; else return P.sbG32;
+}
+template <typename R> __device__ __forceinline__ const cplx<R>* chirp(const DevPlan& P) {
+  if constexpr (sizeof(R) == 8) return P.chirp64; else return P.chirp32;
+}
+template <typename R> __device__ __forceinline__ const cplx<R>* Bh(const DevPlan& P) {
+  if constexpr (sizeof(R) == 8) return P.Bh64; else return P.Bh32;
+}
+template <typename R> __device__ __forceinline__ R* gcol(const DevPlan& P) {
+  if constexpr (sizeof(R) == 8) return P.g64; else return P.g32;
+}
+
+struct SmemAll {
+  Smem<double> d;
+  Smem<float> f;
+};
+
+__device__ __forceinline__ SmemAll smem_setup(const DevPlan& P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  char* base = reinterpret_cast<char*>(smem_raw);
+  double2* tw64 = reinterpret_cast<double2*>(base);
+  float2* tw32 = reinterpret_cast<float2*>(base + (size_t)P.T * sizeof(double2));
+  char* wbase = base + (size_t)P.T * (sizeof(double2) + sizeof(float2));
+  double2* bA = reinterpret_cast<double2*>(wbase);
+  double2* bB = bA + P.W;
+  double* red = reinterpret_cast<double*>(bB + P.W);
+  const int stride = P.L / P.T;
+  for (int k = threadIdx.x; k < P.T; k += blockDim.x) {
+    tw64[k] = P.twL64[k * stride];
+    tw32[k] = P.twL32[k * stride];
+  }
+  __syncthreads();
+  SmemAll s;
+  s.d.tw = tw64; s.d.bA = bA; s.d.bB = bB; s.d.red = red;
+  s.f.tw = tw32; s.f.bA = reinterpret_cast<float2*>(bA); s.f.bB = reinterpret_cast<float2*>(bB);
+  s.f.red = red;
+  return s;
+}
+
+__device__ __forceinline__ void put_partial(const DevPlan& P, int slot, double v) {
+  if (threadIdx.x == 0) P.part[slot * P.G + blockIdx.x] = v;
+}
+// Grid barrier; the _sum variants also return the grid-wide reduction of
+// the partial slots written before the barrier (bit-identical in all CTAs).
+__device__ __forceinline__ bool gsync(const DevPlan& P, double* red) {
+  return grid_sync_red(P.bar, P.timeout, P.part, P.G, 0, nullptr, 0u, nullptr, red);
+}
+__device__ __forceinline__ bool gsync_sum(const DevPlan& P, double* red, int s0, double& o0) {
+  const int sl[1] = {s0};
+  double o[1];
+  const bool ok = grid_sync_red(P.bar, P.timeout, P.part, P.G, 1, sl, 0u, o, red);
+  o0 = o[0];
+  return ok;
+}
+__device__ __forceinline__ bool gsync_sum2(const DevPlan& P, double* red, int s0, int s1,
+                                           unsigned maxmask, double& o0, double& o1) {
+  const int sl[2] = {s0, s1};
+  double o[2];
+  const bool ok = grid_sync_red(P.bar, P.timeout, P.part, P.G, 2, sl, maxmask, o, red);
+  o0 = o[0];
+  o1 = o[1];
+  return ok;
+}
+
+__device__ __forceinline__ bool gsync_sum3(const DevPlan& P, double* red, int s0, int s1, int s2,
+                                           unsigned maxmask, double& o0, double& o1, double& o2) {
+  const int sl[3] = {s0, s1, s2};
+  double o[3];
+  const bool ok = grid_sync_red(P.bar, P.timeout, P.part, P.G, 3, sl, maxmask, o, red);
+  o0 = o[0];
+  o1 = o[1];
+  o2 = o[2];
+  return ok;
+}
+
+// ------------------------------------------------------------------ passes
+// Each thread handles at most kPre elements of a work item (tile or row
+// pair); their store twiddles and spectral coefficients are loaded into
+// registers before the shared-memory FFT so the L2 latency overlaps it.
+constexpr int kPre = 4;  // with 256 threads: work items of <= 1024 elements (n <= 2^18)
+
+// Pass A, real input: x (length nin, zero beyond) -> z_j = x_{2j} + i x_{2j+1},
+// column FFTs over j1 (j = N2 j1 + j2), twiddle W_Nc^{j2 k1}, store
+// S1[k1*N2 + j2].  Without FULL only rows j1 < N1/2 can be non-zero
+// (nin <= L/2).
+template <typename R, bool FULL, class Pro>
+__device__ void passA_real(const DevPlan& P, const Smem<R>& sm, int nin, Pro& pro) {
+  typedef cplx<R> Z;
+  const Geo& g = P.gr;
+  const int lc = lgct<R>(g), ct = 1 << lc;
+  const int N1 = g.N1, N2 = g.N2;
+  const int ntiles = N2 >> lc;
+  const int total = N1 << lc;
+  const int rows = FULL ? N1 : (N1 >> 1);
+  const int tstride = P.L / g.Nfft;
+  Z* S1 = reinterpret_cast<Z*>(P.S1);
+  const Z* tw = twL<R>(P);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int c0 = tile << lc;
+    Z wp[kPre];
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) {
+      const int e = threadIdx.x + q * blockDim.x;
+      if (e < total) {
+        const int k1 = e >> lc, j2 = c0 + (e & (ct - 1));
+        wp[q] = tw[((j2 * k1) & (g.Nfft - 1)) * tstride];
+      }
+    }
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+      const int j1 = e >> lc, c = e & (ct - 1);
+      Z v = mkc<R>(R(0), R(0));
+      if (j1 < rows) {
+        const int i0 = 2 * (N2 * j1 + c0 + c);
+        const R x0 = (i0 < nin) ? pro(i0) : R(0);
+        const R x1 = (i0 + 1 < nin) ? pro(i0 + 1) : R(0);
+        v = mkc<R>(x0, x1);
+      }
+      sm.bA[e] = v;
+    }
+    __syncthreads();
+    const Z* res = fft_batch<R, false>(sm.bA, sm.bB, N1, lc, sm.tw, P.T);
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) {
+      const int e = threadIdx.x + q * blockDim.x;
+      if (e < total) S1[(e >> lc) * N2 + c0 + (e & (ct - 1))] = cmul(res[e], wp[q]);
+    }
+    __syncthreads();
+  }
+}
+
+// Pass A, complex input a_j (j < n, n <= L/2), geometry gc (Nfft = L).
+template <typename R, class Pro>
+__device__ void passA_cplx(const DevPlan& P, const Smem<R>& sm, Pro& pro) {
+  typedef cplx<R> Z;
+  const Geo& g = P.gc;
+  const int lc = lgct<R>(g), ct = 1 << lc;
+  const int N1 = g.N1, N2 = g.N2;
+  const int ntiles = N2 >> lc;
+  const int total = N1 << lc;
+  const int tstride = P.L / g.Nfft;
+  Z* S1 = reinterpret_cast<Z*>(P.S1);
+  const Z* tw = twL<R>(P);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int c0 = tile << lc;
+    Z wp[kPre];
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) {
+      const int e = threadIdx.x + q * blockDim.x;
+      if (e < total) {
+        const int k1 = e >> lc, j2 = c0 + (e & (ct - 1));
+        wp[q] = tw[((j2 * k1) & (g.Nfft - 1)) * tstride];
+      }
+    }
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+      const int j1 = e >> lc, c = e & (ct - 1);
+      const int j = N2 * j1 + c0 + c;
+      sm.bA[e] = (j1 < (N1 >> 1) && j < P.n) ? pro(j) : mkc<R>(R(0), R(0));
+    }
+    __syncthreads();
+    const Z* res = fft_batch<R, false>(sm.bA, sm.bB, N1, lc, sm.tw, P.T);
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) {
+      const int e = threadIdx.x + q * blockDim.x;
+      if (e < total) S1[(e >> lc) * N2 + c0 + (e & (ct - 1))] = cmul(res[e], wp[q]);
+    }
+    __syncthreads();
+  }
+}
+
+enum { MID_APPLY = 0, MID_SPEC = 1, MID_CONV = 2 };
+
+// Pass B: row FFTs (rows k1 and N1-k1 together), the spectral middle step,
+// inverse row FFTs, twiddle W^{-j2 k1}, store S2.  With Z the complex FFT of
+// the packed real input and k' = Nc - k, E = (Z_k + conj Z_k')/2 and
+// O = -i (Z_k - conj Z_k')/2 give the real-input spectrum
+// X_k = E + W_L^k O and conj(X_k') = E - W_L^k O.
+//  MID_APPLY: Y = S X for a real even spectrum S (tables sa = S_k/Nc,
+//    sb = S_k'/Nc), repacked as Z'_k = E' + i O' with
+//    E' = (sa X_k + sb conj X_k')/2, O' = conj(W_L^k) (sa X_k - sb conj X_k')/2.
+//    Each multiplier meets only its own frequency: the split into E and O
+//    is never weighted by the partner's S, which for the IFL symbol can be
+//    ~1e8 times larger (low against high frequencies) and would swamp the
+//    low-frequency result in rounding.
+//  MID_SPEC: forward only; stores sa = Re X_k / Nc, sb = Re conj X_k' / Nc
+//    (the spectrum of an even real sequence is real).
+//  MID_CONV: complex product Z'_k = Z_k * conv_k (geometry gc).
+template <typename R, int MID>
+__device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__ sa,
+                      const R* __restrict__ sb, R* sa_out, R* sb_out,
+                      const cplx<R>* __restrict__ conv) {
+  typedef cplx<R> Z;
+  const Geo& g = (MID == MID_CONV) ? P.gc : P.gr;
+  const int N1 = g.N1, N2 = g.N2;
+  const int npairs = (N1 >> 1) + 1;
+  const int tstride = P.L / g.Nfft;
+  const Z* S1 = reinterpret_cast<const Z*>(P.S1);
+  Z* S2 = reinterpret_cast<Z*>(P.S2);
+  const Z* tw = twL<R>(P);
+  const R invNc = R(1.0) / R(P.Nc);
+  for (int it = blockIdx.x; it < npairs; it += gridDim.x) {
+    const int ka = it;
+    const int kb = (it == 0 || it == (N1 >> 1)) ? -1 : N1 - it;
+    const int lgB = (kb < 0) ? 0 : 1;
+    const int B = 1 << lgB;
+    const int total = N2 << lgB;
+    // per-element coefficients and store twiddles, fetched early
+    Z wp[kPre], cf[kPre];
+    R s1[kPre], s2[kPre];
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) {
+      const int e = threadIdx.x + q * blockDim.x;
+      if (e < total) {
+        const int b = e & (B - 1), k2 = e >> lgB;
+        const int k1 = b ? kb : ka;
+        if constexpr (MID == MID_CONV) {
+          cf[q] = conv[k1 * N2 + k2];
+        } else {
+          cf[q] = tw[k1 + N1 * k2];  // W_L^k, k = k1 + N1 k2
+          if constexpr (MID == MID_APPLY) {
+            s1[q] = sa[k1 * N2 + k2];
+            s2[q] = sb[k1 * N2 + k2];
+          }
+        }
+        if constexpr (MID != MID_SPEC) wp[q] = tw[((k2 * k1) & (g.Nfft - 1)) * tstride];
+      }
+    }
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+      const int b = e & (B - 1), k2 = e >> lgB;
+      const int row = b ? kb : ka;
+      sm.bA[e] = __ldcg(S1 + row * N2 + k2);
+    }
+    __syncthreads();
+    Z* res = fft_batch<R, false>(sm.bA, sm.bB, N2, lgB, sm.tw, P.T);
+    Z* oth = (res == sm.bA) ? sm.bB : sm.bA;
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) {
+      const int e = threadIdx.x + q * blockDim.x;
+      if (e >= total) continue;
+      const int b = e & (B - 1), k2 = e >> lgB;
+      const int k1 = b ? kb : ka;
+      const Z Zk = res[e];
+      if constexpr (MID == MID_CONV) {
+        oth[e] = cmul(Zk, cf[q]);
+      } else {
+        const int q2 = (k1 == 0) ? ((N2 - k2) & (N2 - 1)) : (N2 - 1 - k2);
+        const int qb = (B == 1) ? 0 : 1 - b;
+        const Z Zq = res[(q2 << lgB) + qb];
+        const Z E = mkc<R>(R(0.5) * (Zk.x + Zq.x), R(0.5) * (Zk.y - Zq.y));
+        const Z O = mkc<R>(R(0.5) * (Zk.y + Zq.y), R(-0.5) * (Zk.x - Zq.x));
+        const Z Wk = cf[q];
+        const Z WO = cmul(Wk, O);
+        const Z X = cadd(E, WO);   // X_k
+        const Z Xc = csub(E, WO);  // conj(X_k')
+        if constexpr (MID == MID_APPLY) {
+          const Z Ya = cscale(X, s1[q]);
+          const Z Yb = cscale(Xc, s2[q]);
+          const Z Ep = cscale(cadd(Ya, Yb), R(0.5));
+          const Z Op = cscale(cmulc(csub(Ya, Yb), Wk), R(0.5));
+          oth[e] = mkc<R>(Ep.x - Op.y, Ep.y + Op.x);
+        } else {
+          sa_out[k1 * N2 + k2] = X.x * invNc;
+          sb_out[k1 * N2 + k2] = Xc.x * invNc;
+        }
+      }
+    }
+    __syncthreads();
+    if constexpr (MID == MID_SPEC) continue;
+    const Z* res2 = fft_batch<R, true>(oth, res, N2, lgB, sm.tw, P.T);
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) {
+      const int e = threadIdx.x + q * blockDim.x;
+      if (e < total) {
+        const int b = e & (B - 1), j2 = e >> lgB;
+        const int k1 = b ? kb : ka;
+        S2[k1 * N2 + j2] = cmulc(res2[e], wp[q]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Pass C (+ optional fused pass A): inverse column FFTs, y_{2j} = Re z_j,
+// y_{2j+1} = Im z_j for j1 < N1/2.  epi(i, y_i) consumes each output and
+// returns the next product's input x_i (used only with DO_A).
+template <typename R, bool DO_A, class Epi>
+__device__ void passCA_real(const DevPlan& P, const Smem<R>& sm, Epi& epi) {
+  typedef cplx<R> Z;
+  const Geo& g = P.gr;
+  const int lc = lgct<R>(g), ct = 1 << lc;
+  const int N1 = g.N1, N2 = g.N2, n = P.n;
+  const int ntiles = N2 >> lc;
+  const int total = N1 << lc;
+  const int tstride = P.L / g.Nfft;
+  const Z* S2 = reinterpret_cast<const Z*>(P.S2);
+  Z* S1 = reinterpret_cast<Z*>(P.S1);
+  const Z* tw = twL<R>(P);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int c0 = tile << lc;
+    Z wp[kPre];
+    if constexpr (DO_A) {
+#pragma unroll
+      for (int q = 0; q < kPre; ++q) {
+        const int e = threadIdx.x + q * blockDim.x;
+        if (e < total) {
+          const int k1 = e >> lc, j2 = c0 + (e & (ct - 1));
+          wp[q] = tw[((j2 * k1) & (g.Nfft - 1)) * tstride];
+        }
+      }
+    }
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+      const int k1 = e >> lc, c = e & (ct - 1);
+      sm.bA[e] = __ldcg(S2 + k1 * N2 + c0 + c);
+    }
+    __syncthreads();
+    Z* res = fft_batch<R, true>(sm.bA, sm.bB, N1, lc, sm.tw, P.T);
+    Z* oth = (res == sm.bA) ? sm.bB : sm.bA;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+      const int j1 = e >> lc, c = e & (ct - 1);
+      if (j1 < (N1 >> 1)) {
+        const int i0 = 2 * (N2 * j1 + c0 + c);
+        const Z v = res[e];
+        R x0 = R(0), x1 = R(0);
+        if (i0 < n) x0 = epi(i0, v.x);
+        if (i0 + 1 < n) x1 = epi(i0 + 1, v.y);
+        if (DO_A) oth[e] = mkc<R>(x0, x1);
+      } else if (DO_A) {
+        oth[e] = mkc<R>(R(0), R(0));
+      }
+    }
+    __syncthreads();
+    if constexpr (DO_A) {
+      const Z* res2 = fft_batch<R, false>(oth, res, N1, lc, sm.tw, P.T);
+#pragma unroll
+      for (int q = 0; q < kPre; ++q) {
+        const int e = threadIdx.x + q * blockDim.x;
+        if (e < total) S1[(e >> lc) * N2 + c0 + (e & (ct - 1))] = cmul(res2[e], wp[q]);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Pass C, complex output z_j for j < n (geometry gc).
+template <typename R, class Epi>
+__device__ void passC_cplx(const DevPlan& P, const Smem<R>& sm, Epi& epi) {
+  typedef cplx<R> Z;
+  const Geo& g = P.gc;
+  const int lc = lgct<R>(g), ct = 1 << lc;
+  const int N1 = g.N1, N2 = g.N2;
+  const int ntiles = N2 >> lc;
+  const Z* S2 = reinterpret_cast<const Z*>(P.S2);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int c0 = tile << lc;
+    for (int e = threadIdx.x; e < (N1 << lc); e += blockDim.x) {
+      const int k1 = e >> lc, c = e & (ct - 1);
+      sm.bA[e] = __ldcg(S2 + k1 * N2 + c0 + c);
+    }
+    __syncthreads();
+    const Z* res = fft_batch<R, true>(sm.bA, sm.bB, N1, lc, sm.tw, P.T);
+    for (int e = threadIdx.x; e < (N1 << lc); e += blockDim.x) {
+      const int j1 = e >> lc, c = e & (ct - 1);
+      const int j = N2 * j1 + c0 + c;
+      if (j1 < (N1 >> 1) && j < P.n) epi(j, res[e]);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------- preconditioner
+// P = ahat I + kbar s(A) (Eq. (4.3)) is circulant of size n with eigenvalues
+// d_k = ahat + kbar lambda_k.  Its inverse is the symmetric circulant with
+// first column g = IDFT_n(1/d), computed by a Bluestein chirp-z transform
+// on length-L FFTs; P^{-1} v is then the symmetric Toeplitz product with
+// first column g, i.e. the same zero-padded product as A with the spectrum
+// of the even embedding of g (built here as (sigma, rho) tables).
+template <typename R>
+__device__ bool build_precond(const DevPlan& P, const Smem<R>& sm, double ahat, double kbar) {
+  typedef cplx<R> Z;
+  const double* lam = P.lam;
+  const Z* ch = chirp<R>(P);
+  auto pro = [&](int j) -> Z {
+    const R q = (R)(1.0 / (ahat + kbar * lam[j]));
+    return cscale(ch[j], q);
+  };
+  passA_cplx<R>(P, sm, pro);
+  if (!gsync(P, sm.red)) return false;
+  passB<R, MID_CONV>(P, sm, nullptr, nullptr, nullptr, nullptr, Bh<R>(P));
+  if (!gsync(P, sm.red)) return false;
+  R* gv = gcol<R>(P);
+  const R invn = R(1.0 / (double)P.n);
+  auto epi = [&](int j, Z z) { gv[j] = (ch[j].x * z.x - ch[j].y * z.y) * invn; };
+  passC_cplx<R>(P, sm, epi);
+  if (!gsync(P, sm.red)) return false;
+  const int n = P.n, L = P.L;
+  auto proE = [&](int i) -> R {
+    if (i < n) return gv[i];
+    const int k = L - i;
+    return (k < n) ? gv[k] : R(0);
+  };
+  passA_real<R, true>(P, sm, L, proE);
+  if (!gsync(P, sm.red)) return false;
+  passB<R, MID_SPEC>(P, sm, nullptr, nullptr, saG<R>(P), sbG<R>(P), nullptr);
+  return gsync(P, sm.red);
+}
+
+// ------------------------------------------------------------- PBiCGSTAB
+struct SolveRes {
+  int status;
+  int iters;
+  double relres;
+};
+
+// Right-preconditioned BiCGSTAB (van der Vorst) for (ahat I + K A) x = b,
+// x0 = 0, stop when ||r_k||_2 / ||b||_2 < tol (Sec. 5).  binit(i) gives b_i.
+// Per iteration: P^{-1}p, A p^, P^{-1}s, A s^ as zero-padded FFT products.
+template <typename R, class BInit>
+__device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>& V,
+                             const R* __restrict__ kap, double ahat, bool prec, double tol,
+                             int max_it, BInit& binit) {
+  const int n = P.n;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gstr = gridDim.x * blockDim.x;
+  const R a = (R)ahat;
+  SolveRes out{TSFDE_OK, 0, 0.0};
+  {
+    R acc = 0;
+    for (int i = gtid; i < n; i += gstr) {
+      const R bi = binit(i);
+      V.x[i] = R(0); V.r[i] = bi; V.rh[i] = bi; V.p[i] = R(0); V.v[i] = R(0);
+      acc += bi * bi;
+    }
+    put_partial(P, SL_BB, block_sum((double)acc, sm.red));
+  }
+  double bb;
+  if (!gsync_sum(P, sm.red, SL_BB, bb)) { out.status = TSFDE_ETIMEOUT; return out; }
+  if (!isfinite(bb)) { out.status = TSFDE_ENONFINITE; return out; }
+  if (bb == 0.0) return out;
+  const double nb = sqrt(bb);
+  double rho = 1.0, alpha = 1.0, omega = 1.0, rho_new = bb, rr = bb;
+  int it = 0;
+  for (;;) {
+    const double relres = sqrt(rr) / nb;
+    out.relres = relres;
+    out.iters = it;
+    if (!isfinite(relres) || !isfinite(rho_new)) { out.status = TSFDE_ENONFINITE; return out; }
+    if (relres < tol) return out;
+    if (it >= max_it) { out.status = TSFDE_ENOCONV; return out; }
+    if (rho_new == 0.0 || omega == 0.0) { out.status = TSFDE_EBREAKDOWN; return out; }
+    const double beta = (rho_new / rho) * (alpha / omega);
+    rho = rho_new;
+    ++it;
+    // p = r + beta (p - omega v)
+    {
+      const R bR = (R)beta, oR = (R)omega;
+      auto pro = [&](int i) -> R {
+        const R pi = V.r[i] + bR * (V.p[i] - oR * V.v[i]);
+        V.p[i] = pi;
+        return pi;
+      };
+      passA_real<R, false>(P, sm, n, pro);
+    }
+    if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
+    if (prec) {
+      passB<R, MID_APPLY>(P, sm, saG<R>(P), sbG<R>(P), nullptr, nullptr, nullptr);
+      if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
+      auto epi = [&](int i, R y) -> R { V.ph[i] = y; return y; };
+      passCA_real<R, true>(P, sm, epi);
+      if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
+    }
+    passB<R, MID_APPLY>(P, sm, saT<R>(P), sbT<R>(P), nullptr, nullptr, nullptr);
+    if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
+    const R* ph = prec ? V.ph : V.p;
+    {
+      R acc = 0;
+      auto epi = [&](int i, R y) -> R {
+        const R vi = a * ph[i] + kap[i] * y;
+        V.v[i] = vi;
+        acc += V.rh[i] * vi;
+        return R(0);
+      };
+      passCA_real<R, false>(P, sm, epi);
+      put_partial(P, SL_RV, block_sum((double)acc, sm.red));
+    }
+    double rv;
+    if (!gsync_sum(P, sm.red, SL_RV, rv)) { out.status = TSFDE_ETIMEOUT; return out; }
+    if (!isfinite(rv)) { out.status = TSFDE_ENONFINITE; return out; }
+    if (rv == 0.0) { out.status = TSFDE_EBREAKDOWN; return out; }
+    alpha = rho / rv;
+    // s = r - alpha v
+    {
+      const R aR = (R)alpha;
+      auto pro = [&](int i) -> R {
+        const R si = V.r[i] - aR * V.v[i];
+        V.s[i] = si;
+        return si;
+      };
+      passA_real<R, false>(P, sm, n, pro);
+    }
+    if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
+    if (prec) {
+      passB<R, MID_APPLY>(P, sm, saG<R>(P), sbG<R>(P), nullptr, nullptr, nullptr);
+      if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
+      auto epi = [&](int i, R y) -> R { V.sh[i] = y; return y; };
+      passCA_real<R, true>(P, sm, epi);
+      if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
+    }
+    passB<R, MID_APPLY>(P, sm, saT<R>(P), sbT<R>(P), nullptr, nullptr, nullptr);
+    if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
+    const R* sh = prec ? V.sh : V.s;
+    {
+      R ats = 0, att = 0;
+      auto epi = [&](int i, R y) -> R {
+        const R ti = a * sh[i] + kap[i] * y;
+        V.t[i] = ti;
+        ats += ti * V.s[i];
+        att += ti * ti;
+        return R(0);
+      };
+      passCA_real<R, false>(P, sm, epi);
+      put_partial(P, SL_TS, block_sum((double)ats, sm.red));
+      put_partial(P, SL_TT, block_sum((double)att, sm.red));
+    }
+    double ts, tt;
+    if (!gsync_sum2(P, sm.red, SL_TS, SL_TT, 0u, ts, tt)) { out.status = TSFDE_ETIMEOUT; return out; }
+    omega = (tt > 0.0) ? ts / tt : 0.0;
+    if (!isfinite(omega)) { out.status = TSFDE_ENONFINITE; return out; }
+    // x += alpha p^ + omega s^, r = s - omega t
+    {
+      const R aR = (R)alpha, oR = (R)omega;
+      R arr = 0, ar2 = 0;
+      for (int i = gtid; i < n; i += gstr) {
+        V.x[i] = V.x[i] + aR * ph[i] + oR * sh[i];
+        const R ri = V.s[i] - oR * V.t[i];
+        V.r[i] = ri;
+        arr += V.rh[i] * ri;
+        ar2 += ri * ri;
+      }
+      put_partial(P, SL_RR0, block_sum((double)arr, sm.red));
+      put_partial(P, SL_RR, block_sum((double)ar2, sm.red));
+    }
+    if (!gsync_sum2(P, sm.red, SL_RR0, SL_RR, 0u, rho_new, rr)) { out.status = TSFDE_ETIMEOUT; return out; }
+  }
+}
+
+static __device__ double mean_kappa(const DevPlan& P, const double* kap, double* red) {
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gstr = gridDim.x * blockDim.x;
+  double acc = 0.0;
+  for (int i = gtid; i < P.n; i += gstr) acc += kap[i];
+  put_partial(P, SL_KAP, block_sum(acc, red));
+  double tot;
+  if (!gsync_sum(P, red, SL_KAP, tot)) return -1.0;
+  return tot / (double)P.n;
+}
+
+static __device__ void write_stat(StepStat* st, int status, int iters, int outer, double relres) {
+  if (st && blockIdx.x == 0 && threadIdx.x == 0) {
+    st->status = status;
+    st->iterations = iters;
+    st->outer = outer;
+    st->rel_residual = relres;
+  }
+}
+
+
+// Mixed level solve (shared by both engines).  conv(k) rounds entry k of the
+// FP64 preconditioner spectrum into the inner solver's FP32 tables;
+// inner(sc, res) solves (ahat I + K A) e = sc r64 in FP32 into k32.x (false
+// on a barrier timeout).
+// FP64 refinement around an FP32 PBiCGSTAB: each sweep
+// solves (ahat I + K A) e = r / ||r|| in FP32 (at most inner_max_it
+// iterations), forms w = M e in FP64 and updates u += theta e,
+// r -= theta w with theta = 1, or the minimal-residual
+// theta = (r, w)/(w, w) when the full step would raise ||r||, so the FP64
+// residual never grows.  Stops when the last step satisfies
+// max|theta e| <= tol max|u|, or when a sweep no longer halves ||r|| with
+// ||r||/||b|| <= 1e-9 (its rounding floor at large n).  After three sweeps
+// without progress above that, or at max_outer, the level is finished by
+// FP64 PBiCGSTAB on the remaining residual, so a level never returns an
+// unconverged answer.
+template <class Conv, class Inner>
+__device__ void mixed_level(const LevelArgs& A, SmemAll& S, Conv& conv, Inner& inner) {
+  const DevPlan& P = A.P;
+  const int n = P.n;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gstr = gridDim.x * blockDim.x;
+  const double kbar = mean_kappa(P, A.kappa64, S.d.red);
+  if (kbar < 0.0) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
+  // The preconditioner is built in FP64 and rounded to FP32; building it in
+  // FP32 would bury its smallest eigenvalues (1/(ahat + kbar lambda_max),
+  // ~1e-8 of the largest at n = 2^17-1) under rounding.
+  if (A.precond && !build_precond<double>(P, S.d, A.ahat, kbar)) {
+    write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0);
+    return;
+  }
+  {
+    double acc = 0.0;
+    if (A.precond)
+      for (int k = gtid; k < P.Nc; k += gstr) conv(k);
+    for (int i = gtid; i < n; i += gstr) {
+      const double bi = A.b[i];
+      A.u[i] = 0.0;
+      A.r64[i] = bi;
+      acc += bi * bi;
+    }
+    put_partial(P, SL_RES, block_sum(acc, S.d.red));
+  }
+  double bb;
+  if (!gsync_sum(P, S.d.red, SL_RES, bb)) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
+  if (!isfinite(bb)) { write_stat(A.stat, TSFDE_ENONFINITE, 0, 0, 0.0); return; }
+  if (bb == 0.0) { write_stat(A.stat, TSFDE_OK, 0, 0, 0.0); return; }
+  const double nb = sqrt(bb);
+  double nr = nb, relres = 1.0;
+  int inner_total = 0, outer = 0, status = TSFDE_OK, stalls = 0;
+  bool fallback = false;
+  double* w = A.k64.v;  // FP64 scratch for M e
+  const float* e = A.k32.x;
+  for (;;) {
+    if (outer >= A.max_outer) { fallback = true; break; }
+    SolveRes ir{TSFDE_OK, 0, 0.0};
+    if (!inner(1.0 / nr, ir)) { status = TSFDE_ETIMEOUT; break; }
+    inner_total += ir.iters;
+    ++outer;
+    // w = M (nr e) in FP64
+    const double ah = A.ahat;
+    auto pro = [&](int i) -> double { return nr * (double)e[i]; };
+    passA_real<double, false>(P, S.d, n, pro);
+    if (!gsync(P, S.d.red)) { status = TSFDE_ETIMEOUT; break; }
+    passB<double, MID_APPLY>(P, S.d, P.saT64, P.sbT64, nullptr, nullptr, nullptr);
+    if (!gsync(P, S.d.red)) { status = TSFDE_ETIMEOUT; break; }
+    {
+      double rw = 0.0, ww = 0.0;
+      auto epi = [&](int i, double y) -> double {
+        const double wi = ah * nr * (double)e[i] + A.kappa64[i] * y;
+        w[i] = wi;
+        rw += A.r64[i] * wi;
+        ww += wi * wi;
+        return 0.0;
+      };
+      passCA_real<double, false>(P, S.d, epi);
+      put_partial(P, SL_RV, block_sum(rw, S.d.red));
+      put_partial(P, SL_TT, block_sum(ww, S.d.red));
+    }
+    double rw, ww;
+    if (!gsync_sum2(P, S.d.red, SL_RV, SL_TT, 0u, rw, ww)) { status = TSFDE_ETIMEOUT; break; }
+    // full step unless it would raise ||r||: ||r - w||^2 = ||r||^2 - 2 (r,w) + (w,w)
+    double theta = 1.0;
+    if (ww - 2.0 * rw > 0.0) theta = (ww > 0.0) ? rw / ww : 0.0;
+    if (!isfinite(theta) || !(theta > 0.0)) { fallback = true; break; }
+    {
+      double rr = 0.0, emax = 0.0, xmax = 0.0;
+      const double step = theta * nr;
+      for (int i = gtid; i < n; i += gstr) {
+        const double di = step * (double)e[i];
+        const double xi = A.u[i] + di;
+        A.u[i] = xi;
+        const double ri = A.r64[i] - theta * w[i];
+        A.r64[i] = ri;
+        rr += ri * ri;
+        emax = fmax(emax, fabs(di));
+        xmax = fmax(xmax, fabs(xi));
+      }
+      put_partial(P, SL_RES, block_sum(rr, S.d.red));
+      put_partial(P, SL_EMAX, block_max(emax, S.d.red));
+      put_partial(P, SL_XMAX, block_max(xmax, S.d.red));
+    }
+    double rr, emax, xmax;
+    if (!gsync_sum3(P, S.d.red, SL_RES, SL_EMAX, SL_XMAX, 6u, rr, emax, xmax)) {
+      status = TSFDE_ETIMEOUT;
+      break;
+    }
+    const double nr_prev = nr;
+    nr = sqrt(rr);
+    if (!isfinite(nr) || !isfinite(xmax)) { status = TSFDE_ENONFINITE; break; }
+    relres = nr / nb;
+    if (nr == 0.0 || emax <= A.tol * xmax) break;
+    if (outer >= 2 && nr > 0.5 * nr_prev) {
+      if (relres <= 1e-9) break;  // rounding floor of the FP64 residual
+      if (++stalls >= 3) { fallback = true; break; }
+    } else {
+      stalls = 0;
+    }
+  }
+  if (fallback && status == TSFDE_OK) {
+    // finish in FP64: solve M d = r to the requested overall tolerance
+    KVecs<double> V = A.k64;
+    auto binit = [&](int i) -> double { return A.r64[i]; };
+    const double tol_d = fmax(A.tol * nb / nr, 1e-14);
+    SolveRes fr = bicgstab<double>(P, S.d, V, A.kappa64, A.ahat, A.precond != 0, tol_d,
+                                   A.max_it, binit);
+    if (fr.status == TSFDE_OK) {
+      for (int i = gtid; i < n; i += gstr) A.u[i] += V.x[i];
+      relres = fr.relres * nr / nb;
+      if (!gsync(P, S.d.red)) fr.status = TSFDE_ETIMEOUT;
+    }
+    status = fr.status;
+    inner_total += fr.iters;
+    outer = -outer;  // a negative count marks a level finished in FP64
+  }
+  write_stat(A.stat, status, inner_total, outer, relres);
+}
+
+}  // namespace tsfde

@@ -27,6 +27,24 @@ struct Geo {
   int lgct64, lgct32;  // log2 columns per tile for double / float data
 };
 
+// Cluster engine: one thread-block cluster of Q CTAs holds a length-Nc
+// complex FFT (geometry gr) in distributed shared memory.  CTA q owns the
+// columns j2 in [q cQ, (q+1) cQ) and the vector entries i with
+// (i/2) mod N2 in that range; for the row pass it owns the row units
+// [q U, (q+1) U), unit 0 = rows {0, N1/2}, unit u > 0 = rows {u, N1-u}, held
+// as row slots 2(u - qU) and 2(u - qU) + 1.
+struct CGeo {
+  int Q, lgQ;    // CTAs of the cluster
+  int cQ, lgcQ;  // columns per CTA, N2 / Q
+  int U, lgU;    // row units per CTA, N1 / (2Q)
+  int Bq, lgBq;  // row slots per CTA, 2U
+  int nbuf;      // complex elements per CTA, Nc / Q
+  int cap;       // staging capacity, nbuf + N1
+  int T1;        // stage twiddle table W_{T1}^k, T1 = N1 >= N2
+  int LT, lgLT;  // low twiddle table W_L^l, l < LT = L / T1
+  int G;         // CTAs of the cluster-engine launch (a multiple of Q)
+};
+
 // Everything a cooperative kernel needs to run the FIDS level solve.
 struct DevPlan {
   int n;       // unknowns
@@ -58,6 +76,11 @@ struct DevPlan {
   double* g64; float* g32;  // first column of the circulant inverse (n)
   double2* S1;  // work: Nfft complex (double capacity, reused as float2)
   double2* S2;
+  CGeo cl;
+  // (sa, sb) pairs in the cluster engine's row-pass order: entry
+  // q nbuf + (k2 << lgBq) + slot for the row k1 held in slot `slot` of CTA q
+  const float2* spT_cl;  // Toeplitz symbol
+  float2* spG_cl;        // per-level preconditioner (written by the build)
 };
 
 enum { kSlots = 12 };
@@ -92,6 +115,7 @@ struct LevelArgs {
   KVecs<float> k32;
   double* r64;        // mixed: FP64 residual
   StepStat* stat;
+  int probe;          // cluster engine: return at once (launch check)
 };
 
 struct RhsArgs {
@@ -131,6 +155,15 @@ struct ApplyArgs {
 // launchers (kernels.cu)
 cudaError_t launch_rhs(const RhsArgs& a, cudaStream_t s);
 cudaError_t launch_level(const LevelArgs& a, int mixed, cudaStream_t s);
+// cluster engine (cluster.cu): mixed level solve with the FP32 inner solves
+// on one thread-block cluster; a.P.G must equal a.P.cl.G.
+cudaError_t launch_level_cluster(const LevelArgs& a, cudaStream_t s);
+// Fills P.cl for P's real geometry; false if the sizes do not allow it.
+bool cluster_geometry(DevPlan& P);
+size_t cluster_smem_bytes(const DevPlan& P);
+// Largest cluster-engine grid (CTAs) that can be co-resident with `smem`
+// dynamic shared bytes per CTA, 0 if the engine cannot be launched.
+int cluster_max_grid(const DevPlan& P, size_t smem);
 cudaError_t launch_apply(const ApplyArgs& a, int fp32, cudaStream_t s);
 // out64 = in, out32 = (float) in
 cudaError_t launch_convert(const double* in, double* out64, float* out32, int n, cudaStream_t s);

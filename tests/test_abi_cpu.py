@@ -80,3 +80,15 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.tsfde_reset(None) == pkg.TSFDE_EINVAL
     assert lib.tsfde_step(None, None, None, None, None, None) == pkg.TSFDE_EINVAL
     assert lib.tsfde_strerror(pkg.TSFDE_ETIMEOUT) == b"device barrier timed out"
+
+
+def test_setup_rejects_unknown_engine(lib):
+    import paper_2002_11978_gb300 as pkg
+    ctx = ctypes.c_void_p()
+    o = pkg.default_opts()
+    assert o.engine == pkg.TSFDE_ENGINE_AUTO
+    o.engine = 7
+    assert lib.tsfde_setup(ctypes.byref(ctx), 1.5, 0.5, 1.0, 1.0, 7, 4, 3.0, 1e-12,
+                           ctypes.byref(o)) == pkg.TSFDE_EINVAL
+    assert not ctx
+    assert lib.tsfde_get_engine(None) == -1
