@@ -92,8 +92,10 @@ typedef struct tsfde_opts {
                            value makes every barrier give up and the call
                            return TSFDE_ETIMEOUT: used to test that path.  */
   void* stream;         /* cudaStream_t; NULL = default stream              */
-  int engine;           /* TSFDE_ENGINE_* (default AUTO); CLUSTER where it
-                           cannot run fails tsfde_setup with TSFDE_ENOTSUP  */
+  int engine;           /* TSFDE_ENGINE_* (default AUTO); a MIXED context
+                           asking for CLUSTER where it cannot run fails
+                           tsfde_setup with TSFDE_ENOTSUP; FP64 contexts
+                           ignore the field                                 */
 } tsfde_opts;
 
 typedef struct tsfde_step_info {
@@ -124,6 +126,14 @@ typedef struct tsfde_timing {
                            kernel over those levels (CUDA events)           */
   double level_ms;      /* total device time of the level-solve kernel      */
 } tsfde_timing;
+
+typedef struct tsfde_adjoint_info {
+  int status;           /* first non-OK level status, else TSFDE_OK          */
+  int64_t failed_level; /* level of that status, 0 if none                  */
+  int64_t iterations;   /* total BiCGSTAB iterations of the transposed solves */
+  int max_iterations;
+  double max_rel_residual;
+} tsfde_adjoint_info;
 
 typedef struct tsfde_ctx tsfde_ctx;
 
@@ -192,6 +202,34 @@ int tsfde_get_times(const tsfde_ctx* ctx, double* t);
 
 /* Copy the first column t_0..t_{n-1} of A (Eq. (3.16x)) to host. */
 int tsfde_get_symbol(const tsfde_ctx* ctx, double* t);
+
+/* ---- adjoint sweep (gradients of a scalar J(u^M)) ---------------------
+ * The paper solves only the forward problem; this is the discrete adjoint of
+ * the FIDS march of Eq. (3.16gu) (with the history written through the SOE
+ * recurrence of Sec. 3), for a problem whose kappa is time independent
+ * (tsfde_set_problem with kappa1 = NULL) and whose source f^m is the
+ * caller's fixed f for every level.
+ *
+ * Reverse in time, m = M..1, in FP64 with the right-preconditioned
+ * PBiCGSTAB of the forward path on the transposed operator:
+ *   (ahat_m I + A K) lambda^m = g^m,   g^M = dJ/du^M,
+ *   g^m = ahat_{m+1} lambda^{m+1}
+ *         - sum_j (c_{j,m+1} Y_j^{(m+1)} - c_{j,m+2} Y_j^{(m+2)}),  m < M,
+ *   Y_j^{(m)} = eps_{j,m} (lambda^m + Y_j^{(m+1)}),  Y^{(M+1)} = 0,
+ * with eps_{j,m} = e^{-s_j tau_m} and c_{j,m} = w_j beta_{j,m-1}/Gamma(1-gamma)
+ * the forward SOE coefficients.  Gradients:
+ *   dJ/dkappa = -sum_m lambda^m .* (A u^m),   dJ/df = sum_m lambda^m.
+ *
+ * u_all:   dev (M+1) x n, the forward levels u^0..u^M (as tsfde_solve writes
+ *          them with this context's problem; row m = u^m).
+ * dJ_duM:  dev n.  grad_kappa, grad_f: dev n, overwritten.
+ * Uses the context's krylov_tol / max_it / precond (always FP64).  Does not
+ * change the forward state (tsfde_step continues where it was).  Device
+ * work buffers are allocated on the first call.  Synchronises the stream.
+ * Errors: TSFDE_ESTATE without a problem, TSFDE_ENOTSUP if kappa1 was set,
+ * TSFDE_EINVAL for NULL pointers, else the first failing level's status. */
+int tsfde_adjoint(tsfde_ctx* ctx, const double* u_all, const double* dJ_duM,
+                  double* grad_kappa, double* grad_f, tsfde_adjoint_info* info);
 
 /* Engine the context's mixed level solves use: TSFDE_ENGINE_GRID or
  * TSFDE_ENGINE_CLUSTER (never AUTO); -1 if ctx is NULL. */

@@ -54,6 +54,12 @@ class tsfde_solve_info(ctypes.Structure):
                 ("E", ctypes.c_int), ("E_active_sum", ctypes.c_int64)]
 
 
+class tsfde_adjoint_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("failed_level", ctypes.c_int64),
+                ("iterations", ctypes.c_int64), ("max_iterations", ctypes.c_int),
+                ("max_rel_residual", ctypes.c_double)]
+
+
 class tsfde_timing(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int64), ("rhs_ms", ctypes.c_double),
                 ("level_ms", ctypes.c_double)]
@@ -80,6 +86,7 @@ _SIGNATURES = [
     ("tsfde_get_symbol", ctypes.c_int, [_V, _dp]),
     ("tsfde_get_timing", ctypes.c_int, [_V, ctypes.POINTER(tsfde_timing)]),
     ("tsfde_get_engine", ctypes.c_int, [_V]),
+    ("tsfde_adjoint", ctypes.c_int, [_V, _V, _V, _V, _V, ctypes.POINTER(tsfde_adjoint_info)]),
     ("tsfde_get_level_stats", ctypes.c_int, [_V, ctypes.c_int64, ctypes.c_int64,
                                              ctypes.POINTER(tsfde_step_info)]),
     ("tsfde_get_solution", ctypes.c_int, [_V, _V]),
@@ -313,6 +320,19 @@ class Solver:
     def precond_apply(self, a, kbar, v, z, precision="fp64"):
         _check(self.lib.tsfde_precond_apply(self.ctx, a, kbar, _dev(v, self.n, "v"),
                                             _dev(z, self.n, "z"), _prec(precision)), self.ctx)
+
+    def adjoint(self, u_all, dJ_duM, grad_kappa, grad_f):
+        """Discrete adjoint of the FIDS march (tsfde_adjoint): given the forward
+        levels u_all ((M+1) x n, as solve() writes them) and dJ/du^M, write
+        dJ/dkappa and dJ/df for a time-independent kappa and f."""
+        if tuple(u_all.shape) != (self.M + 1, self.n):
+            raise ValueError(f"u_all must be ({self.M + 1}, {self.n})")
+        info = tsfde_adjoint_info()
+        _check(self.lib.tsfde_adjoint(self.ctx, _dev(u_all, None, "u_all"),
+                                      _dev(dJ_duM, self.n, "dJ_duM"),
+                                      _dev(grad_kappa, self.n, "grad_kappa"),
+                                      _dev(grad_f, self.n, "grad_f"), ctypes.byref(info)), self.ctx)
+        return _info_dict(info)
 
     def linear_solve(self, a, kappa, b, x):
         info = tsfde_step_info()

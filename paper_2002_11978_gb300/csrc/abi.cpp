@@ -44,6 +44,11 @@ struct tsfde_ctx {
   StepStat* stats = nullptr;
   int* status = nullptr;
   int engine = TSFDE_ENGINE_GRID;  // engine of the mixed level solves
+  // adjoint work buffers (allocated by the first tsfde_adjoint)
+  double* adjY = nullptr;       // E x ld reversed SOE history
+  double* adjLam[2] = {nullptr, nullptr};
+  double* adjG = nullptr;
+  StepStat* adjStats = nullptr;
   // profiling: three events per level (before rhs, after rhs, after level)
   std::vector<cudaEvent_t> ev_free, ev_used;
 };
@@ -312,7 +317,7 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
       use_cluster = true;
     }
   }
-  if (o.engine == TSFDE_ENGINE_CLUSTER && !use_cluster)
+  if (o.precision == TSFDE_MIXED && o.engine == TSFDE_ENGINE_CLUSTER && !use_cluster)
     return fail(c, TSFDE_ENOTSUP, "cluster engine unavailable for this size or device");
 
   // ---- device allocations
@@ -729,6 +734,90 @@ int tsfde_precond_apply(tsfde_ctx* c, double a, double kbar, const double* v, do
 }
 
 int tsfde_get_engine(const tsfde_ctx* c) { return c ? c->engine : -1; }
+
+int tsfde_adjoint(tsfde_ctx* c, const double* u_all, const double* dJ, double* grad_kappa,
+                  double* grad_f, tsfde_adjoint_info* info) {
+  if (!c || !u_all || !dJ || !grad_kappa || !grad_f) return TSFDE_EINVAL;
+  if (!c->have_problem) return fail(c, TSFDE_ESTATE, "no problem set");
+  if (c->kap1) return fail(c, TSFDE_ENOTSUP, "adjoint needs a time-independent kappa (kappa1 = NULL)");
+  const int64_t n = c->n, M = c->M;
+  const int E = std::max(c->E, 1);
+  if (!c->adjY) {
+    bool ok = dalloc(c, &c->adjY, (size_t)E * c->ld) && dalloc(c, &c->adjLam[0], n) &&
+              dalloc(c, &c->adjLam[1], n) && dalloc(c, &c->adjG, n) && dalloc(c, &c->adjStats, M + 1);
+    if (!ok) {
+      c->adjY = nullptr;
+      return fail(c, TSFDE_ENOMEM, "cudaMalloc failed (adjoint buffers)");
+    }
+  }
+  cudaStream_t s = c->stream;
+  cudaError_t e;
+  const size_t nb = sizeof(double) * (size_t)n;
+  if ((e = cudaMemsetAsync(c->adjY, 0, sizeof(double) * (size_t)E * c->ld, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(grad_kappa, 0, nb, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(grad_f, 0, nb, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->adjStats, 0, sizeof(StepStat) * (M + 1), s)) != cudaSuccess)
+    return cuda_fail(c, e, "adjoint memset");
+  // kappa of every level is kappa0
+  if ((e = launch_convert(c->kap0, c->kappa64, c->kappa32, (int)n, s)) != cudaSuccess)
+    return cuda_fail(c, e, "convert kernel");
+  const int precond = c->opts.precond == TSFDE_STRANG ? 1 : 0;
+  for (int64_t m = M; m >= 1; --m) {
+    double* lam = c->adjLam[m & 1];
+    const double* lam1 = c->adjLam[(m + 1) & 1];
+    if (m == M) {
+      if ((e = cudaMemcpyAsync(c->adjG, dJ, nb, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return cuda_fail(c, e, "adjoint copy");
+    } else {
+      AdjRhsArgs R{};
+      R.n = (int)n;
+      R.ld = c->ld;
+      R.Eact = c->Eact[m + 1];
+      R.ahat1 = c->ahat[m + 1];
+      R.Y = c->adjY;
+      R.eps1 = c->eps + (m + 1) * c->E;
+      R.c1 = c->cw + (m + 1) * c->E;
+      R.c2 = (m + 2 <= M) ? c->cw + (m + 2) * c->E : nullptr;
+      R.lam1 = lam1;
+      R.g = c->adjG;
+      if ((e = launch_adj_rhs(R, s)) != cudaSuccess) return cuda_fail(c, e, "adjoint rhs kernel");
+    }
+    LevelArgs A{};
+    A.P = c->P;
+    A.ahat = c->ahat[m];
+    A.b = c->adjG;
+    A.kappa64 = c->kappa64;
+    A.kappa32 = c->kappa32;
+    A.u = lam;
+    A.precond = precond;
+    A.tol = c->opts.krylov_tol;
+    A.max_it = c->opts.max_it;
+    A.k64 = c->k64;
+    A.k32 = c->k32;
+    A.r64 = c->r64;
+    A.stat = c->adjStats + m;
+    AdjGradArgs Gd{u_all + (size_t)m * n, grad_kappa, grad_f};
+    if ((e = launch_level_adj(A, Gd, s)) != cudaSuccess) return cuda_fail(c, e, "adjoint level kernel");
+  }
+  std::vector<StepStat> st(M + 1);
+  if ((e = cudaMemcpyAsync(st.data(), c->adjStats, sizeof(StepStat) * (M + 1), cudaMemcpyDeviceToHost, s)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_fail(c, e, "adjoint sync");
+  tsfde_adjoint_info inf{};
+  for (int64_t m = M; m >= 1; --m) {
+    inf.iterations += st[m].iterations;
+    inf.max_iterations = std::max(inf.max_iterations, st[m].iterations);
+    inf.max_rel_residual = std::max(inf.max_rel_residual, st[m].rel_residual);
+    if (st[m].status != TSFDE_OK && inf.status == TSFDE_OK) {
+      inf.status = st[m].status;
+      inf.failed_level = m;
+    }
+  }
+  if (info) *info = inf;
+  if (inf.status != TSFDE_OK) return fail(c, inf.status, tsfde_strerror(inf.status));
+  return TSFDE_OK;
+}
 
 int tsfde_linear_solve(tsfde_ctx* c, double a, const double* kappa, const double* b, double* x,
                        tsfde_step_info* info) {

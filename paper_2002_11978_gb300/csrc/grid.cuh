@@ -467,7 +467,9 @@ struct SolveRes {
 // Right-preconditioned BiCGSTAB (van der Vorst) for (ahat I + K A) x = b,
 // x0 = 0, stop when ||r_k||_2 / ||b||_2 < tol (Sec. 5).  binit(i) gives b_i.
 // Per iteration: P^{-1}p, A p^, P^{-1}s, A s^ as zero-padded FFT products.
-template <typename R, class BInit>
+// TR selects the transposed operator ahat I + A K (the adjoint level solve):
+// kappa then scales the input of the Toeplitz product instead of its output.
+template <typename R, class BInit, bool TR = false>
 __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>& V,
                              const R* __restrict__ kap, double ahat, bool prec, double tol,
                              int max_it, BInit& binit) {
@@ -509,7 +511,7 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
       auto pro = [&](int i) -> R {
         const R pi = V.r[i] + bR * (V.p[i] - oR * V.v[i]);
         V.p[i] = pi;
-        return pi;
+        return (TR && !prec) ? kap[i] * pi : pi;
       };
       passA_real<R, false>(P, sm, n, pro);
     }
@@ -517,7 +519,7 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
     if (prec) {
       passB<R, MID_APPLY>(P, sm, saG<R>(P), sbG<R>(P), nullptr, nullptr, nullptr);
       if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
-      auto epi = [&](int i, R y) -> R { V.ph[i] = y; return y; };
+      auto epi = [&](int i, R y) -> R { V.ph[i] = y; return TR ? kap[i] * y : y; };
       passCA_real<R, true>(P, sm, epi);
       if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
     }
@@ -527,7 +529,7 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
     {
       R acc = 0;
       auto epi = [&](int i, R y) -> R {
-        const R vi = a * ph[i] + kap[i] * y;
+        const R vi = a * ph[i] + (TR ? y : kap[i] * y);
         V.v[i] = vi;
         acc += V.rh[i] * vi;
         return R(0);
@@ -546,7 +548,7 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
       auto pro = [&](int i) -> R {
         const R si = V.r[i] - aR * V.v[i];
         V.s[i] = si;
-        return si;
+        return (TR && !prec) ? kap[i] * si : si;
       };
       passA_real<R, false>(P, sm, n, pro);
     }
@@ -554,7 +556,7 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
     if (prec) {
       passB<R, MID_APPLY>(P, sm, saG<R>(P), sbG<R>(P), nullptr, nullptr, nullptr);
       if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
-      auto epi = [&](int i, R y) -> R { V.sh[i] = y; return y; };
+      auto epi = [&](int i, R y) -> R { V.sh[i] = y; return TR ? kap[i] * y : y; };
       passCA_real<R, true>(P, sm, epi);
       if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
     }
@@ -564,7 +566,7 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
     {
       R ats = 0, att = 0;
       auto epi = [&](int i, R y) -> R {
-        const R ti = a * sh[i] + kap[i] * y;
+        const R ti = a * sh[i] + (TR ? y : kap[i] * y);
         V.t[i] = ti;
         ats += ti * V.s[i];
         att += ti * ti;

@@ -57,6 +57,69 @@ __global__ void __launch_bounds__(kThreads, 2) k_level_mixed(LevelArgs A) {
   mixed_level(A, S, conv, inner);
 }
 
+// Adjoint level solve: (ahat I + A K) lambda = g in FP64 (transposed
+// operator; the Strang preconditioner is symmetric, so the same P serves),
+// then y = A u^m with grad_kappa -= lambda .* y and grad_f += lambda in the
+// product's epilogue.
+__global__ void __launch_bounds__(kThreads, 2) k_level_adj(LevelArgs A, AdjGradArgs Gd) {
+  const DevPlan& P = A.P;
+  SmemAll S = smem_setup(P);
+  const double kbar = mean_kappa(P, A.kappa64, S.d.red);
+  if (kbar < 0.0) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
+  if (A.precond && !build_precond<double>(P, S.d, A.ahat, kbar)) {
+    write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0);
+    return;
+  }
+  KVecs<double> V = A.k64;
+  V.x = A.u;
+  auto binit = [&](int i) -> double { return A.b[i]; };
+  SolveRes r = bicgstab<double, decltype(binit), true>(P, S.d, V, A.kappa64, A.ahat, A.precond != 0,
+                                                       A.tol, A.max_it, binit);
+  if (r.status == TSFDE_OK) {
+    auto pro = [&](int i) -> double { return Gd.um[i]; };
+    passA_real<double, false>(P, S.d, P.n, pro);
+    if (!gsync(P, S.d.red)) { write_stat(A.stat, TSFDE_ETIMEOUT, r.iters, 0, r.relres); return; }
+    passB<double, MID_APPLY>(P, S.d, P.saT64, P.sbT64, nullptr, nullptr, nullptr);
+    if (!gsync(P, S.d.red)) { write_stat(A.stat, TSFDE_ETIMEOUT, r.iters, 0, r.relres); return; }
+    auto epi = [&](int i, double y) -> double {
+      const double li = A.u[i];
+      Gd.grad_kappa[i] -= li * y;
+      Gd.grad_f[i] += li;
+      return 0.0;
+    };
+    passCA_real<double, false>(P, S.d, epi);
+  }
+  write_stat(A.stat, r.status, r.iters, 0, r.relres);
+}
+
+// Reversed SOE recurrence and adjoint right-hand side (see AdjRhsArgs).
+__global__ void __launch_bounds__(kThreads) k_adj_rhs(AdjRhsArgs a) {
+  extern __shared__ double sh[];
+  double* s_eps = sh;
+  double* s_c1 = sh + a.Eact;
+  double* s_c2 = sh + 2 * a.Eact;
+  for (int j = threadIdx.x; j < a.Eact; j += blockDim.x) {
+    s_eps[j] = a.eps1[j];
+    s_c1[j] = a.c1[j];
+    s_c2[j] = a.c2 ? a.c2[j] : 0.0;
+  }
+  __syncthreads();
+  const int gstr = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gstr) {
+    const double lam = a.lam1[i];
+    double acc = 0.0;
+    double* Yi = a.Y + i;
+    const size_t ld = (size_t)a.ld;
+    for (int j = 0; j < a.Eact; ++j) {
+      const double yo = Yi[j * ld];
+      const double yn = s_eps[j] * (lam + yo);
+      Yi[j * ld] = yn;
+      acc += s_c1[j] * yn - s_c2[j] * yo;
+    }
+    a.g[i] = a.ahat1 * lam - acc;
+  }
+}
+
 // ------------------------------------------------------ single products
 template <typename R>
 __device__ void apply_kernel_body(const ApplyArgs& A, const Smem<R>& sm) {
@@ -178,7 +241,7 @@ static cudaError_t set_attrs(size_t smem) {
   cudaError_t e = cudaSuccess;
   if (smem <= g_smem_limit) return e;
   const void* ks[] = {(const void*)k_level64, (const void*)k_level_mixed, (const void*)k_apply64,
-                      (const void*)k_apply32};
+                      (const void*)k_apply32, (const void*)k_level_adj};
   for (const void* k : ks) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -191,7 +254,7 @@ int coop_blocks_per_sm(size_t smem) {
   if (set_attrs(smem) != cudaSuccess) return 0;
   int best = 1 << 30;
   const void* ks[] = {(const void*)k_level64, (const void*)k_level_mixed, (const void*)k_apply64,
-                      (const void*)k_apply32};
+                      (const void*)k_apply32, (const void*)k_level_adj};
   for (const void* k : ks) {
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, smem) != cudaSuccess) return 0;
@@ -221,6 +284,22 @@ cudaError_t launch_level(const LevelArgs& a, int mixed, cudaStream_t s) {
   void* args[] = {(void*)&a};
   return cudaLaunchCooperativeKernel(mixed ? (const void*)k_level_mixed : (const void*)k_level64,
                                      dim3(a.P.G), dim3(kThreads), args, smem, s);
+}
+
+cudaError_t launch_adj_rhs(const AdjRhsArgs& a, cudaStream_t s) {
+  int grid = (a.n + kThreads - 1) / kThreads;
+  if (grid < 1) grid = 1;
+  const size_t smem = 3 * (size_t)(a.Eact > 0 ? a.Eact : 1) * sizeof(double);
+  k_adj_rhs<<<grid, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_level_adj(const LevelArgs& a, const AdjGradArgs& g, cudaStream_t s) {
+  size_t smem = plan_smem_bytes(a.P);
+  cudaError_t e = cudaMemsetAsync(a.P.bar, 0, sizeof(GridBarrier), s);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&a, (void*)&g};
+  return cudaLaunchCooperativeKernel((const void*)k_level_adj, dim3(a.P.G), dim3(kThreads), args, smem, s);
 }
 
 cudaError_t launch_apply(const ApplyArgs& a, int fp32, cudaStream_t s) {

@@ -140,6 +140,30 @@ struct RhsArgs {
   float* kappa32;
 };
 
+// Adjoint sweep (reverse time): the right-hand side g^m of the transposed
+// level system from lambda^{m+1} through the reversed SOE recurrence
+//   Y_j <- eps_{j,m+1} (lambda^{m+1} + Y_j),
+//   g^m = ahat_{m+1} lambda^{m+1} - sum_j (c_{j,m+1} Y_j^new - c_{j,m+2} Y_j^old)
+// (c_{j,k} = w_j beta_{j,k-1} / Gamma(1-gamma), the forward coefficients).
+struct AdjRhsArgs {
+  int n, ld, Eact;      // Eact = active exponentials at level m+1
+  double ahat1;         // ahat_{m+1}
+  double* Y;            // E x ld reversed history
+  const double* eps1;   // eps_{j,m+1}
+  const double* c1;     // c_{j,m+1}
+  const double* c2;     // c_{j,m+2}, NULL when m+2 > M
+  const double* lam1;   // lambda^{m+1}
+  double* g;
+};
+
+// Gradient terms of one adjoint level: grad_kappa -= lambda .* (A u^m),
+// grad_f += lambda, after the transposed solve of that level.
+struct AdjGradArgs {
+  const double* um;     // forward solution u^m
+  double* grad_kappa;
+  double* grad_f;
+};
+
 struct ApplyArgs {
   DevPlan P;
   int kind;         // 0: y = a v + kappa .* (A v)  (kappa NULL -> 1)
@@ -165,6 +189,10 @@ size_t cluster_smem_bytes(const DevPlan& P);
 // dynamic shared bytes per CTA, 0 if the engine cannot be launched.
 int cluster_max_grid(const DevPlan& P, size_t smem);
 cudaError_t launch_apply(const ApplyArgs& a, int fp32, cudaStream_t s);
+// adjoint: reversed SOE right-hand side; FP64 transposed level solve with
+// the gradient accumulation fused behind it
+cudaError_t launch_adj_rhs(const AdjRhsArgs& a, cudaStream_t s);
+cudaError_t launch_level_adj(const LevelArgs& a, const AdjGradArgs& g, cudaStream_t s);
 // out64 = in, out32 = (float) in
 cudaError_t launch_convert(const double* in, double* out64, float* out32, int n, cudaStream_t s);
 // CTAs per SM that every cooperative kernel can co-schedule with `smem`
