@@ -231,6 +231,56 @@ int tsfde_get_symbol(const tsfde_ctx* ctx, double* t);
 int tsfde_adjoint(tsfde_ctx* ctx, const double* u_all, const double* dJ_duM,
                   double* grad_kappa, double* grad_f, tsfde_adjoint_info* info);
 
+/* ---- batched solve: many independent problems in one launch ----------
+ * The paper solves one problem at a time; this runs B independent FIDS
+ * problems (each with its own n, alpha, gamma, grading, SOE table and
+ * data) over a common number of levels M, as one persistent launch of
+ * thread-block clusters: a cluster claims an instance, marches it through
+ * all M levels (SOE update, FP64 Strang preconditioner, level solve) with
+ * its transforms in distributed shared memory, writes u^M and claims the
+ * next.  Instances are taken largest first.  kappa and f are time
+ * independent per instance.  Options (tsfde_opts): mu / kappa_mu (common),
+ * precision (MIXED: FP32 PBiCGSTAB sweeps refined in FP64 with the FP64
+ * fallback of the single-problem path; FP64: PBiCGSTAB in FP64),
+ * krylov_tol, max_it, inner_tol, max_outer, inner_max_it, precond, stream.
+ * Each instance needs n >= 31 (its transforms are split over the cluster). */
+typedef struct tsfde_instance {
+  double alpha, gamma, l, T, r;  /* as tsfde_setup                           */
+  int64_t n;                     /* interior nodes, 31 <= n <= 16383         */
+  double soe_tol;                /* SOE relative tolerance, (0, 1e-2]        */
+  const double* phi;             /* dev n: u^0                               */
+  const double* kappa;           /* dev n: diffusivity (> 0), all levels     */
+  const double* f;               /* dev n: source, all levels                */
+} tsfde_instance;
+
+typedef struct tsfde_batch tsfde_batch;
+
+typedef struct tsfde_batch_info {
+  int status;              /* first non-OK instance status, else TSFDE_OK   */
+  int failed_instance;     /* index of that instance, -1 if none            */
+  int64_t levels;          /* instances x M                                 */
+  int64_t iterations;      /* all Krylov iterations (inner + FP64)          */
+  int64_t outer;           /* refinement sweeps (mixed)                     */
+  int64_t fp64_levels;     /* levels finished by the FP64 fallback          */
+  double max_rel_residual; /* worst final relative residual of any level    */
+} tsfde_batch_info;
+
+/* Copies phi, kappa, f of every instance and builds all tables; the caller's
+ * buffers need not outlive the call.  Errors: TSFDE_EINVAL (arguments, as
+ * tsfde_setup per instance), TSFDE_ENOTSUP (an instance too small or too
+ * large for the cluster transforms), TSFDE_ENOMEM. */
+int tsfde_batch_setup(tsfde_batch** out, int B, const tsfde_instance* inst, int64_t M,
+                      const tsfde_opts* opts);
+/* Solve every instance from u^0 through level M; u_final: host array of B
+ * device pointers (n_i doubles each) that receive u^M.  Synchronises. */
+int tsfde_batch_solve(tsfde_batch* b, double* const* u_final, tsfde_batch_info* info);
+/* Per-instance totals of the last solve (status, iterations, outer = sweeps,
+ * E_active = levels finished in FP64, rel_residual = worst level). */
+int tsfde_batch_instance_stats(const tsfde_batch* b, int i, tsfde_step_info* out);
+/* Thread-block clusters the persistent launch uses and CTAs per cluster. */
+int tsfde_batch_shape(const tsfde_batch* b, int* clusters, int* cluster_size);
+void tsfde_batch_destroy(tsfde_batch* b);
+
 /* Engine the context's mixed level solves use: TSFDE_ENGINE_GRID or
  * TSFDE_ENGINE_CLUSTER (never AUTO); -1 if ctx is NULL. */
 int tsfde_get_engine(const tsfde_ctx* ctx);

@@ -60,6 +60,20 @@ class tsfde_adjoint_info(ctypes.Structure):
                 ("max_rel_residual", ctypes.c_double)]
 
 
+class tsfde_instance(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("gamma", ctypes.c_double), ("l", ctypes.c_double),
+                ("T", ctypes.c_double), ("r", ctypes.c_double), ("n", ctypes.c_int64),
+                ("soe_tol", ctypes.c_double), ("phi", ctypes.c_void_p), ("kappa", ctypes.c_void_p),
+                ("f", ctypes.c_void_p)]
+
+
+class tsfde_batch_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("failed_instance", ctypes.c_int),
+                ("levels", ctypes.c_int64), ("iterations", ctypes.c_int64),
+                ("outer", ctypes.c_int64), ("fp64_levels", ctypes.c_int64),
+                ("max_rel_residual", ctypes.c_double)]
+
+
 class tsfde_timing(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int64), ("rhs_ms", ctypes.c_double),
                 ("level_ms", ctypes.c_double)]
@@ -87,6 +101,13 @@ _SIGNATURES = [
     ("tsfde_get_timing", ctypes.c_int, [_V, ctypes.POINTER(tsfde_timing)]),
     ("tsfde_get_engine", ctypes.c_int, [_V]),
     ("tsfde_adjoint", ctypes.c_int, [_V, _V, _V, _V, _V, ctypes.POINTER(tsfde_adjoint_info)]),
+    ("tsfde_batch_setup", ctypes.c_int, [ctypes.POINTER(_V), ctypes.c_int,
+                                         ctypes.POINTER(tsfde_instance), ctypes.c_int64,
+                                         ctypes.POINTER(tsfde_opts)]),
+    ("tsfde_batch_solve", ctypes.c_int, [_V, ctypes.POINTER(_V), ctypes.POINTER(tsfde_batch_info)]),
+    ("tsfde_batch_instance_stats", ctypes.c_int, [_V, ctypes.c_int, ctypes.POINTER(tsfde_step_info)]),
+    ("tsfde_batch_shape", ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    ("tsfde_batch_destroy", None, [_V]),
     ("tsfde_get_level_stats", ctypes.c_int, [_V, ctypes.c_int64, ctypes.c_int64,
                                              ctypes.POINTER(tsfde_step_info)]),
     ("tsfde_get_solution", ctypes.c_int, [_V, _V]),
@@ -339,6 +360,74 @@ class Solver:
         _check(self.lib.tsfde_linear_solve(self.ctx, a, _dev(kappa, self.n, "kappa"),
                                            _dev(b, self.n, "b"), _dev(x, self.n, "x"),
                                            ctypes.byref(info)), self.ctx)
+        return _info_dict(info)
+
+
+class BatchSolver:
+    """Many independent FIDS problems over a common M (tsfde_batch_*).
+
+    instances: list of dicts with alpha, gamma, n, phi, kappa, f (CUDA
+    float64 tensors of n entries; kappa and f time independent) and optional
+    l (1), T (1), r ((2-gamma)/gamma), soe_tol (1e-12)."""
+
+    def __init__(self, instances, M, *, precision="mixed", precond="strang", krylov_tol=1e-12,
+                 max_it=2000, inner_tol=1e-2, max_outer=60, inner_max_it=40, mu=None,
+                 kappa_mu=None, stream=None):
+        lib = load_library()
+        o = default_opts()
+        o.krylov_tol = krylov_tol
+        o.max_it = max_it
+        o.precision = {"fp64": TSFDE_FP64, "mixed": TSFDE_MIXED}[precision]
+        o.precond = {"strang": TSFDE_STRANG, "none": TSFDE_PRECOND_NONE}[precond]
+        o.inner_tol = inner_tol
+        o.max_outer = max_outer
+        o.inner_max_it = inner_max_it
+        o.mu = 0.0 if mu is None else mu
+        o.kappa_mu = 0 if kappa_mu is None else kappa_mu
+        if stream is not None:
+            o.stream = _stream_handle(stream)
+        B = len(instances)
+        arr = (tsfde_instance * B)()
+        self.ns = []
+        for i, d in enumerate(instances):
+            g = float(d["gamma"])
+            n = int(d["n"])
+            arr[i] = tsfde_instance(float(d["alpha"]), g, float(d.get("l", 1.0)), float(d.get("T", 1.0)),
+                                    float(d.get("r", (2.0 - g) / g)), n, float(d.get("soe_tol", 1e-12)),
+                                    _dev(d["phi"], n, "phi"), _dev(d["kappa"], n, "kappa"),
+                                    _dev(d["f"], n, "f"))
+            self.ns.append(n)
+        self.lib = lib
+        self.B, self.M = B, int(M)
+        self.ctx = ctypes.c_void_p()
+        _check(lib.tsfde_batch_setup(ctypes.byref(self.ctx), B, arr, self.M, ctypes.byref(o)))
+
+    def __del__(self):
+        if getattr(self, "ctx", None):
+            self.lib.tsfde_batch_destroy(self.ctx)
+            self.ctx = None
+
+    @property
+    def shape(self):
+        c, q = ctypes.c_int(), ctypes.c_int()
+        _check(self.lib.tsfde_batch_shape(self.ctx, ctypes.byref(c), ctypes.byref(q)))
+        return c.value, q.value
+
+    def solve(self, u_final):
+        """u_final: list of B CUDA float64 tensors (n_i entries) receiving u^M."""
+        if len(u_final) != self.B:
+            raise ValueError("need one output per instance")
+        ptrs = (ctypes.c_void_p * self.B)(*[_dev(u, n, "u_final").value for u, n in zip(u_final, self.ns)])
+        info = tsfde_batch_info()
+        rc = self.lib.tsfde_batch_solve(self.ctx, ptrs, ctypes.byref(info))
+        out = _info_dict(info)
+        if rc != TSFDE_OK:
+            raise TsfdeError(rc, f"{self.lib.tsfde_strerror(rc).decode()}: batch solve, {out}")
+        return out
+
+    def instance_stats(self, i):
+        info = tsfde_step_info()
+        _check(self.lib.tsfde_batch_instance_stats(self.ctx, i, ctypes.byref(info)))
         return _info_dict(info)
 
 

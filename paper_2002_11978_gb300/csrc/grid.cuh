@@ -458,12 +458,6 @@ __device__ bool build_precond(const DevPlan& P, const Smem<R>& sm, double ahat, 
 }
 
 // ------------------------------------------------------------- PBiCGSTAB
-struct SolveRes {
-  int status;
-  int iters;
-  double relres;
-};
-
 // Right-preconditioned BiCGSTAB (van der Vorst) for (ahat I + K A) x = b,
 // x0 = 0, stop when ||r_k||_2 / ||b||_2 < tol (Sec. 5).  binit(i) gives b_i.
 // Per iteration: P^{-1}p, A p^, P^{-1}s, A s^ as zero-padded FFT products.

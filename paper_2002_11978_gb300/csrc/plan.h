@@ -45,6 +45,33 @@ struct CGeo {
   int G;         // CTAs of the cluster-engine launch (a multiple of Q)
 };
 
+// One transform geometry on the cluster, held in registers by every pass.
+struct CeGeo {
+  int n;           // vector entries the epilogues see
+  int L;           // base of the twiddle tables W_L
+  int tws;         // column-twiddle stride L / Nfft
+  int N1, N2, lgN1, lgN2;
+  int Q, cQ, lgcQ, U, lgU, Bq, lgBq, nbuf;
+  int T1, LT, lgLT;  // tables: hi = W_{T1}^k (k < T1), lo = W_L^l (l < LT = L/T1)
+  int q;           // this CTA's rank
+};
+
+// Shared-memory layout (bytes): C [capB] | S [capB] | R [nbufB] |
+// FP64 tables (if has64) | FP32 tables | part [6 x kMaxQ doubles] | red [64]
+// | context.  C and S hold nbuf elements plus the staging padding.
+struct CeLay {
+  int capB, nbufB;
+  int T1, LT;
+  int has64;
+};
+
+// Result of one Krylov solve.
+struct SolveRes {
+  int status;
+  int iters;
+  double relres;
+};
+
 // Everything a cooperative kernel needs to run the FIDS level solve.
 struct DevPlan {
   int n;       // unknowns
@@ -118,6 +145,54 @@ struct LevelArgs {
   int probe;          // cluster engine: return at once (launch check)
 };
 
+// One instance of the batched solve (device-resident descriptor).  All
+// vectors are per-instance slices of pooled device arrays; FP32 / FP64
+// Krylov vectors have an even length.
+struct BInst {
+  int n, E, ld;          // unknowns, SOE size, leading dimension of H (even)
+  CeGeo gr, gc;          // real-input (Nfft = L/2) and complex (Nfft = L) geometry
+  int tstride;           // twiddle stride: Lmax / L
+  double kbar;           // mean of kappa (time independent)
+  const double* phi;
+  const double* kap64;
+  const float* kap32;
+  const double* f;
+  double* H;             // E x ld scaled SOE history
+  double* u[3];          // rotating levels
+  double* r64;           // FP64 residual (holds b at the start of a level)
+  double* w;             // FP64 scratch (M e, preconditioner column g)
+  KVecs<float> v32;
+  KVecs<double> v64;
+  const double* ahat;    // M+1
+  const double* eps;     // (M+1) x E
+  const double* cw;      // (M+1) x E
+  const int* Eact;       // M+1
+  const double* lam;     // Strang eigenvalues (n)
+  const double2* chirp;  // e^{+pi i j^2/n}, j < n
+  const double2* Bh;     // Bluestein kernel spectrum / L, row-pass order of gc
+  const double2* spT64;  // Toeplitz spectrum pairs, row-pass order of gr
+  const float2* spT32;
+  double2* spG64;        // preconditioner spectrum pairs (per level)
+  float2* spG32;
+  double* u_out;         // caller's u^M (set by each solve)
+  StepStat* stat;        // totals: iterations, outer (sum of |outer|),
+                         // E_active = FP64-finished levels, worst relres
+};
+
+struct BatchArgs {
+  BInst* inst;
+  int count;
+  int M;
+  int* next;             // instance counter (zeroed before the launch)
+  int precision;         // TSFDE_FP64 or TSFDE_MIXED
+  int precond;
+  double tol, inner_tol;
+  int max_it, max_outer, inner_max_it;
+  const double2* tw64;   // W_Lmax^k
+  const float2* tw32;
+  CeLay lay;             // shared-memory layout (sized for the largest instance)
+};
+
 struct RhsArgs {
   int n, ld, Eact;
   double ahat;
@@ -189,6 +264,11 @@ size_t cluster_smem_bytes(const DevPlan& P);
 // dynamic shared bytes per CTA, 0 if the engine cannot be launched.
 int cluster_max_grid(const DevPlan& P, size_t smem);
 cudaError_t launch_apply(const ApplyArgs& a, int fp32, cudaStream_t s);
+// batched engine (batch.cu): one persistent launch of clusters of Q CTAs,
+// each marching whole instances through all M levels
+size_t batch_smem_bytes(const CeLay& lay);
+int batch_max_clusters(int Q, size_t smem);
+cudaError_t launch_batch(const BatchArgs& a, int Q, int clusters, cudaStream_t s);
 // adjoint: reversed SOE right-hand side; FP64 transposed level solve with
 // the gradient accumulation fused behind it
 cudaError_t launch_adj_rhs(const AdjRhsArgs& a, cudaStream_t s);

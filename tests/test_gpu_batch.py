@@ -1,0 +1,119 @@
+"""Batched solve (tsfde_batch_*): many independent FIDS problems in one
+persistent launch of thread-block clusters.  Each instance is checked
+against the oracle's dense-LU FIDS march at small sizes, and against the
+single-problem GPU path (FP64) at the batched workload's sizes, including
+its Krylov iteration counts (which a wrong preconditioner would change)."""
+import numpy as np
+import pytest
+
+import oracle
+import tsfde_inputs as ti
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+    assert T.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2002_11978_gb300 import build
+    build.build()
+    return T
+
+
+def cuda(torch, a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _instances(torch, specs, M):
+    """specs: list of (i, n, alpha, gamma) -> (instance dicts, problems)."""
+    inst, probs = [], []
+    for i, n, a, g in specs:
+        p = ti.config_batched_instance(i, n, a, g, M=M)
+        probs.append(p)
+        inst.append(dict(alpha=p.alpha, gamma=p.gamma, n=p.n, r=p.r, phi=cuda(torch, p.phi),
+                         kappa=cuda(torch, p.kappa0), f=cuda(torch, p.F[0])))
+    return inst, probs
+
+
+def _batch(torch, inst, M, **kw):
+    import paper_2002_11978_gb300 as pkg
+    bs = pkg.BatchSolver(inst, M, **kw)
+    outs = [torch.zeros(d["n"], dtype=torch.float64, device="cuda") for d in inst]
+    info = bs.solve(outs)
+    return bs, [u.cpu().numpy() for u in outs], info
+
+
+def _single(torch, p, precision="fp64"):
+    import paper_2002_11978_gb300 as pkg
+    s = pkg.Solver(p.alpha, p.gamma, p.l, p.T, p.n, p.M, p.r, 1e-12, precision=precision)
+    s.set_problem(cuda(torch, p.phi), cuda(torch, p.kappa0), None, None, F=[cuda(torch, p.F[0])],
+                  G=[np.ones(p.M + 1)])
+    uf = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    info = s.solve(uf)
+    assert info["status"] == 0, info
+    return uf.cpu().numpy(), info
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_matches_oracle(torch, precision):
+    """Five instances of different n, alpha, gamma (cluster sizes from 4 to
+    8 CTAs' worth of rows), M = 12: each u^M against the oracle's dense FIDS
+    march with its plain SOE table (both tables within 1e-12)."""
+    M = 12
+    specs = [(0, 63, 1.5, 0.5), (1, 127, 0.8, 0.3), (2, 200, 1.9, 0.8), (3, 511, 1.2, 0.6),
+             (4, 96, 0.6, 0.2)]
+    inst, probs = _instances(torch, specs, M)
+    bs, U, info = _batch(torch, inst, M, precision=precision)
+    assert info["status"] == 0 and info["iterations"] > 0, info
+    for p, u in zip(probs, U):
+        tm, tau = oracle.graded_mesh(p.T, M, p.r)
+        soe = oracle.soe_build(p.gamma, tau[1], p.T, 1e-12)
+        ref = oracle.march("FIDS", p.alpha, p.gamma, p.l, p.T, p.r, p.n, M, p.phi,
+                           np.tile(p.kappa0, (M + 1, 1)), np.tile(p.F[0], (M + 1, 1)), soe=soe)[M]
+        err = np.max(np.abs(u - ref)) / np.max(np.abs(ref))
+        assert err < 1e-10, (p.n, err)
+
+
+def test_batch_matches_single_problem_path(torch):
+    """Instances at the batched workload's sizes (n up to 2^14 - 1), M = 8,
+    FP64 on both sides: same u^M, same preconditioned iteration counts."""
+    M = 8
+    specs = [(10, 16383, 1.7, 0.4), (11, 4095, 0.9, 0.7), (12, 1023, 1.3, 0.25), (13, 511, 1.85, 0.5)]
+    inst, probs = _instances(torch, specs, M)
+    bs, U, info = _batch(torch, inst, M, precision="fp64")
+    assert info["status"] == 0, info
+    for k, (p, u) in enumerate(zip(probs, U)):
+        ref, sinfo = _single(torch, p)
+        assert np.max(np.abs(u - ref)) / np.max(np.abs(ref)) < 1e-10
+        its = bs.instance_stats(k)["iterations"]
+        assert abs(its - sinfo["iterations"]) <= 0.15 * sinfo["iterations"] + 2, (its, sinfo)
+
+
+def test_batch_mixed_matches_fp64(torch):
+    """Mixed precision (FP32 sweeps, FP64 refinement) against FP64 on a
+    sample of the batched workload's instances, M = 32."""
+    M = 32
+    ns, al, ga = ti.batched_instance_params()
+    specs = [(i, int(ns[i]), float(al[i]), float(ga[i])) for i in (0, 5, 17, 42, 99, 311)]
+    inst, probs = _instances(torch, specs, M)
+    _, Um, im = _batch(torch, inst, M, precision="mixed")
+    _, Ud, idd = _batch(torch, inst, M, precision="fp64")
+    assert im["status"] == 0 and idd["status"] == 0, (im, idd)
+    for um, ud in zip(Um, Ud):
+        assert np.max(np.abs(um - ud)) / np.max(np.abs(ud)) < 1e-10
+
+
+def test_batch_edge_sizes_and_validation(torch):
+    import paper_2002_11978_gb300 as pkg
+    M = 3
+    inst, probs = _instances(torch, [(0, 31, 1.5, 0.5), (1, 33, 1.1, 0.7)], M)
+    bs, U, info = _batch(torch, inst, M, precision="fp64")
+    assert bs.shape[1] == 4  # n = 31 splits over at most 4 CTAs
+    for p, u in zip(probs, U):
+        ref, _ = _single(torch, p)
+        assert np.max(np.abs(u - ref)) / np.max(np.abs(ref)) < 1e-10
+    bad, _ = _instances(torch, [(0, 15, 1.5, 0.5)], M)
+    with pytest.raises(pkg.TsfdeError) as e:
+        pkg.BatchSolver(bad, M)
+    assert e.value.status == pkg.TSFDE_ENOTSUP
