@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=255)
+    ap.add_argument("--batched-levels", type=int, default=128,
+                    help="levels of the batched workload timed (of M = 1024; 0 skips it)")
     return ap.parse_args()
 
 
@@ -180,6 +182,50 @@ def run_arm(torch, pkg, prob, precision, W, K, flush, stream, e2e=False):
     return s, ms, tim, tot
 
 
+def batched_sample(torch, pkg, ti, levels, rank, world, stream):
+    """The batched workload: 512 independent problems (n log-uniform in
+    [2^9-1, 2^14-1], alpha ~ U(0.6, 1.9), gamma ~ U(0.2, 0.9), M = 1024),
+    this rank's share (instance i on rank i mod world), first `levels`
+    levels, mixed and FP64, one persistent cluster launch each.  Its working
+    set (the SOE histories, ~3 GB) is far above L2."""
+    M = 1024
+    ns, al, ga = ti.batched_instance_params()
+    mine = [i for i in range(len(ns)) if i % world == rank]
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    inst = []
+    for i in mine:
+        p = ti.config_batched_instance(i, int(ns[i]), float(al[i]), float(ga[i]), M=M)
+        inst.append(dict(alpha=p.alpha, gamma=p.gamma, n=p.n, r=p.r, phi=dev(p.phi),
+                         kappa=dev(p.kappa0), f=dev(p.F[0])))
+    unknowns = sum(d["n"] for d in inst)
+    out = {"workload": "fids-batched 512 instances n=U_log[511,16383] M=1024 (alpha, gamma random)",
+           "instances": len(inst), "levels_timed": levels, "unknowns": unknowns}
+    us = {}
+    for prec in ("mixed", "fp64"):
+        bs = pkg.BatchSolver(inst, M, precision=prec, stream=stream)
+        outs = [torch.zeros(d["n"], dtype=torch.float64, device="cuda") for d in inst]
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            info = bs.solve(outs, levels=levels)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        clusters, q = bs.shape
+        out[prec] = {"s": t, "instance_levels_per_s": len(inst) * levels / t,
+                     "unknown_levels_per_s": unknowns * levels / t,
+                     "krylov_its": info["iterations"], "outer": info["outer"],
+                     "fp64_levels": info["fp64_levels"], "status": info["status"],
+                     "clusters": clusters, "cluster_size": q}
+        us[prec] = [u.cpu().numpy() for u in outs]
+        del bs
+    out["mixed_vs_fp64_max_rel_err"] = max(
+        float(np.max(np.abs(a - b)) / np.max(np.abs(b))) for a, b in zip(us["mixed"], us["fp64"]))
+    out["mixed_speedup"] = out["fp64"]["s"] / out["mixed"]["s"]
+    return out
+
+
 def current_u(torch, s):
     u = torch.zeros(s.n, dtype=torch.float64, device="cuda")
     s.current_solution(u)
@@ -261,6 +307,16 @@ def ours(args):
     roof = {"kernel": dom[0], "bound": "hbm", "achieved": dom[1], "peak": peak, "unit": "GB/s",
             "frac": dom[1] / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs"}
 
+    batched = None
+    if args.batched_levels > 0:
+        batched = batched_sample(torch, pkg, ti, args.batched_levels, rank, world, stream)
+        if world > 1:
+            t = torch.tensor([batched["mixed"]["s"], batched["fp64"]["s"]], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            for k, prec in enumerate(("mixed", "fp64")):
+                batched[prec]["s_max_over_ranks"] = float(t[k].item())
+                batched[prec]["instance_levels_per_s"] = 512 * args.batched_levels / float(t[k].item())
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample(prob, args.cpu_sample_n, budget_s=20.0)
@@ -282,7 +338,7 @@ def ours(args):
                         "k_level_mixed": {"ms": lvl_ms, "bytes": lvl_bytes, "GB/s": lvl_gbs,
                                           "frac": lvl_gbs / peak}},
             "fp64": fp64, "e2e": e2e, "gpu_launches": 2 * K, "roofline": roof,
-            "cpu_baseline": cpu, "clocks": clk,
+            "cpu_baseline": cpu, "clocks": clk, "batched": batched,
         }
         print(json.dumps(line), flush=True)
     s_mx.close()

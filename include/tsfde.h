@@ -96,6 +96,9 @@ typedef struct tsfde_opts {
                            asking for CLUSTER where it cannot run fails
                            tsfde_setup with TSFDE_ENOTSUP; FP64 contexts
                            ignore the field                                 */
+  int cluster_size;     /* batched solve: CTAs per thread-block cluster,
+                           4, 8 or 16; 0 (default) picks the size that keeps
+                           the most CTAs resident                           */
 } tsfde_opts;
 
 typedef struct tsfde_step_info {
@@ -258,7 +261,7 @@ typedef struct tsfde_batch tsfde_batch;
 typedef struct tsfde_batch_info {
   int status;              /* first non-OK instance status, else TSFDE_OK   */
   int failed_instance;     /* index of that instance, -1 if none            */
-  int64_t levels;          /* instances x M                                 */
+  int64_t levels;          /* instances x levels solved                     */
   int64_t iterations;      /* all Krylov iterations (inner + FP64)          */
   int64_t outer;           /* refinement sweeps (mixed)                     */
   int64_t fp64_levels;     /* levels finished by the FP64 fallback          */
@@ -271,9 +274,11 @@ typedef struct tsfde_batch_info {
  * large for the cluster transforms), TSFDE_ENOMEM. */
 int tsfde_batch_setup(tsfde_batch** out, int B, const tsfde_instance* inst, int64_t M,
                       const tsfde_opts* opts);
-/* Solve every instance from u^0 through level M; u_final: host array of B
- * device pointers (n_i doubles each) that receive u^M.  Synchronises. */
-int tsfde_batch_solve(tsfde_batch* b, double* const* u_final, tsfde_batch_info* info);
+/* Solve every instance from u^0 through level `levels` (1..M; 0 = M) of
+ * its M-level mesh; u_final: host array of B device pointers (n_i doubles
+ * each) that receive u^levels.  Synchronises. */
+int tsfde_batch_solve(tsfde_batch* b, int64_t levels, double* const* u_final,
+                      tsfde_batch_info* info);
 /* Per-instance totals of the last solve (status, iterations, outer = sweeps,
  * E_active = levels finished in FP64, rel_residual = worst level). */
 int tsfde_batch_instance_stats(const tsfde_batch* b, int i, tsfde_step_info* out);

@@ -37,7 +37,7 @@ class tsfde_opts(ctypes.Structure):
                 ("inner_max_it", ctypes.c_int),
                 ("soe_E", ctypes.c_int), ("soe_s", _dp), ("soe_w", _dp), ("profile", ctypes.c_int),
                 ("barrier_timeout_cycles", ctypes.c_longlong), ("stream", ctypes.c_void_p),
-                ("engine", ctypes.c_int)]
+                ("engine", ctypes.c_int), ("cluster_size", ctypes.c_int)]
 
 
 class tsfde_step_info(ctypes.Structure):
@@ -104,7 +104,8 @@ _SIGNATURES = [
     ("tsfde_batch_setup", ctypes.c_int, [ctypes.POINTER(_V), ctypes.c_int,
                                          ctypes.POINTER(tsfde_instance), ctypes.c_int64,
                                          ctypes.POINTER(tsfde_opts)]),
-    ("tsfde_batch_solve", ctypes.c_int, [_V, ctypes.POINTER(_V), ctypes.POINTER(tsfde_batch_info)]),
+    ("tsfde_batch_solve", ctypes.c_int, [_V, ctypes.c_int64, ctypes.POINTER(_V),
+                                         ctypes.POINTER(tsfde_batch_info)]),
     ("tsfde_batch_instance_stats", ctypes.c_int, [_V, ctypes.c_int, ctypes.POINTER(tsfde_step_info)]),
     ("tsfde_batch_shape", ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("tsfde_batch_destroy", None, [_V]),
@@ -372,9 +373,10 @@ class BatchSolver:
 
     def __init__(self, instances, M, *, precision="mixed", precond="strang", krylov_tol=1e-12,
                  max_it=2000, inner_tol=1e-2, max_outer=60, inner_max_it=40, mu=None,
-                 kappa_mu=None, stream=None):
+                 kappa_mu=None, stream=None, cluster_size=0):
         lib = load_library()
         o = default_opts()
+        o.cluster_size = cluster_size
         o.krylov_tol = krylov_tol
         o.max_it = max_it
         o.precision = {"fp64": TSFDE_FP64, "mixed": TSFDE_MIXED}[precision]
@@ -413,13 +415,14 @@ class BatchSolver:
         _check(self.lib.tsfde_batch_shape(self.ctx, ctypes.byref(c), ctypes.byref(q)))
         return c.value, q.value
 
-    def solve(self, u_final):
-        """u_final: list of B CUDA float64 tensors (n_i entries) receiving u^M."""
+    def solve(self, u_final, levels=0):
+        """u_final: list of B CUDA float64 tensors (n_i entries) receiving
+        u^levels (levels = 0: u^M)."""
         if len(u_final) != self.B:
             raise ValueError("need one output per instance")
         ptrs = (ctypes.c_void_p * self.B)(*[_dev(u, n, "u_final").value for u, n in zip(u_final, self.ns)])
         info = tsfde_batch_info()
-        rc = self.lib.tsfde_batch_solve(self.ctx, ptrs, ctypes.byref(info))
+        rc = self.lib.tsfde_batch_solve(self.ctx, int(levels), ptrs, ctypes.byref(info))
         out = _info_dict(info)
         if rc != TSFDE_OK:
             raise TsfdeError(rc, f"{self.lib.tsfde_strerror(rc).decode()}: batch solve, {out}")

@@ -125,6 +125,7 @@ int tsfde_default_opts(tsfde_opts* o) {
   o->barrier_timeout_cycles = 0;
   o->stream = nullptr;
   o->engine = TSFDE_ENGINE_AUTO;
+  o->cluster_size = 0;
   return TSFDE_OK;
 }
 

@@ -243,14 +243,47 @@ int tsfde_batch_setup(tsfde_batch** out, int B, const tsfde_instance* inst, int6
   b->M = M;
   b->opts = o;
   b->stream = static_cast<cudaStream_t>(o.stream);
-  // cluster size: the largest power of two <= 8 every instance can split
-  int Q = 8;
+  // cluster size: among 4, 8, 16 (or the caller's), those every instance can
+  // split and whose shared-memory layout fits; pick the one keeping the most
+  // CTAs resident (ties: the smaller cluster)
+  int Q = 0;
   {
-    int Lmin = 8;
+    int Lmin = 8, Lmax0 = 8;
     while (Lmin < 2 * nmin - 1) Lmin *= 2;
-    const int lg = ilg(Lmin / 2);
-    const int N1 = 1 << ((lg + 1) / 2), N2 = (Lmin / 2) / N1;
-    while (Q > 1 && (2 * Q > N1 || Q > N2)) Q >>= 1;
+    while (Lmax0 < 2 * nmax - 1) Lmax0 *= 2;
+    const int lgs = ilg(Lmin / 2);
+    const int N1s = 1 << ((lgs + 1) / 2), N2s = (Lmin / 2) / N1s;
+    int dev0 = 0, optin0 = 0;
+    cudaGetDevice(&dev0);
+    cudaDeviceGetAttribute(&optin0, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev0);
+    int best = 0;
+    for (int q : {4, 8, 16}) {
+      if (o.cluster_size > 0 && q != o.cluster_size) continue;
+      if (2 * q > N1s || q > N2s) continue;
+      // layout of the largest transform (complex, length Lmax0) with q CTAs
+      const int lgL = ilg(Lmax0);
+      const int N1c = 1 << ((lgL + 1) / 2);
+      CeLay y{};
+      y.has64 = 1;
+      y.capB = (Lmax0 / q + N1c) * (int)sizeof(double2);
+      y.nbufB = (Lmax0 / q) * (int)sizeof(double2);
+      y.T1 = N1c;
+      y.LT = Lmax0 / N1c;
+      y.capB = std::max(y.capB, 2 * 4096 * (int)sizeof(double));  // SOE factors
+      const size_t sm = batch_smem_bytes(y);
+      if (sm > (size_t)optin0) continue;
+      const int res = batch_max_clusters(q, sm) * q;
+      if (res > best) { best = res; Q = q; }
+    }
+    if (o.cluster_size > 0 && o.cluster_size != 4 && o.cluster_size != 8 && o.cluster_size != 16) {
+      delete b;
+      return TSFDE_EINVAL;
+    }
+    if (Q == 0) {
+      const int st = bfail(b, TSFDE_ENOTSUP, "no cluster size fits these instances on this device");
+      tsfde_batch_destroy(b);
+      return st;
+    }
   }
   b->Q = Q;
   // host tables, in parallel
@@ -280,6 +313,7 @@ int tsfde_batch_setup(tsfde_batch** out, int B, const tsfde_instance* inst, int6
     }
   }
   // shared-memory layout for the largest transform
+  bool ok_sizes = true;
   int Lmax = 8;
   CeLay lay{};
   lay.has64 = 1;
@@ -292,8 +326,14 @@ int tsfde_batch_setup(tsfde_batch** out, int B, const tsfde_instance* inst, int6
     lay.LT = std::max(lay.LT, h.gc.LT);
     // the right-hand side stages the level's SOE factors in S
     lay.capB = std::max(lay.capB, 2 * std::max(h.E, 1) * (int)sizeof(double));
+    if (h.E > 4096) ok_sizes = false;
   }
   b->lay = lay;
+  if (!ok_sizes) {
+    const int st = bfail(b, TSFDE_ENOTSUP, "SOE table longer than 4096 exponentials");
+    tsfde_batch_destroy(b);
+    return st;
+  }
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -420,8 +460,10 @@ int tsfde_batch_setup(tsfde_batch** out, int B, const tsfde_instance* inst, int6
   return TSFDE_OK;
 }
 
-int tsfde_batch_solve(tsfde_batch* b, double* const* u_final, tsfde_batch_info* info) {
-  if (!b || !u_final) return TSFDE_EINVAL;
+int tsfde_batch_solve(tsfde_batch* b, int64_t levels, double* const* u_final,
+                      tsfde_batch_info* info) {
+  if (!b || !u_final || levels < 0 || levels > b->M) return TSFDE_EINVAL;
+  if (levels == 0) levels = b->M;
   for (int i = 0; i < b->B; ++i)
     if (!u_final[i]) return TSFDE_EINVAL;
   // descriptors in launch order, each with its output and stats slot
@@ -438,7 +480,7 @@ int tsfde_batch_solve(tsfde_batch* b, double* const* u_final, tsfde_batch_info* 
   BatchArgs A{};
   A.inst = b->dinst;
   A.count = b->B;
-  A.M = (int)b->M;
+  A.M = (int)levels;
   A.next = b->dnext;
   A.precision = b->opts.precision;
   A.precond = b->opts.precond == TSFDE_STRANG ? 1 : 0;
@@ -460,7 +502,7 @@ int tsfde_batch_solve(tsfde_batch* b, double* const* u_final, tsfde_batch_info* 
   }
   tsfde_batch_info inf{};
   inf.failed_instance = -1;
-  inf.levels = (int64_t)b->B * b->M;
+  inf.levels = (int64_t)b->B * levels;
   for (int k = 0; k < b->B; ++k) {
     const int i = b->order[k];
     b->stats[i] = st[k];

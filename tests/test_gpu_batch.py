@@ -117,3 +117,28 @@ def test_batch_edge_sizes_and_validation(torch):
     with pytest.raises(pkg.TsfdeError) as e:
         pkg.BatchSolver(bad, M)
     assert e.value.status == pkg.TSFDE_ENOTSUP
+
+
+def test_batch_partial_levels_and_cluster_sizes(torch):
+    """Solving only the first K levels of the M-level mesh gives u^K of the
+    single-problem march; every cluster size gives the same result."""
+    import paper_2002_11978_gb300 as pkg
+    M, K = 12, 5
+    inst, probs = _instances(torch, [(20, 700, 1.4, 0.45), (21, 2100, 0.7, 0.6)], M)
+    refs = []
+    for p in probs:
+        s = pkg.Solver(p.alpha, p.gamma, p.l, p.T, p.n, M, p.r, 1e-12)
+        s.set_problem(cuda(torch, p.phi), cuda(torch, p.kappa0), None, None, F=[cuda(torch, p.F[0])],
+                      G=[np.ones(M + 1)])
+        u = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+        for _ in range(K):
+            s.step(u_out=u)
+        refs.append(u.cpu().numpy())
+    for q in (4, 8, 16):
+        bs = pkg.BatchSolver(inst, M, precision="fp64", cluster_size=q)
+        assert bs.shape[1] == q
+        outs = [torch.zeros(d["n"], dtype=torch.float64, device="cuda") for d in inst]
+        info = bs.solve(outs, levels=K)
+        assert info["levels"] == 2 * K
+        for u, ref in zip(outs, refs):
+            assert np.max(np.abs(u.cpu().numpy() - ref)) / np.max(np.abs(ref)) < 1e-10
