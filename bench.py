@@ -5,7 +5,10 @@ alpha = 1.6, kappa = exp(GRF) mapped onto [0.2, 5], mixed precision
 (FP32 inner PBiCGSTAB inside FP64 refinement) vs the plain FP64 path.
 
 One step = one time level of the scheme: SOE history update and
-right-hand side, Strang preconditioner for the level, Krylov solve.
+right-hand side, Strang preconditioner for the level, Krylov solve (from
+u^{m-1}, stopping at ||r|| < 1e-12 ||b||; --cold-start: from x0 = 0, the
+paper's setting, with the same stopping rule).  A `batched` object adds the
+512-problem workload (first 128 of its 1024 levels).
 Steps are timed one by one with CUDA events on the solver's stream; L2 is
 flushed (256 MB write, outside the events) before every timed level.
 
@@ -46,6 +49,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=255)
+    ap.add_argument("--cold-start", action="store_true",
+                    help="x0 = 0 for every level as in the paper's experiments (default: start "
+                         "from u^{m-1}, same stopping rule ||r|| < tol ||b||)")
     ap.add_argument("--batched-levels", type=int, default=128,
                     help="levels of the batched workload timed (of M = 1024; 0 skips it)")
     return ap.parse_args()
@@ -115,14 +121,15 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------- our arm
-def run_arm(torch, pkg, prob, precision, W, K, flush, stream, e2e=False):
+def run_arm(torch, pkg, prob, precision, W, K, flush, stream, e2e=False, warm=False):
     """March W untimed levels, then K timed levels (restarting the march
     after level M).  Each timed level is bracketed by CUDA events on the
     solver's stream, with an L2 flush before it.  Returns the solver, the
     per-level milliseconds, the per-kernel event totals and the iteration
     totals of the timed levels."""
     s = pkg.Solver(prob.alpha, prob.gamma, prob.l, prob.T, prob.n, prob.M, prob.r, prob.soe_tol,
-                   precision=precision, krylov_tol=1e-12, profile=True, stream=stream)
+                   precision=precision, krylov_tol=1e-12, profile=True, stream=stream,
+                   warm_start=warm)
     s.set_problem_from(prob)
     n = prob.n
     dev = torch.device("cuda")
@@ -182,7 +189,7 @@ def run_arm(torch, pkg, prob, precision, W, K, flush, stream, e2e=False):
     return s, ms, tim, tot
 
 
-def batched_sample(torch, pkg, ti, levels, rank, world, stream):
+def batched_sample(torch, pkg, ti, levels, rank, world, stream, warm=True):
     """The batched workload: 512 independent problems (n log-uniform in
     [2^9-1, 2^14-1], alpha ~ U(0.6, 1.9), gamma ~ U(0.2, 0.9), M = 1024),
     this rank's share (instance i on rank i mod world), first `levels`
@@ -199,10 +206,11 @@ def batched_sample(torch, pkg, ti, levels, rank, world, stream):
                          kappa=dev(p.kappa0), f=dev(p.F[0])))
     unknowns = sum(d["n"] for d in inst)
     out = {"workload": "fids-batched 512 instances n=U_log[511,16383] M=1024 (alpha, gamma random)",
-           "instances": len(inst), "levels_timed": levels, "unknowns": unknowns}
+           "instances": len(inst), "levels_timed": levels, "unknowns": unknowns,
+           "initial_guess": "u^{m-1}" if warm else "0"}
     us = {}
     for prec in ("mixed", "fp64"):
-        bs = pkg.BatchSolver(inst, M, precision=prec, stream=stream)
+        bs = pkg.BatchSolver(inst, M, precision=prec, stream=stream, warm_start=warm)
         outs = [torch.zeros(d["n"], dtype=torch.float64, device="cuda") for d in inst]
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -261,7 +269,7 @@ def ours(args):
     clocks = ClockSampler(torch.cuda.current_device())
     barrier()
     clocks.start()
-    s_mx, ms_mx, tim_mx, st_mx = run_arm(torch, pkg, prob, "mixed", W, K, flush, stream)
+    s_mx, ms_mx, tim_mx, st_mx = run_arm(torch, pkg, prob, "mixed", W, K, flush, stream, warm=(not args.cold_start))
     barrier()
     clk = clocks.stop()
     t_mx = sum(ms_mx) / 1e3
@@ -274,7 +282,7 @@ def ours(args):
     # ---- plain FP64 arm on the same levels: the comparison
     fp64 = None
     if not args.no_fp64:
-        s64, ms64, tim64, st64 = run_arm(torch, pkg, prob, "fp64", W, K, flush, stream)
+        s64, ms64, tim64, st64 = run_arm(torch, pkg, prob, "fp64", W, K, flush, stream, warm=(not args.cold_start))
         u64 = current_u(torch, s64)
         rel = float(torch.max(torch.abs(u_mx - u64)) / torch.max(torch.abs(u64)))
         t64 = sum(ms64) / 1e3
@@ -289,7 +297,8 @@ def ours(args):
     # ---- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        se, ms_e2e, _, _ = run_arm(torch, pkg, prob, "mixed", W, K, flush, stream, e2e=True)
+        se, ms_e2e, _, _ = run_arm(torch, pkg, prob, "mixed", W, K, flush, stream, e2e=True,
+                                    warm=(not args.cold_start))
         se.close()
         e2e = {"value": world * K / (sum(ms_e2e) / 1e3), "unit": "steps/s",
                "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n,
@@ -309,7 +318,8 @@ def ours(args):
 
     batched = None
     if args.batched_levels > 0:
-        batched = batched_sample(torch, pkg, ti, args.batched_levels, rank, world, stream)
+        batched = batched_sample(torch, pkg, ti, args.batched_levels, rank, world, stream,
+                                 warm=not args.cold_start)
         if world > 1:
             t = torch.tensor([batched["mixed"]["s"], batched["fp64"]["s"]], device="cuda")
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -329,6 +339,7 @@ def ours(args):
             "config": {"workload": WORKLOAD, "n": n, "M": prob.M, "first_timed_level": W + 1,
                        "precision": "mixed: FP32 inner PBiCGSTAB, FP64 refinement/residual/SOE",
                        "krylov_tol": 1e-12, "inner_tol": 1e-2,
+                       "initial_guess": "u^{m-1}" if (not args.cold_start) else "0 (Sec. 5)",
                        "l2": "flushed before every timed level (256 MB write outside the events)",
                        "parallelism": f"replicas x{world}"},
             "status": st_mx["status"],

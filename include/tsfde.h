@@ -99,13 +99,19 @@ typedef struct tsfde_opts {
   int cluster_size;     /* batched solve: CTAs per thread-block cluster,
                            4, 8 or 16; 0 (default) picks the size that keeps
                            the most CTAs resident                           */
+  int warm_start;       /* 1: start every level's solve from u^{m-1} and stop
+                           at ||r|| < krylov_tol ||b^m|| (mixed: same
+                           refinement rules); 0 (default): x0 = 0 and the
+                           residual relative to ||r_0|| = ||b^m|| (Sec. 5)   */
 } tsfde_opts;
 
 typedef struct tsfde_step_info {
   int64_t m;            /* time level just computed (1..M)                  */
   int status;           /* tsfde_status of this level                       */
   int iterations;       /* BiCGSTAB iterations (mixed: summed inner ones)   */
-  int outer;            /* mixed: FP64 refinement sweeps (0 for FP64 path)  */
+  int outer;            /* mixed: FP64 refinement sweeps (0 for FP64 path);
+                           negative: the level was finished (or, after such
+                           a level, solved directly) by FP64 PBiCGSTAB      */
   int E_active;         /* exponentials still non-zero at this level        */
   double rel_residual;  /* FP64 path: recursive ||r||/||b||; mixed: last
                            computed FP64 ||b - M u||/||b||                  */

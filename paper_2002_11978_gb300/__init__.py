@@ -37,7 +37,8 @@ class tsfde_opts(ctypes.Structure):
                 ("inner_max_it", ctypes.c_int),
                 ("soe_E", ctypes.c_int), ("soe_s", _dp), ("soe_w", _dp), ("profile", ctypes.c_int),
                 ("barrier_timeout_cycles", ctypes.c_longlong), ("stream", ctypes.c_void_p),
-                ("engine", ctypes.c_int), ("cluster_size", ctypes.c_int)]
+                ("engine", ctypes.c_int), ("cluster_size", ctypes.c_int),
+                ("warm_start", ctypes.c_int)]
 
 
 class tsfde_step_info(ctypes.Structure):
@@ -190,9 +191,10 @@ class Solver:
     def __init__(self, alpha, gamma, l, T, n, M, r, soe_tol=1e-12, *, precision="fp64",
                  precond="strang", krylov_tol=1e-12, max_it=2000, inner_tol=1e-2,
                  max_outer=60, inner_max_it=40, mu=None, kappa_mu=None, soe=None, barrier_timeout_cycles=0,
-                 profile=False, stream=None, engine="auto"):
+                 profile=False, stream=None, engine="auto", warm_start=False):
         lib = load_library()
         o = default_opts()
+        o.warm_start = 1 if warm_start else 0
         o.engine = {"auto": TSFDE_ENGINE_AUTO, "grid": TSFDE_ENGINE_GRID,
                     "cluster": TSFDE_ENGINE_CLUSTER}[engine]
         o.krylov_tol = krylov_tol
@@ -373,10 +375,11 @@ class BatchSolver:
 
     def __init__(self, instances, M, *, precision="mixed", precond="strang", krylov_tol=1e-12,
                  max_it=2000, inner_tol=1e-2, max_outer=60, inner_max_it=40, mu=None,
-                 kappa_mu=None, stream=None, cluster_size=0):
+                 kappa_mu=None, stream=None, cluster_size=0, warm_start=False):
         lib = load_library()
         o = default_opts()
         o.cluster_size = cluster_size
+        o.warm_start = 1 if warm_start else 0
         o.krylov_tol = krylov_tol
         o.max_it = max_it
         o.precision = {"fp64": TSFDE_FP64, "mixed": TSFDE_MIXED}[precision]

@@ -126,6 +126,7 @@ int tsfde_default_opts(tsfde_opts* o) {
   o->stream = nullptr;
   o->engine = TSFDE_ENGINE_AUTO;
   o->cluster_size = 0;
+  o->warm_start = 0;
   return TSFDE_OK;
 }
 
@@ -549,6 +550,9 @@ static int enqueue_level(tsfde_ctx* c, const double* kappa_m, const double* f_m,
   if (e == cudaSuccess) e = record(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "rhs kernel");
   LevelArgs A = level_args(c, c->ahat[m], c->b, c->u[m % 3], c->stats + m);
+  A.u_prev = c->opts.warm_start ? c->u[(m - 1) % 3] : nullptr;
+  A.prev = (m >= 2) ? c->stats + (m - 1) : nullptr;
+  A.retry_mixed = (m % 64 == 0) ? 1 : 0;
   e = launch_level_ctx(c, A);
   if (e == cudaSuccess) e = record(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "level kernel");

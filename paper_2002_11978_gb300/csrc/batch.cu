@@ -33,7 +33,7 @@ constexpr int kBT = 512;  // threads per CTA
 
 // cluster partial-sum slots of the level loop, apart from ce_bicgstab's 0..5
 // (a CTA may start pushing into those while another still reads these)
-enum { BS_RW = 6, BS_WW = 7, BS_RES = 8, BS_EMAX = 9, BS_XMAX = 10, BS_BB = 11 };
+enum { BS_RW = 6, BS_WW = 7, BS_RES = 8, BS_EMAX = 9, BS_XMAX = 10, BS_BB = 11, BS_R0 = 12 };
 
 // Per-cluster context at CeSm::ctx.
 struct BatchCtx {
@@ -66,9 +66,9 @@ __device__ __noinline__ void bt_init(const BatchCtx* bx) {
   }
 }
 
-// History update and right-hand side of level m into r64, u^m = 0; pushes
-// the cluster partial of b.b into slot BS_BB.
-__device__ __noinline__ void bt_rhs(const BatchCtx* bx, int m) {
+// History update and right-hand side of level m into r64; u^m = 0, or
+// u^{m-1} with warm; pushes the cluster partial of b.b into slot BS_BB.
+__device__ __noinline__ void bt_rhs(const BatchCtx* bx, int m, bool warm) {
   const BInst& I = bx->I;
   const CeGeo g = geo_q(I.gr);
   const CeSm<double> s = ce_sm<double>(bx->c64.lay);
@@ -106,7 +106,7 @@ __device__ __noinline__ void bt_rhs(const BatchCtx* bx, int m) {
     double2 b = make_double2(ah * a1.x - sx + fv.x, ah * a1.y - sy + fv.y);
     if (i0 + 1 >= n) b.y = 0.0;
     st2(I.r64, i0, n, b);
-    st2(um, i0, n, make_double2(0.0, 0.0));
+    st2(um, i0, n, warm ? a1 : make_double2(0.0, 0.0));
     bb += b.x * b.x + b.y * b.y;
   }
   ce_put(s.part, g.Q, BS_BB, block_sum(bb, s.red));
@@ -230,6 +230,53 @@ __device__ __noinline__ void bt_resid_product(const BatchCtx* bx, double nr, dou
   ce_put(s.part, g.Q, BS_WW, wwb);
 }
 
+// Warm start: r64 = b - M u^m (r64 holds b, u^m = u^{m-1}); pushes r.r into
+// BS_R0.  Ends before the barrier of the reduction.
+__device__ __noinline__ void bt_warm_residual(const BatchCtx* bx, int m) {
+  typedef double2 Z;
+  cg::cluster_group cl = cg::this_cluster();
+  const BInst& I = bx->I;
+  const CeGeo g = geo_q(I.gr);
+  const CeSm<double> s = ce_sm<double>(bx->c64.lay);
+  const int n = g.n, npair = (g.N1 >> 1) << g.lgcQ;
+  const double* um = I.u[m % 3];
+  const double ah = I.ahat[m];
+  Z* X = ce_io(g, s);
+  for (int pp = threadIdx.x; pp < npair; pp += blockDim.x) {
+    const int i0 = pair_i0(g, pp);
+    Z x = make_double2(0.0, 0.0);
+    if (i0 < n) {
+      x = ld2(um, i0);
+      if (i0 + 1 >= n) x.y = 0.0;
+    }
+    X[pp] = x;
+  }
+  __syncthreads();
+  ce_colfwd_buf(g, s, g.N1 >> 1);
+  cl.sync();
+  ce_rows<double, CE_APPLY>(g, s, I.spT64, nullptr, nullptr);
+  cl.sync();
+  Z* Y = ce_io(g, s);
+  {
+    const int lgcQ = g.lgcQ, N1 = g.N1;
+    auto st = [=](int j1, int c, Z z) {
+      if (j1 < (N1 >> 1)) Y[(j1 << lgcQ) + c] = z;
+    };
+    ce_colinv(g, s, st);
+  }
+  double rr = 0.0;
+  for (int pp = threadIdx.x; pp < npair; pp += blockDim.x) {
+    const int i0 = pair_i0(g, pp);
+    if (i0 >= n) continue;
+    const Z y = Y[pp], kv = ld2(I.kap64, i0), uv = ld2(um, i0), bv = ld2((const double*)I.r64, i0);
+    Z r = make_double2(bv.x - (ah * uv.x + kv.x * y.x), bv.y - (ah * uv.y + kv.y * y.y));
+    if (i0 + 1 >= n) r.y = 0.0;
+    st2(I.r64, i0, n, r);
+    rr += r.x * r.x + r.y * r.y;
+  }
+  ce_put(s.part, g.Q, BS_R0, block_sum(rr, s.red));
+}
+
 // u += step e, r64 -= theta w; pushes ||r||^2, max|step e|, max|u|.
 __device__ __noinline__ void bt_update(const BatchCtx* bx, int m, double step, double theta) {
   const BInst& I = bx->I;
@@ -295,39 +342,54 @@ struct LevelOut {
 };
 
 // One level: right-hand side, preconditioner, solve.
-__device__ LevelOut bt_level(BatchCtx* bx, const BatchArgs& A, int m) {
+// prev_fp64: the previous level was finished in FP64 (adaptive precision:
+// go to FP64 directly unless m is a retry level).
+__device__ LevelOut bt_level(BatchCtx* bx, const BatchArgs& A, int m, bool prev_fp64) {
   cg::cluster_group cl = cg::this_cluster();
   const CeSm<double> s = ce_sm<double>(A.lay);
   const BInst& I = bx->I;
   const int Q = I.gr.Q;
+  const bool warm = A.warm != 0;
   LevelOut o{TSFDE_OK, 0, 0, false, 0.0};
-  bt_rhs(bx, m);
+  bt_rhs(bx, m, warm);
   if (A.precond) bt_precond(bx, m);  // ends with a barrier
   else cl.sync();
   const double bb = ce_total(s.part, Q, BS_BB);
   if (!isfinite(bb)) { o.status = TSFDE_ENONFINITE; return o; }
   if (bb == 0.0) return o;
+  double rr0 = bb;
+  if (warm) {
+    bt_warm_residual(bx, m);
+    cl.sync();
+    rr0 = ce_total(s.part, Q, BS_R0);
+    if (!isfinite(rr0)) { o.status = TSFDE_ENONFINITE; return o; }
+    if (rr0 == 0.0) return o;
+  }
   const double nb = sqrt(bb);
   const bool prec = A.precond != 0;
   if (threadIdx.x == 0) {
     bx->c32.a = (float)I.ahat[m];
     bx->c64.a = I.ahat[m];
-    bx->c64.V.x = (A.precision == TSFDE_FP64) ? I.u[m % 3] : I.v64.x;
+    bx->c64.V.x = (A.precision == TSFDE_FP64 && !warm) ? I.u[m % 3] : I.v64.x;
   }
   __syncthreads();
   if (A.precision == TSFDE_FP64) {
-    const SolveRes r = ce_bicgstab<double>(&bx->c64, prec, A.tol, A.max_it, I.r64, 1.0);
+    const double scale = sqrt(rr0 / bb);
+    const SolveRes r = ce_bicgstab<double>(&bx->c64, prec, A.tol / scale, A.max_it, I.r64, 1.0);
+    cl.sync();
+    if (warm && r.status == TSFDE_OK) bt_add_fp64(bx, m);
     o.status = r.status;
     o.iters = r.iters;
-    o.relres = r.relres;
+    o.relres = r.relres * scale;
     cl.sync();
     return o;
   }
-  double nr = nb, relres = 1.0;
+  double nr = sqrt(rr0), relres = nr / nb;
   int stalls = 0;
-  bool fallback = false;
+  bool fallback = prev_fp64 && (m % 64) != 0;
+  if (!fallback && relres <= A.tol) { o.relres = relres; cl.sync(); return o; }
   const double ah = I.ahat[m];
-  for (;;) {
+  while (!fallback) {
     if (o.outer >= A.max_outer) { fallback = true; break; }
     const SolveRes ir = ce_bicgstab<float>(&bx->c32, prec, A.inner_tol, A.inner_max_it, I.r64, 1.0 / nr);
     o.iters += ir.iters;
@@ -349,7 +411,9 @@ __device__ LevelOut bt_level(BatchCtx* bx, const BatchArgs& A, int m) {
     relres = nr / nb;
     if (nr == 0.0 || emax <= A.tol * xmax) break;
     if (o.outer >= 2 && nr > 0.5 * nr_prev) {
-      if (relres <= 1e-9) break;  // rounding floor of the FP64 residual
+      // the FP64 residual is at its rounding floor and u no longer moves at
+      // the accuracy asked for
+      if (relres <= 1e-9 && emax <= 100.0 * A.tol * xmax) break;
       if (++stalls >= 3) { fallback = true; break; }
     } else {
       stalls = 0;
@@ -405,8 +469,10 @@ __global__ void __launch_bounds__(kBT, 1) k_batch(BatchArgs A) {
     long long its = 0, outer = 0;
     int nfp64 = 0, status = TSFDE_OK;
     double worst = 0.0;
+    bool prev_fp64 = false;
     for (int m = 1; m <= A.M; ++m) {
-      const LevelOut o = bt_level(bx, A, m);
+      const LevelOut o = bt_level(bx, A, m, prev_fp64);
+      prev_fp64 = o.fp64;
       its += o.iters;
       outer += o.outer;
       nfp64 += o.fp64 ? 1 : 0;

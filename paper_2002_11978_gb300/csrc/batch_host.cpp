@@ -489,6 +489,7 @@ int tsfde_batch_solve(tsfde_batch* b, int64_t levels, double* const* u_final,
   A.max_it = b->opts.max_it;
   A.max_outer = b->opts.max_outer;
   A.inner_max_it = b->opts.inner_max_it;
+  A.warm = b->opts.warm_start;
   A.tw64 = b->tw64;
   A.tw32 = b->tw32;
   A.lay = b->lay;

@@ -32,7 +32,7 @@ namespace cg = cooperative_groups;
 
 constexpr int kMaxQ = 16;  // largest cluster (non-portable size)
 
-constexpr int kCeSlots = 12;  // cluster partial-sum slots (ce_bicgstab: 0..5)
+constexpr int kCeSlots = 13;  // cluster partial-sum slots (ce_bicgstab: 0..5)
 
 __host__ __device__ inline size_t ce_tables_bytes(const CeLay& y) {
   return (size_t)(y.T1 + y.LT) * (sizeof(float2) + (y.has64 ? sizeof(double2) : 0));

@@ -613,6 +613,34 @@ static __device__ void write_stat(StepStat* st, int status, int iters, int outer
 }
 
 
+// Warm start of a level solve: u = u_prev and r64 = b - (ahat I + K A) u_prev
+// (one FP64 product); returns b.b and r.r (grid-wide, in every CTA).
+static __device__ bool warm_residual(const LevelArgs& A, SmemAll& S, double& bb, double& rr) {
+  const DevPlan& P = A.P;
+  auto pro = [&](int i) -> double {
+    const double x = A.u_prev[i];
+    A.u[i] = x;
+    return x;
+  };
+  passA_real<double, false>(P, S.d, P.n, pro);
+  if (!gsync(P, S.d.red)) return false;
+  passB<double, MID_APPLY>(P, S.d, P.saT64, P.sbT64, nullptr, nullptr, nullptr);
+  if (!gsync(P, S.d.red)) return false;
+  double bacc = 0.0, racc = 0.0;
+  auto epi = [&](int i, double y) -> double {
+    const double bi = A.b[i];
+    const double ri = bi - (A.ahat * A.u_prev[i] + A.kappa64[i] * y);
+    A.r64[i] = ri;
+    bacc += bi * bi;
+    racc += ri * ri;
+    return 0.0;
+  };
+  passCA_real<double, false>(P, S.d, epi);
+  put_partial(P, SL_BB, block_sum(bacc, S.d.red));
+  put_partial(P, SL_RES, block_sum(racc, S.d.red));
+  return gsync_sum2(P, S.d.red, SL_BB, SL_RES, 0u, bb, rr);
+}
+
 // Mixed level solve (shared by both engines).  conv(k) rounds entry k of the
 // FP64 preconditioner spectrum into the inner solver's FP32 tables;
 // inner(sc, res) solves (ahat I + K A) e = sc r64 in FP32 into k32.x (false
@@ -624,7 +652,8 @@ static __device__ void write_stat(StepStat* st, int status, int iters, int outer
 // theta = (r, w)/(w, w) when the full step would raise ||r||, so the FP64
 // residual never grows.  Stops when the last step satisfies
 // max|theta e| <= tol max|u|, or when a sweep no longer halves ||r|| with
-// ||r||/||b|| <= 1e-9 (its rounding floor at large n).  After three sweeps
+// ||r||/||b|| <= 1e-9 (its rounding floor at large n) and the step is below
+// 100 tol max|u|.  After three sweeps
 // without progress above that, or at max_outer, the level is finished by
 // FP64 PBiCGSTAB on the remaining residual, so a level never returns an
 // unconverged answer.
@@ -643,29 +672,38 @@ __device__ void mixed_level(const LevelArgs& A, SmemAll& S, Conv& conv, Inner& i
     write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0);
     return;
   }
+  double bb, rr0;
   {
-    double acc = 0.0;
     if (A.precond)
       for (int k = gtid; k < P.Nc; k += gstr) conv(k);
-    for (int i = gtid; i < n; i += gstr) {
-      const double bi = A.b[i];
-      A.u[i] = 0.0;
-      A.r64[i] = bi;
-      acc += bi * bi;
+    if (A.u_prev) {
+      if (!warm_residual(A, S, bb, rr0)) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
+    } else {
+      double acc = 0.0;
+      for (int i = gtid; i < n; i += gstr) {
+        const double bi = A.b[i];
+        A.u[i] = 0.0;
+        A.r64[i] = bi;
+        acc += bi * bi;
+      }
+      put_partial(P, SL_RES, block_sum(acc, S.d.red));
+      if (!gsync_sum(P, S.d.red, SL_RES, bb)) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
+      rr0 = bb;
     }
-    put_partial(P, SL_RES, block_sum(acc, S.d.red));
   }
-  double bb;
-  if (!gsync_sum(P, S.d.red, SL_RES, bb)) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
-  if (!isfinite(bb)) { write_stat(A.stat, TSFDE_ENONFINITE, 0, 0, 0.0); return; }
-  if (bb == 0.0) { write_stat(A.stat, TSFDE_OK, 0, 0, 0.0); return; }
+  if (!isfinite(bb) || !isfinite(rr0)) { write_stat(A.stat, TSFDE_ENONFINITE, 0, 0, 0.0); return; }
+  if (bb == 0.0 || rr0 == 0.0) { write_stat(A.stat, TSFDE_OK, 0, 0, 0.0); return; }
   const double nb = sqrt(bb);
-  double nr = nb, relres = 1.0;
+  double nr = sqrt(rr0), relres = nr / nb;
   int inner_total = 0, outer = 0, status = TSFDE_OK, stalls = 0;
-  bool fallback = false;
+  // After a level that needed the FP64 finish, go to it directly (the
+  // levels grow harder along the graded mesh), retrying the refinement on
+  // the levels the host marks.
+  bool fallback = A.prev && !A.retry_mixed && __ldcg(&A.prev->outer) < 0;
+  if (!fallback && relres <= A.tol) { write_stat(A.stat, TSFDE_OK, 0, 0, relres); return; }
   double* w = A.k64.v;  // FP64 scratch for M e
   const float* e = A.k32.x;
-  for (;;) {
+  while (!fallback) {
     if (outer >= A.max_outer) { fallback = true; break; }
     SolveRes ir{TSFDE_OK, 0, 0.0};
     if (!inner(1.0 / nr, ir)) { status = TSFDE_ETIMEOUT; break; }
@@ -725,7 +763,9 @@ __device__ void mixed_level(const LevelArgs& A, SmemAll& S, Conv& conv, Inner& i
     relres = nr / nb;
     if (nr == 0.0 || emax <= A.tol * xmax) break;
     if (outer >= 2 && nr > 0.5 * nr_prev) {
-      if (relres <= 1e-9) break;  // rounding floor of the FP64 residual
+      // the FP64 residual is at its rounding floor and u no longer moves at
+      // the accuracy asked for
+      if (relres <= 1e-9 && emax <= 100.0 * A.tol * xmax) break;
       if (++stalls >= 3) { fallback = true; break; }
     } else {
       stalls = 0;
@@ -745,7 +785,7 @@ __device__ void mixed_level(const LevelArgs& A, SmemAll& S, Conv& conv, Inner& i
     }
     status = fr.status;
     inner_total += fr.iters;
-    outer = -outer;  // a negative count marks a level finished in FP64
+    outer = -(outer > 0 ? outer : 1);  // negative: the level was finished in FP64
   }
   write_stat(A.stat, status, inner_total, outer, relres);
 }

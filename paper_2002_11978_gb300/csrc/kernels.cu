@@ -32,11 +32,28 @@ __global__ void __launch_bounds__(kThreads, 2) k_level64(LevelArgs A) {
     write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0);
     return;
   }
-  KVecs<double> V = A.k64;
-  V.x = A.u;
-  auto binit = [&](int i) -> double { return A.b[i]; };
-  SolveRes r = bicgstab<double>(P, S.d, V, A.kappa64, A.ahat, A.precond != 0, A.tol, A.max_it, binit);
-  write_stat(A.stat, r.status, r.iters, 0, r.relres);
+  if (!A.u_prev) {
+    KVecs<double> V = A.k64;
+    V.x = A.u;
+    auto binit = [&](int i) -> double { return A.b[i]; };
+    SolveRes r = bicgstab<double>(P, S.d, V, A.kappa64, A.ahat, A.precond != 0, A.tol, A.max_it, binit);
+    write_stat(A.stat, r.status, r.iters, 0, r.relres);
+    return;
+  }
+  // warm start: solve M d = b - M u_prev to ||r|| < tol ||b||, u = u_prev + d
+  double bb, rr;
+  if (!warm_residual(A, S, bb, rr)) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
+  if (!isfinite(bb) || !isfinite(rr)) { write_stat(A.stat, TSFDE_ENONFINITE, 0, 0, 0.0); return; }
+  if (bb == 0.0 || rr == 0.0) { write_stat(A.stat, TSFDE_OK, 0, 0, 0.0); return; }
+  const double scale = sqrt(rr / bb);
+  KVecs<double> V = A.k64;  // V.x: the correction d
+  auto binit = [&](int i) -> double { return A.r64[i]; };
+  SolveRes r = bicgstab<double>(P, S.d, V, A.kappa64, A.ahat, A.precond != 0, A.tol / scale, A.max_it, binit);
+  if (r.status == TSFDE_OK) {
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int i = gtid; i < P.n; i += gridDim.x * blockDim.x) A.u[i] += V.x[i];
+  }
+  write_stat(A.stat, r.status, r.iters, 0, r.relres * scale);
 }
 
 // Mixed level solve on the grid engine: the refinement loop of mixed_level

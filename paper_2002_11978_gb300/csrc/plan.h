@@ -143,6 +143,9 @@ struct LevelArgs {
   double* r64;        // mixed: FP64 residual
   StepStat* stat;
   int probe;          // cluster engine: return at once (launch check)
+  const double* u_prev;   // warm start from u^{m-1} (NULL: x0 = 0)
+  const StepStat* prev;   // mixed: the previous level's stats (NULL: none)
+  int retry_mixed;        // mixed: refine even after a level finished in FP64
 };
 
 // One instance of the batched solve (device-resident descriptor).  All
@@ -188,6 +191,7 @@ struct BatchArgs {
   int precond;
   double tol, inner_tol;
   int max_it, max_outer, inner_max_it;
+  int warm;              // start each level from u^{m-1}
   const double2* tw64;   // W_Lmax^k
   const float2* tw32;
   CeLay lay;             // shared-memory layout (sized for the largest instance)

@@ -142,3 +142,17 @@ def test_batch_partial_levels_and_cluster_sizes(torch):
         assert info["levels"] == 2 * K
         for u, ref in zip(outs, refs):
             assert np.max(np.abs(u.cpu().numpy() - ref)) / np.max(np.abs(ref)) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_warm_start_matches_cold(torch, precision):
+    """Levels started from u^{m-1} reach the cold-started FP64 solutions."""
+    M = 24
+    ns, al, ga = ti.batched_instance_params()
+    specs = [(i, int(ns[i]), float(al[i]), float(ga[i])) for i in (3, 8, 64)]
+    inst, probs = _instances(torch, specs, M)
+    _, Uc, ic = _batch(torch, inst, M, precision="fp64")
+    _, Uw, iw = _batch(torch, inst, M, precision=precision, warm_start=True)
+    assert iw["status"] == 0, iw
+    for a, b in zip(Uw, Uc):
+        assert np.max(np.abs(a - b)) / np.max(np.abs(b)) < 1e-10

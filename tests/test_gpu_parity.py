@@ -279,3 +279,35 @@ def test_paper_tables_on_gpu(torch, row):
         assert _printed(e2, float(row[10])), (e2, row[10])
     if row[11] != "-":
         assert abs(its / M - float(row[11])) <= 1.0, (its / M, row[11])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_warm_start_march_matches_oracle(torch, precision):
+    """Levels started from u^{m-1} (stopping at ||r|| < tol ||b||) reach the
+    same solutions as the oracle's dense-LU march."""
+    prob = ti.config_smallest()
+    tm, tau = oracle.graded_mesh(prob.T, prob.M, prob.r)
+    soe = oracle.soe_build(prob.gamma, tau[1], prob.T, prob.soe_tol)
+    _, U, info = _gpu_solve(torch, prob, precision, soe=soe, warm_start=True)
+    ref = _oracle_fids(prob, soe)
+    assert np.max(np.abs(U - ref)) / np.max(np.abs(ref)) < 1e-10, info
+
+
+def test_warm_start_large_levels_agree(torch):
+    """n = 16383: 24 levels with and without warm start, FP64 and mixed."""
+    import paper_2002_11978_gb300 as pkg
+    prob = ti.config_mid(0.3, 1.8, n=16383, M=64)
+    out = {}
+    for prec in ("fp64", "mixed"):
+        for warm in (False, True):
+            s = pkg.Solver(prob.alpha, prob.gamma, prob.l, prob.T, prob.n, prob.M, prob.r, prob.soe_tol,
+                           precision=prec, warm_start=warm)
+            s.set_problem_from(prob)
+            u = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+            for _ in range(24):
+                info = s.step(u_out=u)
+                assert info["status"] == 0, info
+            out[(prec, warm)] = u.cpu().numpy()
+    ref = out[("fp64", False)]
+    for k, v in out.items():
+        assert np.max(np.abs(v - ref)) / np.max(np.abs(ref)) < 1e-10, k
