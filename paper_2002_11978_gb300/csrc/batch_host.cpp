@@ -171,20 +171,30 @@ bool build_instance(const tsfde_instance& in, int64_t M, double mu_opt, int kmu_
 
 }  // namespace
 
+// Instances of one size class share a cluster size, a shared-memory layout and
+// a persistent launch; the classes' launches run side by side on two streams.
+struct BClass {
+  std::vector<int> members;  // caller indices in launch order (largest first)
+  int Q = 0, clusters = 0;
+  CeLay lay{};
+  BInst* dinst = nullptr;
+  int* dnext = nullptr;
+  StepStat* dstats = nullptr;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+};
+
 struct tsfde_batch {
-  int B = 0, Q = 0, clusters = 0;
+  int B = 0;
   int64_t M = 0;
   tsfde_opts opts{};
   cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<BClass> cls;
   std::vector<BInst> inst;     // host copies (device pointers inside)
-  std::vector<int> order;      // launch order -> caller's index
-  BInst* dinst = nullptr;
-  int* dnext = nullptr;
-  StepStat* dstats = nullptr;  // per launch-order slot
   std::vector<StepStat> stats; // per caller index, last solve
   double2* tw64 = nullptr;
   float2* tw32 = nullptr;
-  CeLay lay{};
   std::vector<void*> allocs;
   std::string err;
 };
@@ -208,6 +218,38 @@ int bfail(tsfde_batch* b, int st, const std::string& msg) {
   if (b) b->err = msg;
   std::fprintf(stderr, "tsfde_batch_setup: %s\n", msg.c_str());
   return st;
+}
+
+// Cluster size for instances with nmin <= n <= nmax: among 4, 8, 16 (or the
+// caller's), those every instance can split and whose shared-memory layout
+// fits; the one keeping the most CTAs resident (ties: the smaller cluster).
+int pick_q(int64_t nmin, int64_t nmax, int want) {
+  int Lmin = 8, Lmax0 = 8;
+  while (Lmin < 2 * nmin - 1) Lmin *= 2;
+  while (Lmax0 < 2 * nmax - 1) Lmax0 *= 2;
+  const int lgs = ilg(Lmin / 2);
+  const int N1s = 1 << ((lgs + 1) / 2), N2s = (Lmin / 2) / N1s;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int best = 0, Q = 0;
+  for (int q : {4, 8, 16}) {
+    if (want > 0 && q != want) continue;
+    if (2 * q > N1s || q > N2s) continue;
+    const int lgL = ilg(Lmax0);
+    const int N1c = 1 << ((lgL + 1) / 2);
+    CeLay y{};
+    y.has64 = 1;
+    y.capB = std::max((Lmax0 / q + N1c) * (int)sizeof(double2), 2 * 4096 * (int)sizeof(double));
+    y.nbufB = (Lmax0 / q) * (int)sizeof(double2);
+    y.T1 = N1c;
+    y.LT = Lmax0 / N1c;
+    const size_t sm = batch_smem_bytes(y);
+    if (sm > (size_t)optin) continue;
+    const int res = batch_max_clusters(q, sm) * q;
+    if (res > best) { best = res; Q = q; }
+  }
+  return Q;
 }
 
 }  // namespace
@@ -238,54 +280,46 @@ int tsfde_batch_setup(tsfde_batch** out, int B, const tsfde_instance* inst, int6
     nmax = std::max(nmax, x.n);
   }
   if (nmin < 31 || nmax > 16383) return TSFDE_ENOTSUP;
+  if (o.cluster_size != 0 && o.cluster_size != 4 && o.cluster_size != 8 && o.cluster_size != 16)
+    return TSFDE_EINVAL;
   tsfde_batch* b = new tsfde_batch();
   b->B = B;
   b->M = M;
   b->opts = o;
   b->stream = static_cast<cudaStream_t>(o.stream);
-  // cluster size: among 4, 8, 16 (or the caller's), those every instance can
-  // split and whose shared-memory layout fits; pick the one keeping the most
-  // CTAs resident (ties: the smaller cluster)
-  int Q = 0;
+  // size classes: transforms of length L >= 16384 (one CTA per SM with their
+  // shared-memory layout) and the rest (several CTAs per SM)
+  std::vector<int> Ls(B);
+  for (int i = 0; i < B; ++i) {
+    int L = 8;
+    while (L < 2 * inst[i].n - 1) L *= 2;
+    Ls[i] = L;
+  }
+  std::vector<int> order(B);
+  for (int i = 0; i < B; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return inst[a].n > inst[c].n; });
   {
-    int Lmin = 8, Lmax0 = 8;
-    while (Lmin < 2 * nmin - 1) Lmin *= 2;
-    while (Lmax0 < 2 * nmax - 1) Lmax0 *= 2;
-    const int lgs = ilg(Lmin / 2);
-    const int N1s = 1 << ((lgs + 1) / 2), N2s = (Lmin / 2) / N1s;
-    int dev0 = 0, optin0 = 0;
-    cudaGetDevice(&dev0);
-    cudaDeviceGetAttribute(&optin0, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev0);
-    int best = 0;
-    for (int q : {4, 8, 16}) {
-      if (o.cluster_size > 0 && q != o.cluster_size) continue;
-      if (2 * q > N1s || q > N2s) continue;
-      // layout of the largest transform (complex, length Lmax0) with q CTAs
-      const int lgL = ilg(Lmax0);
-      const int N1c = 1 << ((lgL + 1) / 2);
-      CeLay y{};
-      y.has64 = 1;
-      y.capB = (Lmax0 / q + N1c) * (int)sizeof(double2);
-      y.nbufB = (Lmax0 / q) * (int)sizeof(double2);
-      y.T1 = N1c;
-      y.LT = Lmax0 / N1c;
-      y.capB = std::max(y.capB, 2 * 4096 * (int)sizeof(double));  // SOE factors
-      const size_t sm = batch_smem_bytes(y);
-      if (sm > (size_t)optin0) continue;
-      const int res = batch_max_clusters(q, sm) * q;
-      if (res > best) { best = res; Q = q; }
+    BClass big, small;
+    for (int i : order) (Ls[i] >= 16384 ? big : small).members.push_back(i);
+    if (!big.members.empty()) b->cls.push_back(big);
+    if (!small.members.empty()) b->cls.push_back(small);
+  }
+  std::vector<int> cls_of(B, 0);
+  for (size_t k = 0; k < b->cls.size(); ++k) {
+    BClass& C = b->cls[k];
+    int64_t lo = INT64_MAX, hi = 0;
+    for (int i : C.members) {
+      cls_of[i] = (int)k;
+      lo = std::min(lo, inst[i].n);
+      hi = std::max(hi, inst[i].n);
     }
-    if (o.cluster_size > 0 && o.cluster_size != 4 && o.cluster_size != 8 && o.cluster_size != 16) {
-      delete b;
-      return TSFDE_EINVAL;
-    }
-    if (Q == 0) {
+    C.Q = pick_q(lo, hi, o.cluster_size);
+    if (C.Q == 0) {
       const int st = bfail(b, TSFDE_ENOTSUP, "no cluster size fits these instances on this device");
       tsfde_batch_destroy(b);
       return st;
     }
   }
-  b->Q = Q;
   // host tables, in parallel
   std::vector<HostInst> H(B);
   {
@@ -298,7 +332,7 @@ int tsfde_batch_setup(tsfde_batch** out, int B, const tsfde_instance* inst, int6
         for (;;) {
           const int i = next.fetch_add(1);
           if (i >= B) break;
-          if (!build_instance(inst[i], M, o.mu, o.kappa_mu, Q, H[i])) {
+          if (!build_instance(inst[i], M, o.mu, o.kappa_mu, b->cls[cls_of[i]].Q, H[i])) {
             int exp = -1;
             bad.compare_exchange_strong(exp, i);
           }
@@ -312,51 +346,59 @@ int tsfde_batch_setup(tsfde_batch** out, int B, const tsfde_instance* inst, int6
       return st;
     }
   }
-  // shared-memory layout for the largest transform
-  bool ok_sizes = true;
+  // shared-memory layout of each class (its largest transform)
   int Lmax = 8;
-  CeLay lay{};
-  lay.has64 = 1;
-  for (int i = 0; i < B; ++i) {
-    const HostInst& h = H[i];
-    Lmax = std::max(Lmax, h.L);
-    lay.capB = std::max(lay.capB, (h.gc.nbuf + h.gc.N1) * (int)sizeof(double2));
-    lay.nbufB = std::max(lay.nbufB, h.gc.nbuf * (int)sizeof(double2));
-    lay.T1 = std::max(lay.T1, h.gc.T1);
-    lay.LT = std::max(lay.LT, h.gc.LT);
-    // the right-hand side stages the level's SOE factors in S
-    lay.capB = std::max(lay.capB, 2 * std::max(h.E, 1) * (int)sizeof(double));
-    if (h.E > 4096) ok_sizes = false;
-  }
-  b->lay = lay;
-  if (!ok_sizes) {
-    const int st = bfail(b, TSFDE_ENOTSUP, "SOE table longer than 4096 exponentials");
-    tsfde_batch_destroy(b);
-    return st;
-  }
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const size_t smem = batch_smem_bytes(lay);
-  if (smem > (size_t)optin) {
-    const int st = bfail(b, TSFDE_ENOTSUP, "largest instance does not fit the cluster's shared memory");
+  for (size_t k = 0; k < b->cls.size(); ++k) {
+    BClass& C = b->cls[k];
+    CeLay lay{};
+    lay.has64 = 1;
+    for (int i : C.members) {
+      const HostInst& h = H[i];
+      Lmax = std::max(Lmax, h.L);
+      lay.capB = std::max(lay.capB, (h.gc.nbuf + h.gc.N1) * (int)sizeof(double2));
+      lay.nbufB = std::max(lay.nbufB, h.gc.nbuf * (int)sizeof(double2));
+      lay.T1 = std::max(lay.T1, h.gc.T1);
+      lay.LT = std::max(lay.LT, h.gc.LT);
+      // the right-hand side stages the level's SOE factors in S
+      lay.capB = std::max(lay.capB, 2 * std::max(h.E, 1) * (int)sizeof(double));
+      if (h.E > 4096) {
+        const int st = bfail(b, TSFDE_ENOTSUP, "SOE table longer than 4096 exponentials");
+        tsfde_batch_destroy(b);
+        return st;
+      }
+    }
+    C.lay = lay;
+    const size_t smem = batch_smem_bytes(lay);
+    C.clusters = (smem <= (size_t)optin) ? batch_max_clusters(C.Q, smem) : 0;
+    if (C.clusters < 1) {
+      const int st = bfail(b, TSFDE_ENOTSUP, "cluster launch not possible on this device");
+      tsfde_batch_destroy(b);
+      return st;
+    }
+    if (k == 0) {
+      C.stream = b->stream;
+    } else if (cudaStreamCreateWithFlags(&C.stream, cudaStreamNonBlocking) == cudaSuccess) {
+      C.own_stream = true;
+    } else {
+      const int st = bfail(b, TSFDE_ECUDA, "cudaStreamCreate failed");
+      tsfde_batch_destroy(b);
+      return st;
+    }
+  }
+  if (cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    const int st = bfail(b, TSFDE_ECUDA, "cudaEventCreate failed");
     tsfde_batch_destroy(b);
     return st;
   }
-  b->clusters = batch_max_clusters(Q, smem);
-  if (b->clusters < 1) {
-    const int st = bfail(b, TSFDE_ENOTSUP, "cluster launch not possible on this device");
-    tsfde_batch_destroy(b);
-    return st;
-  }
-  // launch order: largest first
-  b->order.resize(B);
-  for (int i = 0; i < B; ++i) b->order[i] = i;
-  std::stable_sort(b->order.begin(), b->order.end(),
-                   [&](int a, int c) { return inst[a].n > inst[c].n; });
   // device memory
-  bool ok = balloc(b, &b->dinst, B) && balloc(b, &b->dnext, 1) && balloc(b, &b->dstats, B) &&
-            balloc(b, &b->tw64, Lmax) && balloc(b, &b->tw32, Lmax);
+  bool ok = balloc(b, &b->tw64, Lmax) && balloc(b, &b->tw32, Lmax);
+  for (BClass& C : b->cls)
+    ok = ok && balloc(b, &C.dinst, C.members.size()) && balloc(b, &C.dnext, 1) &&
+         balloc(b, &C.dstats, C.members.size());
   b->inst.resize(B);
   std::vector<double> kmean(B, 0.0);
   for (int i = 0; i < B && ok; ++i) {
@@ -434,7 +476,7 @@ int tsfde_batch_setup(tsfde_batch** out, int B, const tsfde_instance* inst, int6
       return st;
     }
     I.kbar = kmean[i];
-    I.stat = b->dstats;  // set per launch slot below
+    I.stat = nullptr;  // set per launch slot by each solve
   }
   if (!ok) {
     const int st = bfail(b, TSFDE_ENOMEM, "cudaMalloc failed");
@@ -466,37 +508,53 @@ int tsfde_batch_solve(tsfde_batch* b, int64_t levels, double* const* u_final,
   if (levels == 0) levels = b->M;
   for (int i = 0; i < b->B; ++i)
     if (!u_final[i]) return TSFDE_EINVAL;
-  // descriptors in launch order, each with its output and stats slot
-  std::vector<BInst> d(b->B);
-  for (int k = 0; k < b->B; ++k) {
-    const int i = b->order[k];
-    d[k] = b->inst[i];
-    d[k].u_out = u_final[i];
-    d[k].stat = b->dstats + k;
+  BatchArgs A0{};
+  A0.M = (int)levels;
+  A0.precision = b->opts.precision;
+  A0.precond = b->opts.precond == TSFDE_STRANG ? 1 : 0;
+  A0.tol = b->opts.krylov_tol;
+  A0.inner_tol = b->opts.inner_tol;
+  A0.max_it = b->opts.max_it;
+  A0.max_outer = b->opts.max_outer;
+  A0.inner_max_it = b->opts.inner_max_it;
+  A0.warm = b->opts.warm_start;
+  A0.tw64 = b->tw64;
+  A0.tw32 = b->tw32;
+  // the classes' streams start after the caller's stream reaches this point
+  // and the caller's stream continues after all of them
+  cudaError_t e = cudaEventRecord(b->ev_in, b->stream);
+  const size_t nc = b->cls.size();
+  std::vector<std::vector<BInst>> d(nc);
+  std::vector<std::vector<StepStat>> st(nc);
+  for (size_t k = 0; k < nc && e == cudaSuccess; ++k) {
+    BClass& C = b->cls[k];
+    const int cnt = (int)C.members.size();
+    d[k].resize(cnt);
+    st[k].resize(cnt);
+    for (int j = 0; j < cnt; ++j) {
+      const int i = C.members[j];
+      d[k][j] = b->inst[i];
+      d[k][j].u_out = u_final[i];
+      d[k][j].stat = C.dstats + j;
+    }
+    if (C.stream != b->stream) e = cudaStreamWaitEvent(C.stream, b->ev_in, 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(C.dinst, d[k].data(), sizeof(BInst) * cnt, cudaMemcpyHostToDevice, C.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(C.dstats, 0, sizeof(StepStat) * cnt, C.stream);
+    BatchArgs A = A0;
+    A.inst = C.dinst;
+    A.count = cnt;
+    A.next = C.dnext;
+    A.lay = C.lay;
+    if (e == cudaSuccess) e = launch_batch(A, C.Q, C.clusters, C.stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(st[k].data(), C.dstats, sizeof(StepStat) * cnt, cudaMemcpyDeviceToHost, C.stream);
+    if (e == cudaSuccess && C.stream != b->stream) {
+      e = cudaEventRecord(b->ev_out, C.stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_out, 0);
+    }
   }
-  cudaStream_t s = b->stream;
-  cudaError_t e = cudaMemcpyAsync(b->dinst, d.data(), sizeof(BInst) * b->B, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->dstats, 0, sizeof(StepStat) * b->B, s);
-  BatchArgs A{};
-  A.inst = b->dinst;
-  A.count = b->B;
-  A.M = (int)levels;
-  A.next = b->dnext;
-  A.precision = b->opts.precision;
-  A.precond = b->opts.precond == TSFDE_STRANG ? 1 : 0;
-  A.tol = b->opts.krylov_tol;
-  A.inner_tol = b->opts.inner_tol;
-  A.max_it = b->opts.max_it;
-  A.max_outer = b->opts.max_outer;
-  A.inner_max_it = b->opts.inner_max_it;
-  A.warm = b->opts.warm_start;
-  A.tw64 = b->tw64;
-  A.tw32 = b->tw32;
-  A.lay = b->lay;
-  if (e == cudaSuccess) e = launch_batch(A, b->Q, b->clusters, s);
-  std::vector<StepStat> st(b->B);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(st.data(), b->dstats, sizeof(StepStat) * b->B, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) {
     b->err = std::string("batch launch: ") + cudaGetErrorString(e);
     return TSFDE_ECUDA;
@@ -504,18 +562,20 @@ int tsfde_batch_solve(tsfde_batch* b, int64_t levels, double* const* u_final,
   tsfde_batch_info inf{};
   inf.failed_instance = -1;
   inf.levels = (int64_t)b->B * levels;
-  for (int k = 0; k < b->B; ++k) {
-    const int i = b->order[k];
-    b->stats[i] = st[k];
-    inf.iterations += st[k].iterations;
-    inf.outer += st[k].outer;
-    inf.fp64_levels += st[k].E_active;
-    inf.max_rel_residual = std::max(inf.max_rel_residual, st[k].rel_residual);
-    if (st[k].status != TSFDE_OK && inf.status == TSFDE_OK) {
-      inf.status = st[k].status;
-      inf.failed_instance = i;
+  for (size_t k = 0; k < nc; ++k)
+    for (size_t j = 0; j < b->cls[k].members.size(); ++j) {
+      const int i = b->cls[k].members[j];
+      const StepStat& x = st[k][j];
+      b->stats[i] = x;
+      inf.iterations += x.iterations;
+      inf.outer += x.outer;
+      inf.fp64_levels += x.E_active;
+      inf.max_rel_residual = std::max(inf.max_rel_residual, x.rel_residual);
+      if (x.status != TSFDE_OK && (inf.status == TSFDE_OK || i < inf.failed_instance)) {
+        inf.status = x.status;
+        inf.failed_instance = i;
+      }
     }
-  }
   if (info) *info = inf;
   return inf.status;
 }
@@ -534,13 +594,17 @@ int tsfde_batch_instance_stats(const tsfde_batch* b, int i, tsfde_step_info* out
 
 int tsfde_batch_shape(const tsfde_batch* b, int* clusters, int* cluster_size) {
   if (!b) return TSFDE_EINVAL;
-  if (clusters) *clusters = b->clusters;
-  if (cluster_size) *cluster_size = b->Q;
+  if (clusters) *clusters = b->cls.empty() ? 0 : b->cls[0].clusters;
+  if (cluster_size) *cluster_size = b->cls.empty() ? 0 : b->cls[0].Q;
   return TSFDE_OK;
 }
 
 void tsfde_batch_destroy(tsfde_batch* b) {
   if (!b) return;
+  for (BClass& C : b->cls)
+    if (C.own_stream) cudaStreamDestroy(C.stream);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
   for (void* p : b->allocs) cudaFree(p);
   delete b;
 }
