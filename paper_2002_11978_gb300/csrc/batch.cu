@@ -29,7 +29,7 @@
 
 namespace tsfde {
 
-constexpr int kBT = 512;  // threads per CTA
+constexpr int kBT = 256;  // threads per CTA
 
 // cluster partial-sum slots of the level loop, apart from ce_bicgstab's 0..5
 // (a CTA may start pushing into those while another still reads these)
@@ -436,7 +436,7 @@ __device__ LevelOut bt_level(BatchCtx* bx, const BatchArgs& A, int m, bool prev_
   return o;
 }
 
-__global__ void __launch_bounds__(kBT, 1) k_batch(BatchArgs A) {
+__global__ void __launch_bounds__(kBT, 2) k_batch(BatchArgs A) {
   cg::cluster_group cl = cg::this_cluster();
   const CeSm<double> s = ce_sm<double>(A.lay);
   BatchCtx* bx = reinterpret_cast<BatchCtx*>(s.ctx);
