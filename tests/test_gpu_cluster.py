@@ -150,3 +150,35 @@ def test_full_size_levels_mixed_vs_fp64(torch):
     for m, (umx, bmx) in enumerate(sols["mixed"], start=1):
         ahat_m = oracle.l1_weight(prob.T, prob.M, prob.r, prob.gamma, m, m) / math.gamma(1 - prob.gamma)
         assert _sampled_residual(t, ahat_m, prob.kappa0, umx, bmx, rows) < 1e-9
+
+
+@pytest.mark.parametrize("gamma", [0.3, 0.7])
+@pytest.mark.parametrize("alpha", [0.8, 1.2, 1.8])
+def test_mid_size_levels_fp64_mixed_and_sampled_rows(torch, gamma, alpha):
+    """The mid workload (n = 2^14 - 1, M = 2048, six (gamma, alpha) pairs),
+    first 12 levels: FP64 and mixed agree to 1e-10, and the last level's
+    solution satisfies its equation on 64 sampled rows summed with the
+    oracle's symbol."""
+    import paper_2002_11978_gb300 as pkg
+    prob = ti.config_mid(gamma, alpha)
+    n, levels = prob.n, 12
+    t = oracle.ifl_symbol(prob.alpha, n)
+    tm, _ = oracle.graded_mesh(prob.T, prob.M, prob.r)
+    rows = np.random.default_rng(1).choice(n, 64, replace=False)
+    rows[:2] = [0, n - 1]
+    out = {}
+    for prec in ("fp64", "mixed"):
+        s = pkg.Solver(prob.alpha, prob.gamma, prob.l, prob.T, n, prob.M, prob.r, prob.soe_tol,
+                       precision=prec, krylov_tol=prob.krylov_tol)
+        s.set_problem_from(prob)
+        u = torch.zeros(n, dtype=torch.float64, device="cuda")
+        rhs = torch.zeros(n, dtype=torch.float64, device="cuda")
+        for m in range(1, levels + 1):
+            info = s.step(u_out=u, rhs_out=rhs)
+            assert info["status"] == 0, info
+        out[prec] = (u.cpu().numpy(), rhs.cpu().numpy())
+    u64, umx = out["fp64"][0], out["mixed"][0]
+    assert np.max(np.abs(umx - u64)) / np.max(np.abs(u64)) < 1e-10
+    ahat = oracle.l1_weight(prob.T, prob.M, prob.r, prob.gamma, levels, levels) / math.gamma(1 - prob.gamma)
+    kap = prob.kappa_at(tm[levels])
+    assert _sampled_residual(t, ahat, kap, umx, out["mixed"][1], rows) < 1e-9
