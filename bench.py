@@ -8,7 +8,8 @@ One step = one time level of the scheme: SOE history update and
 right-hand side, Strang preconditioner for the level, Krylov solve (from
 u^{m-1}, stopping at ||r|| < 1e-12 ||b||; --cold-start: from x0 = 0, the
 paper's setting, with the same stopping rule).  A `batched` object adds the
-512-problem workload (first 128 of its 1024 levels).
+512-problem workload (first 128 of its 1024 levels), an `adjoint` object the
+gradient sweep of the adjoint workload (n = 4095, M = 1024).
 Steps are timed one by one with CUDA events on the solver's stream; L2 is
 flushed (256 MB write, outside the events) before every timed level.
 
@@ -52,6 +53,7 @@ def parse():
     ap.add_argument("--cold-start", action="store_true",
                     help="x0 = 0 for every level as in the paper's experiments (default: start "
                          "from u^{m-1}, same stopping rule ||r|| < tol ||b||)")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
     ap.add_argument("--batched-levels", type=int, default=128,
                     help="levels of the batched workload timed (of M = 1024; 0 skips it)")
     return ap.parse_args()
@@ -60,6 +62,22 @@ def parse():
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
             int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def shard(count, rank, world):
+    """Instances of a batched workload on this rank: i with i mod world == rank
+    (independent problems, no exchange between ranks)."""
+    return [i for i in range(count) if i % world == rank]
+
+
+def max_over_ranks(values, device):
+    """Element-wise maximum of per-rank times over all ranks (the job's wall
+    time is the slowest rank's)."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
 
 
 # ----------------------------------------------------------------- clocks
@@ -217,7 +235,7 @@ def batched_sample(torch, pkg, ti, levels, rank, world, stream, warm=True):
     set (the SOE histories, ~3 GB) is far above L2."""
     M = 1024
     ns, al, ga = ti.batched_instance_params()
-    mine = [i for i in range(len(ns)) if i % world == rank]
+    mine = shard(len(ns), rank, world)
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
     inst = []
     for i in mine:
@@ -261,6 +279,52 @@ def batched_sample(torch, pkg, ti, levels, rank, world, stream, warm=True):
     return out
 
 
+def adjoint_sample(torch, pkg, ti, stream):
+    """The adjoint workload: n = 4095, M = 1024, J = 1/2 ||u^M - u_obs||^2
+    with u_obs from another kappa; forward march (FP64, all levels kept) and
+    the reverse sweep (transposed FP64 solves, reversed SOE recurrence,
+    fused gradient products), each timed with CUDA events.  The gradient is
+    checked against a central difference of J along one random direction."""
+    prob, kobs = ti.config_adjoint()
+    n, M = prob.n, prob.M
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    s = pkg.Solver(prob.alpha, prob.gamma, prob.l, prob.T, n, M, prob.r, 1e-12, stream=stream)
+    ones = np.ones(M + 1)
+    U = torch.zeros((M + 1, n), dtype=torch.float64, device="cuda")
+    uf = torch.zeros(n, dtype=torch.float64, device="cuda")
+
+    def forward(kap):
+        s.set_problem(dev(prob.phi), dev(kap), None, None, F=[dev(prob.F[0])], G=[ones])
+        s.solve(uf, U)
+        torch.cuda.synchronize()
+        return U
+
+    u_obs = forward(kobs)[M].clone()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    with torch.cuda.stream(stream):
+        e[0].record(stream)
+        forward(prob.kappa0)
+        e[1].record(stream)
+        gk = torch.zeros(n, dtype=torch.float64, device="cuda")
+        gf = torch.zeros(n, dtype=torch.float64, device="cuda")
+        info = s.adjoint(U, U[M] - u_obs, gk, gf)
+        e[2].record(stream)
+    torch.cuda.synchronize()
+    t_fwd = e[0].elapsed_time(e[1]) / 1e3
+    t_adj = e[1].elapsed_time(e[2]) / 1e3
+    d = np.random.default_rng(5).standard_normal(n)
+    d /= np.linalg.norm(d)
+    h = 1e-5 * float(np.max(prob.kappa0))
+    J = lambda kap: 0.5 * float(torch.sum((forward(kap)[M] - u_obs) ** 2))
+    fd = (J(prob.kappa0 + h * d) - J(prob.kappa0 - h * d)) / (2 * h)
+    ad = float(gk.cpu().numpy() @ d)
+    return {"workload": "fids-adjoint n=4095 M=1024 gamma=0.5 alpha=1.4 kappa=lognormal GRF",
+            "forward_s": t_fwd, "adjoint_s": t_adj, "adjoint_levels_per_s": M / t_adj,
+            "adjoint_iterations": info["iterations"], "status": info["status"],
+            "grad_dir_adjoint": ad, "grad_dir_central_difference": fd,
+            "grad_rel_diff": abs(ad - fd) / max(abs(fd), 1e-300)}
+
+
 def current_u(torch, s):
     u = torch.zeros(s.n, dtype=torch.float64, device="cuda")
     s.current_solution(u)
@@ -299,11 +363,7 @@ def ours(args):
     s_mx, ms_mx, tim_mx, st_mx = run_arm(torch, pkg, prob, "mixed", W, K, flush, stream, warm=(not args.cold_start))
     barrier()
     clk = clocks.stop()
-    t_mx = sum(ms_mx) / 1e3
-    if world > 1:
-        t = torch.tensor([t_mx], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_mx = float(t.item())
+    t_mx = max_over_ranks([sum(ms_mx) / 1e3], "cuda")[0]
     u_mx = current_u(torch, s_mx)
 
     # ---- plain FP64 arm on the same levels: the comparison
@@ -348,11 +408,14 @@ def ours(args):
         batched = batched_sample(torch, pkg, ti, args.batched_levels, rank, world, stream,
                                  warm=not args.cold_start)
         if world > 1:
-            t = torch.tensor([batched["mixed"]["s"], batched["fp64"]["s"]], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            tm = max_over_ranks([batched["mixed"]["s"], batched["fp64"]["s"]], "cuda")
             for k, prec in enumerate(("mixed", "fp64")):
-                batched[prec]["s_max_over_ranks"] = float(t[k].item())
-                batched[prec]["instance_levels_per_s"] = 512 * args.batched_levels / float(t[k].item())
+                batched[prec]["s_max_over_ranks"] = tm[k]
+                batched[prec]["instance_levels_per_s"] = 512 * args.batched_levels / tm[k]
+
+    adjoint = None
+    if rank == 0 and not args.no_adjoint:
+        adjoint = adjoint_sample(torch, pkg, ti, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -376,7 +439,7 @@ def ours(args):
                         "k_level_mixed": {"ms": lvl_ms, "bytes": lvl_bytes, "GB/s": lvl_gbs,
                                           "frac": lvl_gbs / peak}},
             "fp64": fp64, "e2e": e2e, "gpu_launches": 2 * K, "roofline": roof,
-            "cpu_baseline": cpu, "clocks": clk, "batched": batched,
+            "cpu_baseline": cpu, "clocks": clk, "batched": batched, "adjoint": adjoint,
         }
         print(json.dumps(line), flush=True)
     s_mx.close()
