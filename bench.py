@@ -11,7 +11,8 @@ paper's setting, with the same stopping rule).  A `batched` object adds the
 512-problem workload (first 128 of its 1024 levels), an `adjoint` object the
 gradient sweep of the adjoint workload (n = 4095, M = 1024).
 Steps are timed one by one with CUDA events on the solver's stream; L2 is
-flushed (256 MB write, outside the events) before every timed level.
+flushed (256 MB write, then a 256 MB read so that no dirty flush lines are
+left to write back) outside the events before every timed level.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
@@ -213,7 +214,9 @@ def run_arm(torch, pkg, prob, precision, W, K, flush, stream, e2e=False, warm=Fa
         s.timing()  # discard the warm-up kernel times
         evs = []
         for _ in range(K):
-            flush.zero_()
+            flush[0].zero_()            # write a buffer larger than L2 ...
+            flush[1].sum(dtype=torch.float64)  # ... then read another, so that the
+            # level does not start by writing the flush's dirty lines back to HBM
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -348,7 +351,8 @@ def ours(args):
     W = args.warmup
     K = args.steps if args.steps is not None else max(1, prob.M - W)
     stream = torch.cuda.Stream()
-    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device="cuda")
+    flush = (torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device="cuda"),
+             torch.zeros(256 * 1024 * 1024 // 8, dtype=torch.float64, device="cuda"))
     n = prob.n
 
     def barrier():
@@ -430,7 +434,7 @@ def ours(args):
                        "precision": "mixed: FP32 inner PBiCGSTAB, FP64 refinement/residual/SOE",
                        "krylov_tol": 1e-12, "inner_tol": 1e-2,
                        "initial_guess": "u^{m-1}" if (not args.cold_start) else "0 (Sec. 5)",
-                       "l2": "flushed before every timed level (256 MB write outside the events)",
+                       "l2": "flushed before every timed level (256 MB write, then 256 MB read, outside the events)",
                        "parallelism": f"replicas x{world}"},
             "status": st_mx["status"],
             "iterations_per_step": st_mx["its"] / K, "outer_per_step": st_mx["outer"] / K, "fp64_fallback_levels": st_mx.get("fallback", 0),

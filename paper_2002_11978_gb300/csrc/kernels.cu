@@ -187,57 +187,86 @@ __global__ void __launch_bounds__(kThreads, 2) k_apply32(ApplyArgs A) {
 // Gamma(1-gamma)); b = ahat u^{m-1} - sum_j G_j + f^m (Eq. (3.16gu) with the
 // history sum written through the SOE recurrence).  Also materialises
 // kappa^m in FP64 and FP32.
+constexpr int kRhsU = 8;      // exponentials whose history loads are issued together
+constexpr int kRhsPairs = 64; // entry pairs per block
+constexpr int kRhsGroups = kThreads / kRhsPairs;  // row groups per pair
+
+// Block = kRhsPairs entry pairs (i, i+1) x kRhsGroups row groups: the warps
+// of group g update rows [g c, (g+1) c) of the E x ld history for the
+// block's 64 pairs with 16-byte accesses (1 KB contiguous per row), kRhsU
+// rows' loads in flight at a time; the groups' partial sums are added in a
+// fixed order.
 __global__ void __launch_bounds__(kThreads) k_rhs(RhsArgs a) {
   extern __shared__ double sh[];
   double* s_eps = sh;
   double* s_cw = sh + a.Eact;
+  double2* s_part = reinterpret_cast<double2*>(sh + 2 * a.Eact);  // 16-byte aligned
   for (int j = threadIdx.x; j < a.Eact; j += blockDim.x) {
     s_eps[j] = a.eps[j];
     s_cw[j] = a.cw[j];
   }
   __syncthreads();
-  const int gstr = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gstr) {
-    const double u1 = a.u1[i];
-    double acc = 0.0;
-    if (a.Eact > 0) {
-      const double d = u1 - a.u2[i];
-      double* Gi = a.Gm + i;
-      const size_t ld = (size_t)a.ld;
-      int j = 0;
-      for (; j + 4 <= a.Eact; j += 4) {
-        double g0 = Gi[(j + 0) * ld], g1 = Gi[(j + 1) * ld];
-        double g2 = Gi[(j + 2) * ld], g3 = Gi[(j + 3) * ld];
-        g0 = s_eps[j + 0] * fma(s_cw[j + 0], d, g0);
-        g1 = s_eps[j + 1] * fma(s_cw[j + 1], d, g1);
-        g2 = s_eps[j + 2] * fma(s_cw[j + 2], d, g2);
-        g3 = s_eps[j + 3] * fma(s_cw[j + 3], d, g3);
-        Gi[(j + 0) * ld] = g0; Gi[(j + 1) * ld] = g1;
-        Gi[(j + 2) * ld] = g2; Gi[(j + 3) * ld] = g3;
-        acc += g0; acc += g1; acc += g2; acc += g3;
-      }
-      for (; j < a.Eact; ++j) {
-        double g0 = Gi[j * ld];
-        g0 = s_eps[j] * fma(s_cw[j], d, g0);
-        Gi[j * ld] = g0;
-        acc += g0;
+  const int npair = (a.n + 1) >> 1;
+  const size_t ld2 = (size_t)a.ld >> 1;  // row stride in pairs (ld is even)
+  const int lane = threadIdx.x % kRhsPairs, grp = threadIdx.x / kRhsPairs;
+  const int chunk = (a.Eact + kRhsGroups - 1) / kRhsGroups;
+  const int j0 = grp * chunk, j1 = min(a.Eact, j0 + chunk);
+  for (int base = blockIdx.x * kRhsPairs; base < npair; base += gridDim.x * kRhsPairs) {
+    const int pp = base + lane;
+    const int i = 2 * pp;
+    const bool in = pp < npair;
+    const bool two = i + 1 < a.n;
+    double sx = 0.0, sy = 0.0;
+    if (in && j1 > j0) {
+      const double dx = a.u1[i] - a.u2[i];
+      const double dy = two ? a.u1[i + 1] - a.u2[i + 1] : 0.0;
+      double2* G = reinterpret_cast<double2*>(a.Gm + i);
+      for (int j = j0; j < j1; j += kRhsU) {
+        double2 g[kRhsU];
+#pragma unroll
+        for (int u = 0; u < kRhsU; ++u)
+          if (j + u < j1) g[u] = G[(j + u) * ld2];
+#pragma unroll
+        for (int u = 0; u < kRhsU; ++u) {
+          if (j + u < j1) {
+            const double e = s_eps[j + u], c = s_cw[j + u];
+            g[u].x = e * fma(c, dx, g[u].x);
+            g[u].y = e * fma(c, dy, g[u].y);
+            G[(j + u) * ld2] = g[u];
+            sx += g[u].x;
+            sy += g[u].y;
+          }
+        }
       }
     }
-    double f;
-    if (a.f_m) {
-      f = a.f_m[i];
-    } else {
-      f = 0.0;
-      for (int q = 0; q < a.rank; ++q) f += a.Gr[q] * a.F[(size_t)q * a.n + i];
+    s_part[threadIdx.x] = make_double2(sx, sy);
+    __syncthreads();
+    if (grp == 0 && in) {
+      for (int q = 1; q < kRhsGroups; ++q) {
+        const double2 v = s_part[q * kRhsPairs + lane];
+        sx += v.x;
+        sy += v.y;
+      }
+      for (int h = 0; h < (two ? 2 : 1); ++h) {
+        const int ii = i + h;
+        double f;
+        if (a.f_m) {
+          f = a.f_m[ii];
+        } else {
+          f = 0.0;
+          for (int q = 0; q < a.rank; ++q) f += a.Gr[q] * a.F[(size_t)q * a.n + ii];
+        }
+        const double bi = a.ahat * a.u1[ii] - (h ? sy : sx) + f;
+        a.b[ii] = bi;
+        if (a.rhs_copy) a.rhs_copy[ii] = bi;
+        double k;
+        if (a.kap_m) k = a.kap_m[ii];
+        else k = a.kap0[ii] + (a.kap1 ? a.theta * a.kap1[ii] : 0.0);
+        a.kappa64[ii] = k;
+        a.kappa32[ii] = (float)k;
+      }
     }
-    const double bi = a.ahat * u1 - acc + f;
-    a.b[i] = bi;
-    if (a.rhs_copy) a.rhs_copy[i] = bi;
-    double k;
-    if (a.kap_m) k = a.kap_m[i];
-    else k = a.kap0[i] + (a.kap1 ? a.theta * a.kap1[i] : 0.0);
-    a.kappa64[i] = k;
-    a.kappa32[i] = (float)k;
+    __syncthreads();
   }
 }
 
@@ -281,9 +310,11 @@ int coop_blocks_per_sm(size_t smem) {
 }
 
 cudaError_t launch_rhs(const RhsArgs& a, cudaStream_t s) {
-  int grid = (a.n + kThreads - 1) / kThreads;
+  const int npair = (a.n + 1) / 2;
+  int grid = (npair + kRhsPairs - 1) / kRhsPairs;
   if (grid < 1) grid = 1;
-  size_t smem = 2 * (size_t)(a.Eact > 0 ? a.Eact : 1) * sizeof(double);
+  const size_t smem = (2 * (size_t)(a.Eact > 0 ? a.Eact : 1) + 1) * sizeof(double) +
+                      kThreads * sizeof(double2);
   k_rhs<<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
