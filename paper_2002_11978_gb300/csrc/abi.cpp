@@ -338,8 +338,6 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
   ok &= dalloc(c, &dsaG64, Nc) && dalloc(c, &dsbG64, Nc) && dalloc(c, &dsaG32, Nc) && dalloc(c, &dsbG32, Nc);
   ok &= dalloc(c, &dg64, n) && dalloc(c, &dg32, n);
   ok &= dalloc(c, &dS1, L) && dalloc(c, &dS2, L);
-  double2* dCf = nullptr;
-  ok &= dalloc(c, &dCf, 5 * (size_t)Nc);
   ok &= dalloc(c, &dpart, (size_t)kSlots * std::max(P.G, P.cl.G)) && dalloc(c, &dbar, 1);
   float2* dspT = nullptr;
   float2* dspG = nullptr;
@@ -379,7 +377,7 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
   P.saT64 = dsa64; P.sbT64 = dsb64; P.saT32 = dsa32; P.sbT32 = dsb32;
   P.lam = dlam; P.chirp64 = dch64; P.chirp32 = dch32; P.Bh64 = dBh64; P.Bh32 = dBh32;
   P.saG64 = dsaG64; P.sbG64 = dsbG64; P.saG32 = dsaG32; P.sbG32 = dsbG32;
-  P.g64 = dg64; P.g32 = dg32; P.S1 = dS1; P.S2 = dS2; P.Cf = dCf;
+  P.g64 = dg64; P.g32 = dg32; P.S1 = dS1; P.S2 = dS2;
   if (use_cluster) {
     // Toeplitz spectrum in the cluster engine's row-pass order
     const CGeo& g = P.cl;

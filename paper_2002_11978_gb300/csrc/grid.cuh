@@ -138,8 +138,7 @@ constexpr int kPre = 4;  // with 256 threads: work items of <= 1024 elements (n 
 // S1[k1*N2 + j2].  Without FULL only rows j1 < N1/2 can be non-zero
 // (nin <= L/2).
 template <typename R, bool FULL, class Pro>
-__device__ void passA_real(const DevPlan& P, const Smem<R>& sm, int nin, Pro& pro,
-                           cplx<R>* out = nullptr) {
+__device__ void passA_real(const DevPlan& P, const Smem<R>& sm, int nin, Pro& pro) {
   typedef cplx<R> Z;
   const Geo& g = P.gr;
   const int lc = lgct<R>(g), ct = 1 << lc;
@@ -148,7 +147,7 @@ __device__ void passA_real(const DevPlan& P, const Smem<R>& sm, int nin, Pro& pr
   const int total = N1 << lc;
   const int rows = FULL ? N1 : (N1 >> 1);
   const int tstride = P.L / g.Nfft;
-  Z* S1 = out ? out : reinterpret_cast<Z*>(P.S1);
+  Z* S1 = reinterpret_cast<Z*>(P.S1);
   const Z* tw = twL<R>(P);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int c0 = tile << lc;
@@ -239,17 +238,16 @@ enum { MID_APPLY = 0, MID_SPEC = 1, MID_CONV = 2 };
 //  MID_SPEC: forward only; stores sa = Re X_k / Nc, sb = Re conj X_k' / Nc
 //    (the spectrum of an even real sequence is real).
 //  MID_CONV: complex product Z'_k = Z_k * conv_k (geometry gc).
-// ld(idx) supplies the input spectrum element idx = k1 N2 + k2 (default:
-// the column pass's output S1); it is called once per element.
-template <typename R, int MID, class Ld>
-__device__ void passB_ld(const DevPlan& P, const Smem<R>& sm, const R* __restrict__ sa,
-                         const R* __restrict__ sb, R* sa_out, R* sb_out,
-                         const cplx<R>* __restrict__ conv, Ld& ld) {
+template <typename R, int MID>
+__device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__ sa,
+                      const R* __restrict__ sb, R* sa_out, R* sb_out,
+                      const cplx<R>* __restrict__ conv) {
   typedef cplx<R> Z;
   const Geo& g = (MID == MID_CONV) ? P.gc : P.gr;
   const int N1 = g.N1, N2 = g.N2;
   const int npairs = (N1 >> 1) + 1;
   const int tstride = P.L / g.Nfft;
+  const Z* S1 = reinterpret_cast<const Z*>(P.S1);
   Z* S2 = reinterpret_cast<Z*>(P.S2);
   const Z* tw = twL<R>(P);
   const R invNc = R(1.0) / R(P.Nc);
@@ -283,7 +281,7 @@ __device__ void passB_ld(const DevPlan& P, const Smem<R>& sm, const R* __restric
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int b = e & (B - 1), k2 = e >> lgB;
       const int row = b ? kb : ka;
-      sm.bA[e] = ld(row * N2 + k2);
+      sm.bA[e] = __ldcg(S1 + row * N2 + k2);
     }
     __syncthreads();
     Z* res = fft_batch<R, false>(sm.bA, sm.bB, N2, lgB, sm.tw, P.T);
@@ -335,20 +333,11 @@ __device__ void passB_ld(const DevPlan& P, const Smem<R>& sm, const R* __restric
   }
 }
 
-template <typename R, int MID>
-__device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__ sa,
-                      const R* __restrict__ sb, R* sa_out, R* sb_out,
-                      const cplx<R>* __restrict__ conv) {
-  const cplx<R>* S1 = reinterpret_cast<const cplx<R>*>(P.S1);
-  auto ld = [&](int idx) -> cplx<R> { return __ldcg(S1 + idx); };
-  passB_ld<R, MID>(P, sm, sa, sb, sa_out, sb_out, conv, ld);
-}
-
 // Pass C (+ optional fused pass A): inverse column FFTs, y_{2j} = Re z_j,
 // y_{2j+1} = Im z_j for j1 < N1/2.  epi(i, y_i) consumes each output and
 // returns the next product's input x_i (used only with DO_A).
 template <typename R, bool DO_A, class Epi>
-__device__ void passCA_real(const DevPlan& P, const Smem<R>& sm, Epi& epi, cplx<R>* out = nullptr) {
+__device__ void passCA_real(const DevPlan& P, const Smem<R>& sm, Epi& epi) {
   typedef cplx<R> Z;
   const Geo& g = P.gr;
   const int lc = lgct<R>(g), ct = 1 << lc;
@@ -357,7 +346,7 @@ __device__ void passCA_real(const DevPlan& P, const Smem<R>& sm, Epi& epi, cplx<
   const int total = N1 << lc;
   const int tstride = P.L / g.Nfft;
   const Z* S2 = reinterpret_cast<const Z*>(P.S2);
-  Z* S1 = out ? out : reinterpret_cast<Z*>(P.S1);
+  Z* S1 = reinterpret_cast<Z*>(P.S1);
   const Z* tw = twL<R>(P);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int c0 = tile << lc;
@@ -600,184 +589,6 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
       put_partial(P, SL_RR, block_sum((double)ar2, sm.red));
     }
     if (!gsync_sum2(P, sm.red, SL_RR0, SL_RR, 0u, rho_new, rr)) { out.status = TSFDE_ETIMEOUT; return out; }
-  }
-}
-
-// Right-preconditioned BiCGSTAB, the iteration of bicgstab with 8 grid
-// phases instead of 11 (for the FP32 inner solves of the mixed level solve;
-// prec only).  The column-pass spectra C(.) of r, p, v, s, t are kept in
-// P.Cf: the column transform is linear, so the products' inputs
-// p = r + beta (p - omega v) and s = r - alpha v are formed spectrally inside
-// the row pass's load, and the inverse column passes of v and t also leave
-// C(v), C(t) behind.  x and r are brought up to date lazily in the next
-// iteration's first column pass, and (rh, r) and (r, r) come from the
-// expansions (rh, s) - omega (rh, t) and (s,s) - 2 omega (s,t) + omega^2 (t,t)
-// (exact in exact arithmetic; the rounding of the cancellation is far below
-// the loose inner tolerances this is used with).
-template <typename R, class BInit>
-__device__ SolveRes bicgstab_fused(const DevPlan& P, const Smem<R>& sm, const KVecs<R>& V,
-                                   const R* __restrict__ kap, double ahat, double tol, int max_it,
-                                   BInit& binit) {
-  typedef cplx<R> Z;
-  const int n = P.n, Nc = P.Nc;
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int gstr = gridDim.x * blockDim.x;
-  const R a = (R)ahat;
-  Z* const Cr = reinterpret_cast<Z*>(P.Cf);
-  Z* const Cp = Cr + Nc;
-  Z* const Cv = Cp + Nc;
-  Z* const Cs = Cv + Nc;
-  Z* const Ct = Cs + Nc;
-  SolveRes out{TSFDE_OK, 0, 0.0};
-  // x = 0, r = rh = b; C(r) = C(b)
-  {
-    R acc = 0;
-    auto pro = [&](int i) -> R {
-      const R bi = binit(i);
-      V.x[i] = R(0); V.r[i] = bi; V.rh[i] = bi;
-      acc += bi * bi;
-      return bi;
-    };
-    passA_real<R, false>(P, sm, n, pro, Cr);
-    put_partial(P, SL_BB, block_sum((double)acc, sm.red));
-  }
-  double bb;
-  if (!gsync_sum(P, sm.red, SL_BB, bb)) { out.status = TSFDE_ETIMEOUT; return out; }
-  if (!isfinite(bb)) { out.status = TSFDE_ENONFINITE; return out; }
-  if (bb == 0.0) return out;
-  const double nb = sqrt(bb);
-  double rho = 1.0, alpha = 1.0, omega = 1.0, rho_new = bb, rr = bb;
-  int it = 0;
-  bool pending = false;  // x += alpha ph + omega sh and r = s - omega t still to apply
-  for (;;) {
-    const double relres = sqrt(rr) / nb;
-    out.relres = relres;
-    out.iters = it;
-    int st = TSFDE_OK;
-    if (!isfinite(relres) || !isfinite(rho_new)) st = TSFDE_ENONFINITE;
-    else if (relres < tol) st = -1;
-    else if (it >= max_it) st = TSFDE_ENOCONV;
-    else if (rho_new == 0.0 || omega == 0.0) st = TSFDE_EBREAKDOWN;
-    if (st != TSFDE_OK) {
-      if (pending) {
-        const R aR = (R)alpha, oR = (R)omega;
-        for (int i = gtid; i < n; i += gstr) V.x[i] = V.x[i] + aR * V.ph[i] + oR * V.sh[i];
-        if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
-      }
-      out.status = (st == -1) ? TSFDE_OK : st;
-      return out;
-    }
-    const double beta = (rho_new / rho) * (alpha / omega);
-    rho = rho_new;
-    ++it;
-    const bool first = !pending;
-    // row pass of P^{-1} p: C(r) = C(s) - omega C(t), C(p) = C(r) + beta (C(p) - omega C(v))
-    {
-      const R bR = (R)beta, oR = (R)omega;
-      auto ld = [&](int idx) -> Z {
-        Z cr;
-        if (first) {
-          cr = __ldcg(Cr + idx);
-        } else {
-          const Z cs = __ldcg(Cs + idx), ct = __ldcg(Ct + idx);
-          cr = mkc<R>(cs.x - oR * ct.x, cs.y - oR * ct.y);
-          Cr[idx] = cr;
-        }
-        Z cp = cr;
-        if (!first) {
-          const Z p0 = __ldcg(Cp + idx), v0 = __ldcg(Cv + idx);
-          cp = mkc<R>(cr.x + bR * (p0.x - oR * v0.x), cr.y + bR * (p0.y - oR * v0.y));
-        }
-        Cp[idx] = cp;
-        return cp;
-      };
-      passB_ld<R, MID_APPLY>(P, sm, saG<R>(P), sbG<R>(P), nullptr, nullptr, nullptr, ld);
-    }
-    if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
-    // ph = P^{-1} p; the previous iteration's x and r updates; C(ph) -> S1
-    {
-      const R aR = (R)alpha, oR = (R)omega;
-      auto epi = [&](int i, R y) -> R {
-        if (!first) {
-          V.x[i] = V.x[i] + aR * V.ph[i] + oR * V.sh[i];
-          V.r[i] = (V.r[i] - aR * V.v[i]) - oR * V.t[i];
-        }
-        V.ph[i] = y;
-        return y;
-      };
-      passCA_real<R, true>(P, sm, epi);
-    }
-    pending = false;
-    if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
-    passB<R, MID_APPLY>(P, sm, saT<R>(P), sbT<R>(P), nullptr, nullptr, nullptr);
-    if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
-    // v = M ph, (rh, v); C(v)
-    {
-      R acc = 0;
-      auto epi = [&](int i, R y) -> R {
-        const R vi = a * V.ph[i] + kap[i] * y;
-        V.v[i] = vi;
-        acc += V.rh[i] * vi;
-        return vi;
-      };
-      passCA_real<R, true>(P, sm, epi, Cv);
-      put_partial(P, SL_RV, block_sum((double)acc, sm.red));
-    }
-    double rv;
-    if (!gsync_sum(P, sm.red, SL_RV, rv)) { out.status = TSFDE_ETIMEOUT; return out; }
-    if (!isfinite(rv)) { out.status = TSFDE_ENONFINITE; return out; }
-    if (rv == 0.0) { out.status = TSFDE_EBREAKDOWN; return out; }
-    alpha = rho / rv;
-    // row pass of P^{-1} s: C(s) = C(r) - alpha C(v)
-    {
-      const R aR = (R)alpha;
-      auto ld = [&](int idx) -> Z {
-        const Z cr = __ldcg(Cr + idx), cv = __ldcg(Cv + idx);
-        const Z cs = mkc<R>(cr.x - aR * cv.x, cr.y - aR * cv.y);
-        Cs[idx] = cs;
-        return cs;
-      };
-      passB_ld<R, MID_APPLY>(P, sm, saG<R>(P), sbG<R>(P), nullptr, nullptr, nullptr, ld);
-    }
-    if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
-    {
-      auto epi = [&](int i, R y) -> R { V.sh[i] = y; return y; };
-      passCA_real<R, true>(P, sm, epi);
-    }
-    if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
-    passB<R, MID_APPLY>(P, sm, saT<R>(P), sbT<R>(P), nullptr, nullptr, nullptr);
-    if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
-    // t = M sh with s = r - alpha v: (rh,s), (rh,t), (s,s), (s,t), (t,t); C(t)
-    double d[5];
-    {
-      const R aR = (R)alpha;
-      R q0 = 0, q1 = 0, q2 = 0, q3 = 0, q4 = 0;
-      auto epi = [&](int i, R y) -> R {
-        const R ti = a * V.sh[i] + kap[i] * y;
-        V.t[i] = ti;
-        const R si = V.r[i] - aR * V.v[i];
-        const R hi = V.rh[i];
-        q0 += hi * si; q1 += hi * ti; q2 += si * si; q3 += si * ti; q4 += ti * ti;
-        return ti;
-      };
-      passCA_real<R, true>(P, sm, epi, Ct);
-      put_partial(P, SL_BB, block_sum((double)q0, sm.red));
-      put_partial(P, SL_TS, block_sum((double)q1, sm.red));
-      put_partial(P, SL_TT, block_sum((double)q2, sm.red));
-      put_partial(P, SL_RR0, block_sum((double)q3, sm.red));
-      put_partial(P, SL_RR, block_sum((double)q4, sm.red));
-      const int sl[5] = {SL_BB, SL_TS, SL_TT, SL_RR0, SL_RR};
-      if (!grid_sync_red(P.bar, P.timeout, P.part, P.G, 5, sl, 0u, d, sm.red)) {
-        out.status = TSFDE_ETIMEOUT;
-        return out;
-      }
-    }
-    const double rhs_ = d[0], rht = d[1], ss = d[2], st_ = d[3], tt = d[4];
-    omega = (tt > 0.0) ? st_ / tt : 0.0;
-    if (!isfinite(omega)) { out.status = TSFDE_ENONFINITE; return out; }
-    rho_new = rhs_ - omega * rht;
-    rr = fmax(ss - 2.0 * omega * st_ + omega * omega * tt, 0.0);
-    pending = true;
   }
 }
 

@@ -67,10 +67,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_level_mixed(LevelArgs A) {
   };
   auto inner = [&](double sc, SolveRes& ir) -> bool {
     auto binit = [&](int i) -> float { return (float)(A.r64[i] * sc); };
-    if (A.precond)
-      ir = bicgstab_fused<float>(P, S.f, A.k32, A.kappa32, A.ahat, A.inner_tol, A.inner_max_it, binit);
-    else
-      ir = bicgstab<float>(P, S.f, A.k32, A.kappa32, A.ahat, false, A.inner_tol, A.inner_max_it, binit);
+    ir = bicgstab<float>(P, S.f, A.k32, A.kappa32, A.ahat, A.precond != 0, A.inner_tol,
+                         A.inner_max_it, binit);
     return ir.status != TSFDE_ETIMEOUT;
   };
   mixed_level(A, S, conv, inner);

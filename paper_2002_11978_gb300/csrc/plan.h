@@ -103,8 +103,6 @@ struct DevPlan {
   double* g64; float* g32;  // first column of the circulant inverse (n)
   double2* S1;  // work: Nfft complex (double capacity, reused as float2)
   double2* S2;
-  double2* Cf;  // 5 x Nc complex: column-pass spectra of r, p, v, s, t (fused
-                // FP32 PBiCGSTAB; double capacity, used as float2)
   CGeo cl;
   // (sa, sb) pairs in the cluster engine's row-pass order: entry
   // q nbuf + (k2 << lgBq) + slot for the row k1 held in slot `slot` of CTA q
