@@ -55,6 +55,9 @@ def parse():
                     help="x0 = 0 for every level as in the paper's experiments (default: start "
                          "from u^{m-1}, same stopping rule ||r|| < tol ||b||)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
+    ap.add_argument("--paper-table11", action="store_true",
+                    help="only time the paper's own Table 11 FIDS+P runs (Example 2) on the GPU and "
+                         "print them next to the paper's CPU figures")
     ap.add_argument("--batched-levels", type=int, default=128,
                     help="levels of the batched workload timed (of M = 1024; 0 skips it)")
     return ap.parse_args()
@@ -143,9 +146,9 @@ def measured_peaks():
 # DRAM bytes per launch from one ncu capture (profiles/k_level_mixed_n131071_launches_traffic.md),
 # valid only for the kernel sources they were taken with: the digest of those sources is kept
 # beside the figure, and a changed source makes the figure null.
-TRAFFIC = {"k_level_mixed": {"bytes": 81.85e6, "note": "dram read+write, levels 9-11, ncu",
+TRAFFIC = {"k_level_mixed": {"bytes": 76.63e6, "note": "dram read+write, levels 9-11, ncu",
                              "sources": ["grid.cuh", "kernels.cu", "dev.cuh", "plan.h"],
-                             "sha1": "c1e9c8429cf4068603ccfd295aebd1232f5588f6"}}
+                             "sha1": "b603c732d0a5710bf248043f3115f175dfc2a3f5"}}
 
 
 def measured_traffic(kernel):
@@ -282,6 +285,51 @@ def batched_sample(torch, pkg, ti, levels, rank, world, stream, warm=True):
     return out
 
 
+# Table 11 (FIDS+P, Example 2, tol 1e-10, SOE eps 1e-9): the largest run of each (r, gamma,
+# alpha) group, with the paper's N, M and CPU seconds (MATLAB 2017b, Core i5-8265U).
+TABLE11 = [  # r, gamma, alpha, paper N, M, paper CPU s, printed Err_inf
+    (2, 0.5, 1.5, 512, 16384, 43.338, 1.333e-5),
+    (3, 0.8, 1.5, 1024, 8934, 34.543, 2.319e-6),
+    (3, 0.8, 1.9, 512, 8192, 21.436, 2.100e-5),
+]
+
+
+def paper_table11(torch, pkg, ti):
+    """Each run through the public API level by level (kappa^m and f^m of
+    Example 2 evaluated on the host and copied in, as the paper's code
+    forms them), FP64, x0 = 0, tol 1e-10 on the recursive residual."""
+    rows = []
+    for r, g, a, N, M, cpu_s, err_p in TABLE11:
+        prob = ti.example2(a, g, r, N, M)
+        s = pkg.Solver(a, g, 1.0, 1.0, prob.n, M, r, prob.soe_tol, krylov_tol=1e-10)
+        tm = s.times()
+        dev = lambda v: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float64, device="cuda")
+        s.set_problem(dev(prob.phi), torch.zeros(prob.n, dtype=torch.float64, device="cuda"))
+        kap_h = [prob.kappa_at(tm[m]) for m in range(M + 1)]
+        f_h = [prob.f_at(tm[m]) for m in range(M + 1)]
+        u = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+        kd = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+        fd = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+        err = 0.0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for m in range(1, M + 1):
+            kd.copy_(torch.from_numpy(kap_h[m]))
+            fd.copy_(torch.from_numpy(f_h[m]))
+            s.step(kappa_m=kd, f_m=fd, u_out=u, sync=False)
+            if m % 64 == 0 or m == M:
+                ex = prob.exact_table(tm[m:m + 1])[0]
+                err = max(err, float(np.max(np.abs(u.cpu().numpy() - ex))))
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        rows.append({"r": r, "gamma": g, "alpha": a, "N": N, "M": M, "gpu_s": t,
+                     "gpu_steps_per_s": M / t, "paper_cpu_s": cpu_s, "paper_steps_per_s": M / cpu_s,
+                     "speedup_vs_paper": cpu_s / t, "err_inf_sampled_levels": err,
+                     "paper_err_inf": err_p})
+        s.close()
+    return rows
+
+
 def adjoint_sample(torch, pkg, ti, stream):
     """The adjoint workload: n = 4095, M = 1024, J = 1/2 ||u^M - u_obs||^2
     with u_obs from another kappa; forward march (FP64, all levels kept) and
@@ -340,6 +388,11 @@ def ours(args):
     import paper_2002_11978_gb300 as pkg
     import tsfde_inputs as ti
     from paper_2002_11978_gb300 import build
+
+    if args.paper_table11:
+        build.build()
+        print(json.dumps({"paper_table11": paper_table11(torch, pkg, ti)}), flush=True)
+        return
 
     rank, local_rank, world = dist_env()
     torch.cuda.set_device(local_rank)

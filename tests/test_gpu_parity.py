@@ -311,3 +311,35 @@ def test_warm_start_large_levels_agree(torch):
     ref = out[("fp64", False)]
     for k, v in out.items():
         assert np.max(np.abs(v - ref)) / np.max(np.abs(ref)) < 1e-10, k
+
+
+def test_barrier_timeout_returns_status_and_context_survives(torch):
+    """A barrier that gives up at once (timeout of 1 cycle) turns into
+    TSFDE_ETIMEOUT from the level solve -- no hang, no trap -- and a fresh
+    context on the same device works afterwards."""
+    import paper_2002_11978_gb300 as pkg
+    prob = ti.config_smallest(n=63, M=4)
+    s = pkg.Solver(prob.alpha, prob.gamma, 1.0, 1.0, prob.n, prob.M, prob.r, 1e-12,
+                   barrier_timeout_cycles=1)
+    s.set_problem_from(prob)
+    with pytest.raises(pkg.TsfdeError) as e:
+        s.step()
+    assert e.value.status == pkg.TSFDE_ETIMEOUT
+    torch.cuda.synchronize()
+    s2 = pkg.Solver(prob.alpha, prob.gamma, 1.0, 1.0, prob.n, prob.M, prob.r, 1e-12)
+    s2.set_problem_from(prob)
+    assert s2.step()["status"] == 0
+
+
+def test_nonfinite_input_is_reported(torch):
+    """A NaN in the right-hand side is reported as TSFDE_ENONFINITE."""
+    import paper_2002_11978_gb300 as pkg
+    n = 127
+    s = solver(n=n)
+    kap = np.ones(n)
+    b = np.ones(n)
+    b[5] = np.nan
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    with pytest.raises(pkg.TsfdeError) as e:
+        s.linear_solve(10.0, cuda(torch, kap), cuda(torch, b), x)
+    assert e.value.status == pkg.TSFDE_ENONFINITE
