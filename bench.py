@@ -55,6 +55,9 @@ def parse():
                     help="x0 = 0 for every level as in the paper's experiments (default: start "
                          "from u^{m-1}, same stopping rule ||r|| < tol ||b||)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
+    ap.add_argument("--inner", choices=["fp32", "ds"], default="fp32",
+                    help="arithmetic of the mixed arm's inner PBiCGSTAB: FP32, or double-single "
+                         "(FP32 pairs, ~48-bit significand)")
     ap.add_argument("--paper-table11", action="store_true",
                     help="only time the paper's own Table 11 FIDS+P runs (Example 2) on the GPU and "
                          "print them next to the paper's CPU figures")
@@ -417,7 +420,9 @@ def ours(args):
     clocks = ClockSampler(torch.cuda.current_device())
     barrier()
     clocks.start()
-    s_mx, ms_mx, tim_mx, st_mx = run_arm(torch, pkg, prob, "mixed", W, K, flush, stream, warm=(not args.cold_start))
+    ds = args.inner == "ds"
+    prec_mx = "mixed_ds" if ds else "mixed"
+    s_mx, ms_mx, tim_mx, st_mx = run_arm(torch, pkg, prob, prec_mx, W, K, flush, stream, warm=(not args.cold_start))
     barrier()
     clk = clocks.stop()
     t_mx = max_over_ranks([sum(ms_mx) / 1e3], "cuda")[0]
@@ -441,7 +446,7 @@ def ours(args):
     # ---- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        se, ms_e2e, _, _ = run_arm(torch, pkg, prob, "mixed", W, K, flush, stream, e2e=True,
+        se, ms_e2e, _, _ = run_arm(torch, pkg, prob, prec_mx, W, K, flush, stream, e2e=True,
                                     warm=(not args.cold_start))
         se.close()
         e2e = {"value": world * K / (sum(ms_e2e) / 1e3), "unit": "steps/s",
@@ -453,10 +458,13 @@ def ours(args):
     rhs_ms = tim_mx["rhs_ms"] / K
     lvl_ms = tim_mx["level_ms"] / K
     rhs_bytes = (16.0 * n * st_mx["E_active_sum"] + K * 8.0 * n * (3 + 1)) / K
-    lvl_bytes = (88.0 * n * st_mx["its"] + 40.0 * n * st_mx["outer"]) / K
+    # 22 inner-vector accesses per inner iteration (4 or 8 bytes per entry),
+    # 5 FP64 vector accesses per refinement sweep
+    lvl_bytes = ((176.0 if ds else 88.0) * n * st_mx["its"] + 40.0 * n * st_mx["outer"]) / K
+    kname = "k_level_mixed_ds" if ds else "k_level_mixed"
     rhs_gbs = rhs_bytes / (rhs_ms * 1e-3) / 1e9
     lvl_gbs = lvl_bytes / (lvl_ms * 1e-3) / 1e9
-    dom = ("k_level_mixed", lvl_gbs) if lvl_ms >= rhs_ms else ("k_rhs", rhs_gbs)
+    dom = (kname, lvl_gbs) if lvl_ms >= rhs_ms else ("k_rhs", rhs_gbs)
     roof = {"kernel": dom[0], "bound": "hbm", "achieved": dom[1], "peak": peak, "unit": "GB/s",
             "frac": dom[1] / peak, "traffic": measured_traffic(dom[0]), "peak_source": f"{peak_kind} hbm_gbs"}
 
@@ -484,7 +492,8 @@ def ours(args):
             "steps": K, "warmup": W, "ms_per_step": t_mx * 1e3 / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "M": prob.M, "first_timed_level": W + 1,
-                       "precision": "mixed: FP32 inner PBiCGSTAB, FP64 refinement/residual/SOE",
+                       "precision": ("mixed: double-single (FP32-pair) inner PBiCGSTAB" if ds else
+                                     "mixed: FP32 inner PBiCGSTAB") + ", FP64 refinement/residual/SOE",
                        "krylov_tol": 1e-12, "inner_tol": 1e-2,
                        "initial_guess": "u^{m-1}" if (not args.cold_start) else "0 (Sec. 5)",
                        "l2": "flushed before every timed level (256 MB write, then 256 MB read, outside the events)",
@@ -493,8 +502,8 @@ def ours(args):
             "iterations_per_step": st_mx["its"] / K, "outer_per_step": st_mx["outer"] / K, "fp64_fallback_levels": st_mx.get("fallback", 0),
             "krylov_its_per_s": world * st_mx["its"] / t_mx,
             "kernels": {"k_rhs": {"ms": rhs_ms, "bytes": rhs_bytes, "GB/s": rhs_gbs, "frac": rhs_gbs / peak},
-                        "k_level_mixed": {"ms": lvl_ms, "bytes": lvl_bytes, "GB/s": lvl_gbs,
-                                          "frac": lvl_gbs / peak}},
+                        kname: {"ms": lvl_ms, "bytes": lvl_bytes, "GB/s": lvl_gbs,
+                                "frac": lvl_gbs / peak}},
             "fp64": fp64, "e2e": e2e, "gpu_launches": 2 * K, "roofline": roof,
             "cpu_baseline": cpu, "clocks": clk, "batched": batched, "adjoint": adjoint,
         }

@@ -49,7 +49,16 @@ typedef enum tsfde_status {
   TSFDE_ENOTSUP = 9      /* option not supported by this build             */
 } tsfde_status;
 
-enum { TSFDE_FP64 = 0, TSFDE_MIXED = 1 };       /* tsfde_opts.precision */
+/* tsfde_opts.precision.  FP64: PBiCGSTAB in FP64.  MIXED and MIXED_DS: FP64
+ * iterative refinement (FP64 residual b - M u and update) around an inner
+ * PBiCGSTAB that runs in FP32 (MIXED) or in double-single arithmetic
+ * (MIXED_DS: every value an unevaluated sum of two FP32 numbers, about 48
+ * significant bits, computed on the FP32 pipes).  FP32 products cannot
+ * resolve a spectral range of ~1e8 (the IFL symbol at n ~ 1e5), so MIXED
+ * needs more inner iterations and may finish levels in FP64; MIXED_DS
+ * resolves it and converges like FP64 at FP32-pipe cost.  The
+ * preconditioner is always built in FP64 and rounded. */
+enum { TSFDE_FP64 = 0, TSFDE_MIXED = 1, TSFDE_MIXED_DS = 2 };
 enum { TSFDE_STRANG = 0, TSFDE_PRECOND_NONE = 1 }; /* tsfde_opts.precond */
 /* tsfde_opts.engine: how a mixed level solve runs its FP32 inner solves.
  * GRID: spread over the whole cooperative grid (grid barriers between the
@@ -66,17 +75,23 @@ typedef struct tsfde_opts {
                            <= 0 selects the paper's default 1 + alpha/2     */
   int kappa_mu;         /* 1 for mu < 2, 2 for mu = 2; 0 derives it from mu */
   double krylov_tol;    /* FP64 path: stop when ||r_k||_2/||r_0||_2 < tol
-                           (recursive residual, x0 = 0, Sec. 5); mixed path:
-                           stop the FP64 refinement when the last correction
-                           satisfies max|e| <= tol * max|u|, or when a sweep
-                           no longer halves the FP64 residual (it has reached
-                           its rounding floor).  Default 1e-12              */
+                           (recursive residual, x0 = 0, Sec. 5); mixed paths:
+                           stop the FP64 refinement when the true FP64
+                           residual satisfies ||b - M u|| <= tol ||b||, or
+                           the last correction max|e| <= tol * max|u|, or a
+                           sweep no longer halves the FP64 residual (it has
+                           reached its rounding floor).  Default 1e-12      */
   int max_it;           /* BiCGSTAB iteration cap per solve (default 2000)  */
-  int precision;        /* TSFDE_FP64 (default) or TSFDE_MIXED              */
+  int precision;        /* TSFDE_FP64 (default), TSFDE_MIXED or
+                           TSFDE_MIXED_DS                                   */
   int precond;          /* TSFDE_STRANG (default) or TSFDE_PRECOND_NONE     */
-  double inner_tol;     /* mixed: FP32 inner relative tolerance (def. 1e-2) */
+  double inner_tol;     /* MIXED: FP32 inner relative tolerance (default
+                           1e-2).  MIXED_DS ignores it and inner_max_it:
+                           each of its inner solves asks for the
+                           whole remaining reduction, tol ||b|| / ||r|| / 2
+                           (not below 1e-13), within max_it iterations      */
   int max_outer;        /* mixed: FP64 refinement cap (default 60)          */
-  int inner_max_it;     /* mixed: FP32 BiCGSTAB iterations per refinement
+  int inner_max_it;     /* MIXED: inner BiCGSTAB iterations per refinement
                            sweep (default 40).  The inner solve stops there
                            even short of inner_tol: at large n its FP32
                            products cannot resolve every residual, and the
@@ -94,8 +109,8 @@ typedef struct tsfde_opts {
   void* stream;         /* cudaStream_t; NULL = default stream              */
   int engine;           /* TSFDE_ENGINE_* (default AUTO); a MIXED context
                            asking for CLUSTER where it cannot run fails
-                           tsfde_setup with TSFDE_ENOTSUP; FP64 contexts
-                           ignore the field                                 */
+                           tsfde_setup with TSFDE_ENOTSUP; FP64 and
+                           MIXED_DS contexts ignore the field (grid only)   */
   int cluster_size;     /* batched solve: CTAs per thread-block cluster,
                            4, 8 or 16; 0 (default) picks the size that keeps
                            the most CTAs resident                           */
@@ -303,8 +318,9 @@ int tsfde_get_timing(tsfde_ctx* ctx, tsfde_timing* out);
 /* ---- single operations of the hot path (used by tests and tools) ------ */
 
 /* y = A v (Toeplitz product by zero-padded FFT circulant embedding,
- * Sec. 4.1).  v, y: dev n.  precision: TSFDE_FP64 or TSFDE_MIXED (FP32
- * transform, FP64 in/out). */
+ * Sec. 4.1).  v, y: dev n.  precision: TSFDE_FP64, TSFDE_MIXED (FP32
+ * transform) or TSFDE_MIXED_DS (double-single transform; only in a context
+ * set up with that precision, else TSFDE_EINVAL); FP64 in/out. */
 int tsfde_toeplitz_apply(tsfde_ctx* ctx, const double* v, double* y, int precision);
 
 /* y = (a I + diag(kappa) A) v, the matrix-free product of Sec. 4.1.

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libtsfde.so")
 
 TSFDE_OK, TSFDE_EINVAL, TSFDE_ENOMEM, TSFDE_ECUDA, TSFDE_ENOCONV = 0, 1, 2, 3, 4
 TSFDE_EBREAKDOWN, TSFDE_ETIMEOUT, TSFDE_ESTATE, TSFDE_ENONFINITE, TSFDE_ENOTSUP = 5, 6, 7, 8, 9
-TSFDE_FP64, TSFDE_MIXED = 0, 1
+TSFDE_FP64, TSFDE_MIXED, TSFDE_MIXED_DS = 0, 1, 2
 TSFDE_STRANG, TSFDE_PRECOND_NONE = 0, 1
 TSFDE_ENGINE_AUTO, TSFDE_ENGINE_GRID, TSFDE_ENGINE_CLUSTER = 0, 1, 2
 
@@ -199,7 +199,7 @@ class Solver:
                     "cluster": TSFDE_ENGINE_CLUSTER}[engine]
         o.krylov_tol = krylov_tol
         o.max_it = max_it
-        o.precision = {"fp64": TSFDE_FP64, "mixed": TSFDE_MIXED}[precision]
+        o.precision = {"fp64": TSFDE_FP64, "mixed": TSFDE_MIXED, "mixed_ds": TSFDE_MIXED_DS}[precision]
         o.precond = {"strang": TSFDE_STRANG, "none": TSFDE_PRECOND_NONE}[precond]
         o.inner_tol = inner_tol
         o.max_outer = max_outer
@@ -448,7 +448,8 @@ def toeplitz_apply_static(alpha, n, v, y, l=1.0, mu=None, kappa_mu=None, stream=
 
 
 def _prec(p):
-    return {"fp64": TSFDE_FP64, "mixed": TSFDE_MIXED, "fp32": TSFDE_MIXED}[p]
+    return {"fp64": TSFDE_FP64, "mixed": TSFDE_MIXED, "fp32": TSFDE_MIXED,
+            "mixed_ds": TSFDE_MIXED_DS, "ds": TSFDE_MIXED_DS}[p]
 
 
 def _info_dict(info):

@@ -40,6 +40,8 @@ struct tsfde_ctx {
   float* kappa32 = nullptr;
   KVecs<double> k64{};
   KVecs<float> k32{};
+  KVecs<dsf> kds{};        // TSFDE_MIXED_DS inner vectors
+  dsf* kappads = nullptr;
   double* r64 = nullptr;
   StepStat* stats = nullptr;
   int* status = nullptr;
@@ -175,11 +177,11 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
   if (kmu != 1 && kmu != 2) return fail(c, TSFDE_EINVAL, "kappa_mu must be 1 or 2");
   if (!(o.krylov_tol > 0.0)) return fail(c, TSFDE_EINVAL, "krylov_tol must be positive");
   if (o.max_it < 1) return fail(c, TSFDE_EINVAL, "max_it must be >= 1");
-  if (o.precision != TSFDE_FP64 && o.precision != TSFDE_MIXED)
-    return fail(c, TSFDE_EINVAL, "precision must be TSFDE_FP64 or TSFDE_MIXED");
+  if (o.precision != TSFDE_FP64 && o.precision != TSFDE_MIXED && o.precision != TSFDE_MIXED_DS)
+    return fail(c, TSFDE_EINVAL, "precision must be TSFDE_FP64, TSFDE_MIXED or TSFDE_MIXED_DS");
   if (o.precond != TSFDE_STRANG && o.precond != TSFDE_PRECOND_NONE)
     return fail(c, TSFDE_EINVAL, "precond must be TSFDE_STRANG or TSFDE_PRECOND_NONE");
-  if (o.precision == TSFDE_MIXED &&
+  if (o.precision != TSFDE_FP64 &&
       (!(o.inner_tol > 0.0 && o.inner_tol < 1.0) || o.max_outer < 1 || o.inner_max_it < 1))
     return fail(c, TSFDE_EINVAL, "mixed needs inner_tol in (0,1), max_outer >= 1, inner_max_it >= 1");
   if (o.barrier_timeout_cycles < 0) return fail(c, TSFDE_EINVAL, "barrier_timeout_cycles < 0");
@@ -356,7 +358,36 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
   for (float** p : v32) ok &= dalloc(c, p, ld);
   ok &= dalloc(c, &c->stats, M + 1) && dalloc(c, &c->status, 1);
   ok &= dalloc(c, &c->k64.x, n);  // FP64 correction of the mixed fallback
+  // double-single tables and inner vectors
+  const bool ds = o.precision == TSFDE_MIXED_DS;
+  dsf2* dtwds = nullptr;
+  dsf *dsads = nullptr, *dsbds = nullptr, *dsaGds = nullptr, *dsbGds = nullptr;
+  if (ds) {
+    ok &= dalloc(c, &dtwds, L) && dalloc(c, &dsads, Nc) && dalloc(c, &dsbds, Nc) &&
+          dalloc(c, &dsaGds, Nc) && dalloc(c, &dsbGds, Nc) && dalloc(c, &c->kappads, ld);
+    dsf** vds[] = {&c->kds.x, &c->kds.r, &c->kds.rh, &c->kds.p, &c->kds.v, &c->kds.s, &c->kds.t,
+                   &c->kds.ph, &c->kds.sh};
+    for (dsf** p : vds) ok &= dalloc(c, p, ld);
+  }
   if (!ok) return fail(c, TSFDE_ENOMEM, "cudaMalloc failed");
+  if (ds) {
+    std::vector<dsf2> twds(L);
+    for (int64_t k = 0; k < L; ++k) {
+      twds[k].x = dsf(tw[k].real());
+      twds[k].y = dsf(tw[k].imag());
+    }
+    std::vector<dsf> sads(Nc), sbds(Nc);
+    for (int i = 0; i < Nc; ++i) {
+      sads[i] = dsf(sa[i]);
+      sbds[i] = dsf(sb[i]);
+    }
+    if ((e = upload(dtwds, twds)) != cudaSuccess || (e = upload(dsads, sads)) != cudaSuccess ||
+        (e = upload(dsbds, sbds)) != cudaSuccess)
+      return cuda_fail(c, e, "upload");
+    P.twLds = dtwds;
+    P.saTds = dsads; P.sbTds = dsbds;
+    P.saGds = dsaGds; P.sbGds = dsbGds;
+  }
 
   if ((e = upload(dtw64, tw64)) != cudaSuccess || (e = upload(dtw32, tw32)) != cudaSuccess ||
       (e = upload(dsa64, sa)) != cudaSuccess || (e = upload(dsb64, sb)) != cudaSuccess ||
@@ -493,6 +524,8 @@ static LevelArgs level_args(tsfde_ctx* c, double ahat, const double* b, double* 
   A.inner_max_it = c->opts.inner_max_it;
   A.k64 = c->k64;
   A.k32 = c->k32;
+  A.kds = c->kds;
+  A.kappads = c->kappads;
   A.r64 = c->r64;
   A.stat = st;
   return A;
@@ -517,7 +550,7 @@ static cudaError_t launch_level_ctx(tsfde_ctx* c, LevelArgs& A) {
     A.P.G = A.P.cl.G;
     return launch_level_cluster(A, c->stream);
   }
-  return launch_level(A, c->opts.precision == TSFDE_MIXED, c->stream);
+  return launch_level(A, c->opts.precision, c->stream);
 }
 
 // Enqueue level m = c->m + 1.
@@ -704,7 +737,10 @@ int tsfde_get_symbol(const tsfde_ctx* c, double* t) {
 static int run_apply(tsfde_ctx* c, int kind, double a, double kbar, const double* kappa, const double* v,
                      double* y, int precision) {
   if (!c || !v || !y) return TSFDE_EINVAL;
-  if (precision != TSFDE_FP64 && precision != TSFDE_MIXED) return fail(c, TSFDE_EINVAL, "bad precision");
+  if (precision != TSFDE_FP64 && precision != TSFDE_MIXED && precision != TSFDE_MIXED_DS)
+    return fail(c, TSFDE_EINVAL, "bad precision");
+  if (precision == TSFDE_MIXED_DS && !c->P.twLds)
+    return fail(c, TSFDE_EINVAL, "double-single products need a context set up with TSFDE_MIXED_DS");
   ApplyArgs A{};
   A.P = c->P;
   A.kind = kind;
@@ -714,7 +750,7 @@ static int run_apply(tsfde_ctx* c, int kind, double a, double kbar, const double
   A.v = v;
   A.y = y;
   A.status = c->status;
-  cudaError_t e = launch_apply(A, precision == TSFDE_MIXED, c->stream);
+  cudaError_t e = launch_apply(A, precision, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "apply kernel");
   int st = 0;
   if ((e = cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||

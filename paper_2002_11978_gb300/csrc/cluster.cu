@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(kCT, 1) k_level_cluster(LevelArgs A) {
   SmemAll S = smem_setup(P);
   const int N1 = P.gr.N1, N2 = P.gr.N2, lgN2 = P.gr.lgN2;
   auto conv = [&](int k) {
+    if (!A.precond) return;
     const int k1 = k >> lgN2, k2 = k & (N2 - 1);
     int u, b;
     unit_of(k1, N1, u, b);
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(kCT, 1) k_level_cluster(LevelArgs A) {
     P.spG_cl[(size_t)r * cg_.nbuf + (k2 << cg_.lgBq) + slot] =
         make_float2((float)P.saG64[k], (float)P.sbG64[k]);
   };
-  auto inner = [&](double sc, SolveRes& ir) -> bool {
+  auto inner = [&](double sc, double, SolveRes& ir) -> bool {
     double its = 0.0, stv = 0.0;
     if ((int)blockIdx.x < cg_.Q) {
       const CeLay lay = cluster_layout(cg_);
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(kCT, 1) k_level_cluster(LevelArgs A) {
     ir.status = (int)o_st;
     return ok;
   };
-  mixed_level(A, S, conv, inner);
+  mixed_level(A, S, conv, inner, A.k32.x);
 }
 
 // ------------------------------------------------------------- host side

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dsf.cuh"
 #include "plan.h"
 
 namespace tsfde {
@@ -14,6 +15,7 @@ namespace tsfde {
 template <typename R> struct CT;
 template <> struct CT<double> { using T = double2; };
 template <> struct CT<float> { using T = float2; };
+template <> struct CT<dsf> { using T = dsf2; };
 template <typename R> using cplx = typename CT<R>::T;
 
 template <typename R> __device__ __forceinline__ cplx<R> mkc(R x, R y) {

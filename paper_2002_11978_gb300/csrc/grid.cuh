@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <type_traits>
 
 #include "../../include/tsfde.h"
 #include "dev.cuh"
@@ -36,58 +37,81 @@ template <typename R> struct Smem {
   double* red;  // 33 doubles
 };
 
+// Tables of each arithmetic type.  The Bluestein tables (chirp, Bh, gcol)
+// exist in FP64 and FP32 only: the preconditioner is never built in
+// double-single.
+template <typename R> constexpr bool is_f64 = std::is_same_v<R, double>;
+template <typename R> constexpr bool is_ds = std::is_same_v<R, dsf>;
+
 template <typename R> __device__ __forceinline__ const cplx<R>* twL(const DevPlan& P) {
-  if constexpr (sizeof(R) == 8) return P.twL64; else return P.twL32;
+  if constexpr (is_f64<R>) return P.twL64;
+  else if constexpr (is_ds<R>) return P.twLds;
+  else return P.twL32;
 }
 template <typename R> __device__ __forceinline__ int lgct(const Geo& g) {
-  if constexpr (sizeof(R) == 8) return g.lgct64; else return g.lgct32;
+  if constexpr (sizeof(cplx<R>) == 16) return g.lgct64; else return g.lgct32;
 }
 template <typename R> __device__ __forceinline__ const R* saT(const DevPlan& P) {
-  if constexpr (sizeof(R) == 8) return P.saT64; else return P.saT32;
+  if constexpr (is_f64<R>) return P.saT64;
+  else if constexpr (is_ds<R>) return P.saTds;
+  else return P.saT32;
 }
 template <typename R> __device__ __forceinline__ const R* sbT(const DevPlan& P) {
-  if constexpr (sizeof(R) == 8) return P.sbT64; else return P.sbT32;
+  if constexpr (is_f64<R>) return P.sbT64;
+  else if constexpr (is_ds<R>) return P.sbTds;
+  else return P.sbT32;
 }
 template <typename R> __device__ __forceinline__ R* saG(const DevPlan& P) {
-  if constexpr (sizeof(R) == 8) return P.saG64; else return P.saG32;
+  if constexpr (is_f64<R>) return P.saG64;
+  else if constexpr (is_ds<R>) return P.saGds;
+  else return P.saG32;
 }
 template <typename R> __device__ __forceinline__ R* sbG(const DevPlan& P) {
-  if constexpr (sizeof(R) == 8) return P.sbG64; else return P.sbG32;
+  if constexpr (is_f64<R>) return P.sbG64;
+  else if constexpr (is_ds<R>) return P.sbGds;
+  else return P.sbG32;
 }
 template <typename R> __device__ __forceinline__ const cplx<R>* chirp(const DevPlan& P) {
-  if constexpr (sizeof(R) == 8) return P.chirp64; else return P.chirp32;
+  if constexpr (is_f64<R>) return P.chirp64; else return P.chirp32;
 }
 template <typename R> __device__ __forceinline__ const cplx<R>* Bh(const DevPlan& P) {
-  if constexpr (sizeof(R) == 8) return P.Bh64; else return P.Bh32;
+  if constexpr (is_f64<R>) return P.Bh64; else return P.Bh32;
 }
 template <typename R> __device__ __forceinline__ R* gcol(const DevPlan& P) {
-  if constexpr (sizeof(R) == 8) return P.g64; else return P.g32;
+  if constexpr (is_f64<R>) return P.g64; else return P.g32;
 }
 
 struct SmemAll {
   Smem<double> d;
   Smem<float> f;
+  Smem<dsf> s;  // tw is NULL unless the plan has double-single tables
 };
 
+// Shared memory: [tw64 T][tw32 T][twds T][bufA W][bufB W][red 64]
 __device__ __forceinline__ SmemAll smem_setup(const DevPlan& P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   char* base = reinterpret_cast<char*>(smem_raw);
   double2* tw64 = reinterpret_cast<double2*>(base);
   float2* tw32 = reinterpret_cast<float2*>(base + (size_t)P.T * sizeof(double2));
-  char* wbase = base + (size_t)P.T * (sizeof(double2) + sizeof(float2));
+  dsf2* twds = reinterpret_cast<dsf2*>(base + (size_t)P.T * (sizeof(double2) + sizeof(float2)));
+  char* wbase = base + (size_t)P.T * (2 * sizeof(double2) + sizeof(float2));
   double2* bA = reinterpret_cast<double2*>(wbase);
   double2* bB = bA + P.W;
   double* red = reinterpret_cast<double*>(bB + P.W);
   const int stride = P.L / P.T;
+  const bool ds = P.twLds != nullptr;
   for (int k = threadIdx.x; k < P.T; k += blockDim.x) {
     tw64[k] = P.twL64[k * stride];
     tw32[k] = P.twL32[k * stride];
+    if (ds) twds[k] = P.twLds[k * stride];
   }
   __syncthreads();
   SmemAll s;
   s.d.tw = tw64; s.d.bA = bA; s.d.bB = bB; s.d.red = red;
   s.f.tw = tw32; s.f.bA = reinterpret_cast<float2*>(bA); s.f.bB = reinterpret_cast<float2*>(bB);
   s.f.red = red;
+  s.s.tw = ds ? twds : nullptr; s.s.bA = reinterpret_cast<dsf2*>(bA); s.s.bB = reinterpret_cast<dsf2*>(bB);
+  s.s.red = red;
   return s;
 }
 
@@ -250,7 +274,7 @@ __device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__
   const Z* S1 = reinterpret_cast<const Z*>(P.S1);
   Z* S2 = reinterpret_cast<Z*>(P.S2);
   const Z* tw = twL<R>(P);
-  const R invNc = R(1.0) / R(P.Nc);
+  const R invNc = R(1.0 / (double)P.Nc);  // Nc is a power of two: exact
   for (int it = blockIdx.x; it < npairs; it += gridDim.x) {
     const int ka = it;
     const int kb = (it == 0 || it == (N1 >> 1)) ? -1 : N1 - it;
@@ -281,7 +305,7 @@ __device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int b = e & (B - 1), k2 = e >> lgB;
       const int row = b ? kb : ka;
-      sm.bA[e] = __ldcg(S1 + row * N2 + k2);
+      sm.bA[e] = ldcg(S1 + row * N2 + k2);
     }
     __syncthreads();
     Z* res = fft_batch<R, false>(sm.bA, sm.bB, N2, lgB, sm.tw, P.T);
@@ -363,7 +387,7 @@ __device__ void passCA_real(const DevPlan& P, const Smem<R>& sm, Epi& epi) {
     }
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int k1 = e >> lc, c = e & (ct - 1);
-      sm.bA[e] = __ldcg(S2 + k1 * N2 + c0 + c);
+      sm.bA[e] = ldcg(S2 + k1 * N2 + c0 + c);
     }
     __syncthreads();
     Z* res = fft_batch<R, true>(sm.bA, sm.bB, N1, lc, sm.tw, P.T);
@@ -407,7 +431,7 @@ __device__ void passC_cplx(const DevPlan& P, const Smem<R>& sm, Epi& epi) {
     const int c0 = tile << lc;
     for (int e = threadIdx.x; e < (N1 << lc); e += blockDim.x) {
       const int k1 = e >> lc, c = e & (ct - 1);
-      sm.bA[e] = __ldcg(S2 + k1 * N2 + c0 + c);
+      sm.bA[e] = ldcg(S2 + k1 * N2 + c0 + c);
     }
     __syncthreads();
     const Z* res = fft_batch<R, true>(sm.bA, sm.bB, N1, lc, sm.tw, P.T);
@@ -641,24 +665,28 @@ static __device__ bool warm_residual(const LevelArgs& A, SmemAll& S, double& bb,
   return gsync_sum2(P, S.d.red, SL_BB, SL_RES, 0u, bb, rr);
 }
 
-// Mixed level solve (shared by both engines).  conv(k) rounds entry k of the
-// FP64 preconditioner spectrum into the inner solver's FP32 tables;
-// inner(sc, res) solves (ahat I + K A) e = sc r64 in FP32 into k32.x (false
-// on a barrier timeout).
-// FP64 refinement around an FP32 PBiCGSTAB: each sweep
-// solves (ahat I + K A) e = r / ||r|| in FP32 (at most inner_max_it
+// Mixed level solve (shared by both engines and both inner arithmetics).
+// conv(k), called for every k < Nc after the preconditioner build, rounds
+// entry k of the FP64 preconditioner spectrum into the inner solver's
+// tables (and whatever else the inner solver needs rounded);
+// inner(sc, target, res) solves (ahat I + K A) e = sc r64 in the inner
+// arithmetic into e (false on a barrier timeout); target = tol ||b|| / ||r||
+// is the relative reduction that would meet the FP64 path's criterion.
+// FP64 refinement around a lower-precision PBiCGSTAB: each sweep
+// solves (ahat I + K A) e = r / ||r|| (at most inner_max_it
 // iterations), forms w = M e in FP64 and updates u += theta e,
 // r -= theta w with theta = 1, or the minimal-residual
 // theta = (r, w)/(w, w) when the full step would raise ||r||, so the FP64
 // residual never grows.  Stops when the last step satisfies
-// max|theta e| <= tol max|u|, or when a sweep no longer halves ||r|| with
+// max|theta e| <= tol max|u|, or ||r|| <= tol ||b|| (the FP64 path's
+// criterion, on the true residual), or when a sweep no longer halves ||r|| with
 // ||r||/||b|| <= 1e-9 (its rounding floor at large n) and the step is below
 // 100 tol max|u|.  After three sweeps
 // without progress above that, or at max_outer, the level is finished by
 // FP64 PBiCGSTAB on the remaining residual, so a level never returns an
 // unconverged answer.
-template <class Conv, class Inner>
-__device__ void mixed_level(const LevelArgs& A, SmemAll& S, Conv& conv, Inner& inner) {
+template <typename RI, class Conv, class Inner>
+__device__ void mixed_level(const LevelArgs& A, SmemAll& S, Conv& conv, Inner& inner, const RI* e) {
   const DevPlan& P = A.P;
   const int n = P.n;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -674,8 +702,7 @@ __device__ void mixed_level(const LevelArgs& A, SmemAll& S, Conv& conv, Inner& i
   }
   double bb, rr0;
   {
-    if (A.precond)
-      for (int k = gtid; k < P.Nc; k += gstr) conv(k);
+    for (int k = gtid; k < P.Nc; k += gstr) conv(k);
     if (A.u_prev) {
       if (!warm_residual(A, S, bb, rr0)) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
     } else {
@@ -702,11 +729,10 @@ __device__ void mixed_level(const LevelArgs& A, SmemAll& S, Conv& conv, Inner& i
   bool fallback = A.prev && !A.retry_mixed && __ldcg(&A.prev->outer) < 0;
   if (!fallback && relres <= A.tol) { write_stat(A.stat, TSFDE_OK, 0, 0, relres); return; }
   double* w = A.k64.v;  // FP64 scratch for M e
-  const float* e = A.k32.x;
   while (!fallback) {
     if (outer >= A.max_outer) { fallback = true; break; }
     SolveRes ir{TSFDE_OK, 0, 0.0};
-    if (!inner(1.0 / nr, ir)) { status = TSFDE_ETIMEOUT; break; }
+    if (!inner(1.0 / nr, A.tol * nb / nr, ir)) { status = TSFDE_ETIMEOUT; break; }
     inner_total += ir.iters;
     ++outer;
     // w = M (nr e) in FP64
@@ -761,7 +787,7 @@ __device__ void mixed_level(const LevelArgs& A, SmemAll& S, Conv& conv, Inner& i
     nr = sqrt(rr);
     if (!isfinite(nr) || !isfinite(xmax)) { status = TSFDE_ENONFINITE; break; }
     relres = nr / nb;
-    if (nr == 0.0 || emax <= A.tol * xmax) break;
+    if (nr == 0.0 || emax <= A.tol * xmax || relres <= A.tol) break;
     if (outer >= 2 && nr > 0.5 * nr_prev) {
       // the FP64 residual is at its rounding floor and u no longer moves at
       // the accuracy asked for

@@ -14,9 +14,9 @@
 
 namespace tsfde {
 
-// Shared memory: [tw64 T][tw32 T][bufA W][bufB W][red 64]
+// Shared memory: [tw64 T][tw32 T][twds T][bufA W][bufB W][red 64]
 size_t plan_smem_bytes(const DevPlan& P) {
-  return (size_t)P.T * sizeof(double2) + (size_t)P.T * sizeof(float2) +
+  return (size_t)P.T * (2 * sizeof(double2) + sizeof(float2)) +
          2 * (size_t)P.W * sizeof(double2) + 64 * sizeof(double);
 }
 
@@ -62,16 +62,43 @@ __global__ void __launch_bounds__(kThreads, 2) k_level_mixed(LevelArgs A) {
   const DevPlan& P = A.P;
   SmemAll S = smem_setup(P);
   auto conv = [&](int k) {
+    if (!A.precond) return;
     P.saG32[k] = (float)P.saG64[k];
     P.sbG32[k] = (float)P.sbG64[k];
   };
-  auto inner = [&](double sc, SolveRes& ir) -> bool {
+  auto inner = [&](double sc, double, SolveRes& ir) -> bool {
     auto binit = [&](int i) -> float { return (float)(A.r64[i] * sc); };
     ir = bicgstab<float>(P, S.f, A.k32, A.kappa32, A.ahat, A.precond != 0, A.inner_tol,
                          A.inner_max_it, binit);
     return ir.status != TSFDE_ETIMEOUT;
   };
-  mixed_level(A, S, conv, inner);
+  mixed_level(A, S, conv, inner, A.k32.x);
+}
+
+// Mixed level solve with the inner PBiCGSTAB in double-single arithmetic
+// (dsf.cuh): the same refinement loop, every inner vector, product and
+// scalar update carried as FP32 pairs.  kappa^m and the preconditioner
+// spectrum are rounded from FP64 once per level.  With ~48 bits the inner
+// solve resolves the operator, so each sweep asks for the whole remaining
+// reduction (half the target, at most max_it iterations, not below 1e-13)
+// instead of restarting every 1e-2: a level takes one sweep plus a short
+// second one.
+__global__ void __launch_bounds__(kThreads, 2) k_level_mixed_ds(LevelArgs A) {
+  const DevPlan& P = A.P;
+  SmemAll S = smem_setup(P);
+  auto conv = [&](int k) {
+    if (k < P.n) A.kappads[k] = dsf(A.kappa64[k]);
+    if (!A.precond) return;
+    P.saGds[k] = dsf(P.saG64[k]);
+    P.sbGds[k] = dsf(P.sbG64[k]);
+  };
+  auto inner = [&](double sc, double target, SolveRes& ir) -> bool {
+    auto binit = [&](int i) -> dsf { return dsf(A.r64[i] * sc); };
+    const double tin = fmax(0.5 * target, 1e-13);
+    ir = bicgstab<dsf>(P, S.s, A.kds, A.kappads, A.ahat, A.precond != 0, tin, A.max_it, binit);
+    return ir.status != TSFDE_ETIMEOUT;
+  };
+  mixed_level(A, S, conv, inner, A.kds.x);
 }
 
 // Adjoint level solve: (ahat I + A K) lambda = g in FP64 (transposed
@@ -139,11 +166,22 @@ __global__ void __launch_bounds__(kThreads) k_adj_rhs(AdjRhsArgs a) {
 
 // ------------------------------------------------------ single products
 template <typename R>
-__device__ void apply_kernel_body(const ApplyArgs& A, const Smem<R>& sm) {
+__device__ void apply_kernel_body(const ApplyArgs& A, const Smem<R>& sm, const Smem<double>& sd) {
   const DevPlan& P = A.P;
   const int n = P.n;
   if (A.kind == 1) {
-    if (!build_precond<R>(P, sm, A.a, A.kbar)) {
+    bool ok;
+    if constexpr (is_ds<R>) {
+      // built in FP64 and rounded, as in the double-single level solve
+      ok = build_precond<double>(P, sd, A.a, A.kbar);
+      for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P.Nc; k += gridDim.x * blockDim.x) {
+        P.saGds[k] = dsf(P.saG64[k]);
+        P.sbGds[k] = dsf(P.sbG64[k]);
+      }
+    } else {
+      ok = build_precond<R>(P, sm, A.a, A.kbar);
+    }
+    if (!ok) {
       if (blockIdx.x == 0 && threadIdx.x == 0) *A.status = TSFDE_ETIMEOUT;
       return;
     }
@@ -174,11 +212,15 @@ fail:
 
 __global__ void __launch_bounds__(kThreads, 2) k_apply64(ApplyArgs A) {
   SmemAll S = smem_setup(A.P);
-  apply_kernel_body<double>(A, S.d);
+  apply_kernel_body<double>(A, S.d, S.d);
 }
 __global__ void __launch_bounds__(kThreads, 2) k_apply32(ApplyArgs A) {
   SmemAll S = smem_setup(A.P);
-  apply_kernel_body<float>(A, S.f);
+  apply_kernel_body<float>(A, S.f, S.d);
+}
+__global__ void __launch_bounds__(kThreads, 2) k_apply_ds(ApplyArgs A) {
+  SmemAll S = smem_setup(A.P);
+  apply_kernel_body<dsf>(A, S.s, S.d);
 }
 
 // ------------------------------------------------- SOE history and RHS
@@ -286,8 +328,9 @@ static size_t g_smem_limit = 0;
 static cudaError_t set_attrs(size_t smem) {
   cudaError_t e = cudaSuccess;
   if (smem <= g_smem_limit) return e;
-  const void* ks[] = {(const void*)k_level64, (const void*)k_level_mixed, (const void*)k_apply64,
-                      (const void*)k_apply32, (const void*)k_level_adj};
+  const void* ks[] = {(const void*)k_level64, (const void*)k_level_mixed, (const void*)k_level_mixed_ds,
+                      (const void*)k_apply64, (const void*)k_apply32, (const void*)k_apply_ds,
+                      (const void*)k_level_adj};
   for (const void* k : ks) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -299,8 +342,9 @@ static cudaError_t set_attrs(size_t smem) {
 int coop_blocks_per_sm(size_t smem) {
   if (set_attrs(smem) != cudaSuccess) return 0;
   int best = 1 << 30;
-  const void* ks[] = {(const void*)k_level64, (const void*)k_level_mixed, (const void*)k_apply64,
-                      (const void*)k_apply32, (const void*)k_level_adj};
+  const void* ks[] = {(const void*)k_level64, (const void*)k_level_mixed, (const void*)k_level_mixed_ds,
+                      (const void*)k_apply64, (const void*)k_apply32, (const void*)k_apply_ds,
+                      (const void*)k_level_adj};
   for (const void* k : ks) {
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, smem) != cudaSuccess) return 0;
@@ -325,13 +369,15 @@ cudaError_t launch_convert(const double* in, double* o64, float* o32, int n, cud
   return cudaGetLastError();
 }
 
-cudaError_t launch_level(const LevelArgs& a, int mixed, cudaStream_t s) {
+cudaError_t launch_level(const LevelArgs& a, int precision, cudaStream_t s) {
   size_t smem = plan_smem_bytes(a.P);
   cudaError_t e = cudaMemsetAsync(a.P.bar, 0, sizeof(GridBarrier), s);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&a};
-  return cudaLaunchCooperativeKernel(mixed ? (const void*)k_level_mixed : (const void*)k_level64,
-                                     dim3(a.P.G), dim3(kThreads), args, smem, s);
+  const void* k = precision == TSFDE_MIXED_DS ? (const void*)k_level_mixed_ds
+                  : precision == TSFDE_MIXED  ? (const void*)k_level_mixed
+                                              : (const void*)k_level64;
+  return cudaLaunchCooperativeKernel(k, dim3(a.P.G), dim3(kThreads), args, smem, s);
 }
 
 cudaError_t launch_adj_rhs(const AdjRhsArgs& a, cudaStream_t s) {
@@ -350,13 +396,15 @@ cudaError_t launch_level_adj(const LevelArgs& a, const AdjGradArgs& g, cudaStrea
   return cudaLaunchCooperativeKernel((const void*)k_level_adj, dim3(a.P.G), dim3(kThreads), args, smem, s);
 }
 
-cudaError_t launch_apply(const ApplyArgs& a, int fp32, cudaStream_t s) {
+cudaError_t launch_apply(const ApplyArgs& a, int precision, cudaStream_t s) {
   size_t smem = plan_smem_bytes(a.P);
   cudaError_t e = cudaMemsetAsync(a.P.bar, 0, sizeof(GridBarrier), s);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&a};
-  return cudaLaunchCooperativeKernel(fp32 ? (const void*)k_apply32 : (const void*)k_apply64,
-                                     dim3(a.P.G), dim3(kThreads), args, smem, s);
+  const void* k = precision == TSFDE_MIXED_DS ? (const void*)k_apply_ds
+                  : precision == TSFDE_MIXED  ? (const void*)k_apply32
+                                              : (const void*)k_apply64;
+  return cudaLaunchCooperativeKernel(k, dim3(a.P.G), dim3(kThreads), args, smem, s);
 }
 
 }  // namespace tsfde

@@ -6,6 +6,20 @@
 
 namespace tsfde {
 
+// Double-single number: the unevaluated sum hi + lo of two FP32 values
+// (|lo| <= ulp(hi)/2), about 48 significant bits; device arithmetic in
+// dsf.cuh.  Conversions from FP64 round hi to nearest and keep the FP32
+// rounding of the remainder.
+struct __align__(8) dsf {
+  float hi, lo;
+  dsf() = default;
+  __host__ __device__ constexpr dsf(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ constexpr dsf(int i) : hi((float)i), lo(0.0f) {}  // |i| < 2^24: exact
+  __host__ __device__ explicit dsf(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+struct __align__(16) dsf2 { dsf x, y; };
+
 // Bounded grid barrier state (cleared by the host before each cooperative
 // launch); see grid_sync_red in dev.cuh.  The arrival counter and the
 // release word sit on separate 128-byte lines so that polling does not
@@ -101,7 +115,13 @@ struct DevPlan {
   double* saG64; double* sbG64;
   float* saG32;  float* sbG32;
   double* g64; float* g32;  // first column of the circulant inverse (n)
-  double2* S1;  // work: Nfft complex (double capacity, reused as float2)
+  // double-single copies (mixed solves with the double-single inner solver;
+  // NULL otherwise): twiddles, Toeplitz spectrum, per-level preconditioner
+  // spectrum (rounded from the FP64 build)
+  const dsf2* twLds;
+  const dsf* saTds; const dsf* sbTds;
+  dsf* saGds; dsf* sbGds;
+  double2* S1;  // work: Nfft complex (double capacity, reused as float2 / dsf2)
   double2* S2;
   CGeo cl;
   // (sa, sb) pairs in the cluster engine's row-pass order: entry
@@ -140,6 +160,8 @@ struct LevelArgs {
   int inner_max_it;
   KVecs<double> k64;
   KVecs<float> k32;
+  KVecs<dsf> kds;     // double-single inner solver (TSFDE_MIXED_DS)
+  dsf* kappads;       // kappa^m rounded to double-single (written by the level kernel)
   double* r64;        // mixed: FP64 residual
   StepStat* stat;
   int probe;          // cluster engine: return at once (launch check)
@@ -257,7 +279,8 @@ struct ApplyArgs {
 
 // launchers (kernels.cu)
 cudaError_t launch_rhs(const RhsArgs& a, cudaStream_t s);
-cudaError_t launch_level(const LevelArgs& a, int mixed, cudaStream_t s);
+// precision: TSFDE_FP64, TSFDE_MIXED (FP32 inner) or TSFDE_MIXED_DS
+cudaError_t launch_level(const LevelArgs& a, int precision, cudaStream_t s);
 // cluster engine (cluster.cu): mixed level solve with the FP32 inner solves
 // on one thread-block cluster; a.P.G must equal a.P.cl.G.
 cudaError_t launch_level_cluster(const LevelArgs& a, cudaStream_t s);
@@ -267,7 +290,9 @@ size_t cluster_smem_bytes(const DevPlan& P);
 // Largest cluster-engine grid (CTAs) that can be co-resident with `smem`
 // dynamic shared bytes per CTA, 0 if the engine cannot be launched.
 int cluster_max_grid(const DevPlan& P, size_t smem);
-cudaError_t launch_apply(const ApplyArgs& a, int fp32, cudaStream_t s);
+// precision: TSFDE_FP64, TSFDE_MIXED (FP32 product) or TSFDE_MIXED_DS
+// (double-single product; a preconditioner is built in FP64 and rounded)
+cudaError_t launch_apply(const ApplyArgs& a, int precision, cudaStream_t s);
 // batched engine (batch.cu): one persistent launch of clusters of Q CTAs,
 // each marching whole instances through all M levels
 size_t batch_smem_bytes(const CeLay& lay);
