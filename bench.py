@@ -2,7 +2,8 @@
 """Benchmark of the FIDS hot path on the headline workload:
 n = 2^17 - 1 interior points, M = 4096 graded levels, gamma = 0.4 (r = 4),
 alpha = 1.6, kappa = exp(GRF) mapped onto [0.2, 5], mixed precision
-(FP32 inner PBiCGSTAB inside FP64 refinement) vs the plain FP64 path.
+(double-single inner PBiCGSTAB inside FP64 refinement; --inner fp32 for the
+FP32 inner solver) vs the plain FP64 path.
 
 One step = one time level of the scheme: SOE history update and
 right-hand side, Strang preconditioner for the level, Krylov solve (from
@@ -55,7 +56,9 @@ def parse():
                     help="x0 = 0 for every level as in the paper's experiments (default: start "
                          "from u^{m-1}, same stopping rule ||r|| < tol ||b||)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
-    ap.add_argument("--inner", choices=["fp32", "ds"], default="fp32",
+    ap.add_argument("--flush-mb", type=int, default=256,
+                    help="L2 flush buffer size (MB, twice L2 by default); smaller only for profiler runs")
+    ap.add_argument("--inner", choices=["fp32", "ds"], default="ds",
                     help="arithmetic of the mixed arm's inner PBiCGSTAB: FP32, or double-single "
                          "(FP32 pairs, ~48-bit significand)")
     ap.add_argument("--paper-table11", action="store_true",
@@ -407,8 +410,9 @@ def ours(args):
     W = args.warmup
     K = args.steps if args.steps is not None else max(1, prob.M - W)
     stream = torch.cuda.Stream()
-    flush = (torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device="cuda"),
-             torch.zeros(256 * 1024 * 1024 // 8, dtype=torch.float64, device="cuda"))
+    fl = max(1, args.flush_mb) * 1024 * 1024 // 8
+    flush = (torch.empty(fl, dtype=torch.float64, device="cuda"),
+             torch.zeros(fl, dtype=torch.float64, device="cuda"))
     n = prob.n
 
     def barrier():
@@ -496,7 +500,7 @@ def ours(args):
                                      "mixed: FP32 inner PBiCGSTAB") + ", FP64 refinement/residual/SOE",
                        "krylov_tol": 1e-12, "inner_tol": 1e-2,
                        "initial_guess": "u^{m-1}" if (not args.cold_start) else "0 (Sec. 5)",
-                       "l2": "flushed before every timed level (256 MB write, then 256 MB read, outside the events)",
+                       "l2": f"flushed before every timed level ({args.flush_mb} MB write, then {args.flush_mb} MB read, outside the events)",
                        "parallelism": f"replicas x{world}"},
             "status": st_mx["status"],
             "iterations_per_step": st_mx["its"] / K, "outer_per_step": st_mx["outer"] / K, "fp64_fallback_levels": st_mx.get("fallback", 0),

@@ -15,9 +15,10 @@
 // Multiplication adds the two cross terms to the exact error of hi * hi,
 // error a few u^2 |a b|.
 //
-// Every operation here is a handful of FP32 adds and FMAs (add 11, multiply
-// 6): on GB300 that runs ~8x faster than the same operation in FP64, whose
-// pipe is 1/58 of the FP32 rate.
+// Every operation is a handful of FP32 adds and FMAs (add 11, multiply 6,
+// dot2 19).  GB300 issues FP32 at 58x its FP64 rate (72.6 against 1.25
+// TFLOP/s measured), so a double-single operation costs several times less
+// pipe time than the FP64 one it replaces.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -62,6 +63,41 @@ __device__ __forceinline__ dsf operator*(dsf a, dsf b) {
 __device__ __forceinline__ dsf& operator+=(dsf& a, dsf b) { a = a + b; return a; }
 __device__ __forceinline__ dsf& operator-=(dsf& a, dsf b) { a = a - b; return a; }
 __device__ __forceinline__ dsf& operator*=(dsf& a, dsf b) { a = a * b; return a; }
+
+// a1 b1 + a2 b2 with one renormalisation: both high products exactly
+// (two_prod), their sum exactly (two_sum), the product errors and cross
+// terms accumulated in FP32.  19 operations against 23 for two products and
+// a sum; error a few u^2 (|a1 b1| + |a2 b2|).
+__device__ __forceinline__ dsf dot2(dsf a1, dsf b1, dsf a2, dsf b2) {
+  const float p1 = __fmul_rn(a1.hi, b1.hi);
+  const float e1 = __fmaf_rn(a1.hi, b1.hi, -p1);
+  const float p2 = __fmul_rn(a2.hi, b2.hi);
+  const float e2 = __fmaf_rn(a2.hi, b2.hi, -p2);
+  float s, e;
+  two_sum(p1, p2, s, e);
+  e = __fadd_rn(e, __fadd_rn(e1, e2));
+  e = __fmaf_rn(a1.hi, b1.lo, e);
+  e = __fmaf_rn(a1.lo, b1.hi, e);
+  e = __fmaf_rn(a2.hi, b2.lo, e);
+  e = __fmaf_rn(a2.lo, b2.hi, e);
+  dsf r;
+  fast_two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+
+// Complex products (overloads of the generic ones in dev.cuh): a b and a conj(b).
+__device__ __forceinline__ dsf2 cmul(dsf2 a, dsf2 b) {
+  dsf2 c;
+  c.x = dot2(a.x, b.x, -a.y, b.y);
+  c.y = dot2(a.x, b.y, a.y, b.x);
+  return c;
+}
+__device__ __forceinline__ dsf2 cmulc(dsf2 a, dsf2 b) {
+  dsf2 c;
+  c.x = dot2(a.x, b.x, a.y, b.y);
+  c.y = dot2(a.y, b.x, -a.x, b.y);
+  return c;
+}
 
 // Cache-global loads (L2 only): the work buffers are rewritten by other CTAs
 // between grid barriers.

@@ -152,16 +152,19 @@ __device__ __forceinline__ bool gsync_sum3(const DevPlan& P, double* red, int s0
 }
 
 // ------------------------------------------------------------------ passes
-// Each thread handles at most kPre elements of a work item (tile or row
+// Each thread handles at most KP elements of a work item (tile or row
 // pair); their store twiddles and spectral coefficients are loaded into
 // registers before the shared-memory FFT so the L2 latency overlaps it.
-constexpr int kPre = 4;  // with 256 threads: work items of <= 1024 elements (n <= 2^18)
+// kPre = 4 covers every size (with 256 threads: work items of <= 1024
+// elements, n <= 2^18); solvers whose items are <= 512 elements can be
+// instantiated with KP = 2, which frees registers.
+constexpr int kPre = 4;
 
 // Pass A, real input: x (length nin, zero beyond) -> z_j = x_{2j} + i x_{2j+1},
 // column FFTs over j1 (j = N2 j1 + j2), twiddle W_Nc^{j2 k1}, store
 // S1[k1*N2 + j2].  Without FULL only rows j1 < N1/2 can be non-zero
 // (nin <= L/2).
-template <typename R, bool FULL, class Pro>
+template <typename R, bool FULL, int KP = kPre, class Pro>
 __device__ void passA_real(const DevPlan& P, const Smem<R>& sm, int nin, Pro& pro) {
   typedef cplx<R> Z;
   const Geo& g = P.gr;
@@ -175,9 +178,9 @@ __device__ void passA_real(const DevPlan& P, const Smem<R>& sm, int nin, Pro& pr
   const Z* tw = twL<R>(P);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int c0 = tile << lc;
-    Z wp[kPre];
+    Z wp[KP];
 #pragma unroll
-    for (int q = 0; q < kPre; ++q) {
+    for (int q = 0; q < KP; ++q) {
       const int e = threadIdx.x + q * blockDim.x;
       if (e < total) {
         const int k1 = e >> lc, j2 = c0 + (e & (ct - 1));
@@ -198,7 +201,7 @@ __device__ void passA_real(const DevPlan& P, const Smem<R>& sm, int nin, Pro& pr
     __syncthreads();
     const Z* res = fft_batch<R, false>(sm.bA, sm.bB, N1, lc, sm.tw, P.T);
 #pragma unroll
-    for (int q = 0; q < kPre; ++q) {
+    for (int q = 0; q < KP; ++q) {
       const int e = threadIdx.x + q * blockDim.x;
       if (e < total) S1[(e >> lc) * N2 + c0 + (e & (ct - 1))] = cmul(res[e], wp[q]);
     }
@@ -262,7 +265,7 @@ enum { MID_APPLY = 0, MID_SPEC = 1, MID_CONV = 2 };
 //  MID_SPEC: forward only; stores sa = Re X_k / Nc, sb = Re conj X_k' / Nc
 //    (the spectrum of an even real sequence is real).
 //  MID_CONV: complex product Z'_k = Z_k * conv_k (geometry gc).
-template <typename R, int MID>
+template <typename R, int MID, int KP = kPre>
 __device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__ sa,
                       const R* __restrict__ sb, R* sa_out, R* sb_out,
                       const cplx<R>* __restrict__ conv) {
@@ -282,10 +285,10 @@ __device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__
     const int B = 1 << lgB;
     const int total = N2 << lgB;
     // per-element coefficients and store twiddles, fetched early
-    Z wp[kPre], cf[kPre];
-    R s1[kPre], s2[kPre];
+    Z wp[KP], cf[KP];
+    R s1[KP], s2[KP];
 #pragma unroll
-    for (int q = 0; q < kPre; ++q) {
+    for (int q = 0; q < KP; ++q) {
       const int e = threadIdx.x + q * blockDim.x;
       if (e < total) {
         const int b = e & (B - 1), k2 = e >> lgB;
@@ -311,7 +314,7 @@ __device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__
     Z* res = fft_batch<R, false>(sm.bA, sm.bB, N2, lgB, sm.tw, P.T);
     Z* oth = (res == sm.bA) ? sm.bB : sm.bA;
 #pragma unroll
-    for (int q = 0; q < kPre; ++q) {
+    for (int q = 0; q < KP; ++q) {
       const int e = threadIdx.x + q * blockDim.x;
       if (e >= total) continue;
       const int b = e & (B - 1), k2 = e >> lgB;
@@ -345,7 +348,7 @@ __device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__
     if constexpr (MID == MID_SPEC) continue;
     const Z* res2 = fft_batch<R, true>(oth, res, N2, lgB, sm.tw, P.T);
 #pragma unroll
-    for (int q = 0; q < kPre; ++q) {
+    for (int q = 0; q < KP; ++q) {
       const int e = threadIdx.x + q * blockDim.x;
       if (e < total) {
         const int b = e & (B - 1), j2 = e >> lgB;
@@ -360,7 +363,7 @@ __device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__
 // Pass C (+ optional fused pass A): inverse column FFTs, y_{2j} = Re z_j,
 // y_{2j+1} = Im z_j for j1 < N1/2.  epi(i, y_i) consumes each output and
 // returns the next product's input x_i (used only with DO_A).
-template <typename R, bool DO_A, class Epi>
+template <typename R, bool DO_A, int KP = kPre, class Epi>
 __device__ void passCA_real(const DevPlan& P, const Smem<R>& sm, Epi& epi) {
   typedef cplx<R> Z;
   const Geo& g = P.gr;
@@ -374,10 +377,10 @@ __device__ void passCA_real(const DevPlan& P, const Smem<R>& sm, Epi& epi) {
   const Z* tw = twL<R>(P);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int c0 = tile << lc;
-    Z wp[kPre];
+    Z wp[KP];
     if constexpr (DO_A) {
 #pragma unroll
-      for (int q = 0; q < kPre; ++q) {
+      for (int q = 0; q < KP; ++q) {
         const int e = threadIdx.x + q * blockDim.x;
         if (e < total) {
           const int k1 = e >> lc, j2 = c0 + (e & (ct - 1));
@@ -409,7 +412,7 @@ __device__ void passCA_real(const DevPlan& P, const Smem<R>& sm, Epi& epi) {
     if constexpr (DO_A) {
       const Z* res2 = fft_batch<R, false>(oth, res, N1, lc, sm.tw, P.T);
 #pragma unroll
-      for (int q = 0; q < kPre; ++q) {
+      for (int q = 0; q < KP; ++q) {
         const int e = threadIdx.x + q * blockDim.x;
         if (e < total) S1[(e >> lc) * N2 + c0 + (e & (ct - 1))] = cmul(res2[e], wp[q]);
       }
@@ -487,7 +490,7 @@ __device__ bool build_precond(const DevPlan& P, const Smem<R>& sm, double ahat, 
 // Per iteration: P^{-1}p, A p^, P^{-1}s, A s^ as zero-padded FFT products.
 // TR selects the transposed operator ahat I + A K (the adjoint level solve):
 // kappa then scales the input of the Toeplitz product instead of its output.
-template <typename R, class BInit, bool TR = false>
+template <typename R, class BInit, bool TR = false, int KP = kPre>
 __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>& V,
                              const R* __restrict__ kap, double ahat, bool prec, double tol,
                              int max_it, BInit& binit) {
@@ -531,17 +534,17 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
         V.p[i] = pi;
         return (TR && !prec) ? kap[i] * pi : pi;
       };
-      passA_real<R, false>(P, sm, n, pro);
+      passA_real<R, false, KP>(P, sm, n, pro);
     }
     if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
     if (prec) {
-      passB<R, MID_APPLY>(P, sm, saG<R>(P), sbG<R>(P), nullptr, nullptr, nullptr);
+      passB<R, MID_APPLY, KP>(P, sm, saG<R>(P), sbG<R>(P), nullptr, nullptr, nullptr);
       if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
       auto epi = [&](int i, R y) -> R { V.ph[i] = y; return TR ? kap[i] * y : y; };
-      passCA_real<R, true>(P, sm, epi);
+      passCA_real<R, true, KP>(P, sm, epi);
       if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
     }
-    passB<R, MID_APPLY>(P, sm, saT<R>(P), sbT<R>(P), nullptr, nullptr, nullptr);
+    passB<R, MID_APPLY, KP>(P, sm, saT<R>(P), sbT<R>(P), nullptr, nullptr, nullptr);
     if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
     const R* ph = prec ? V.ph : V.p;
     {
@@ -552,7 +555,7 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
         acc += V.rh[i] * vi;
         return R(0);
       };
-      passCA_real<R, false>(P, sm, epi);
+      passCA_real<R, false, KP>(P, sm, epi);
       put_partial(P, SL_RV, block_sum((double)acc, sm.red));
     }
     double rv;
@@ -568,17 +571,17 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
         V.s[i] = si;
         return (TR && !prec) ? kap[i] * si : si;
       };
-      passA_real<R, false>(P, sm, n, pro);
+      passA_real<R, false, KP>(P, sm, n, pro);
     }
     if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
     if (prec) {
-      passB<R, MID_APPLY>(P, sm, saG<R>(P), sbG<R>(P), nullptr, nullptr, nullptr);
+      passB<R, MID_APPLY, KP>(P, sm, saG<R>(P), sbG<R>(P), nullptr, nullptr, nullptr);
       if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
       auto epi = [&](int i, R y) -> R { V.sh[i] = y; return TR ? kap[i] * y : y; };
-      passCA_real<R, true>(P, sm, epi);
+      passCA_real<R, true, KP>(P, sm, epi);
       if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
     }
-    passB<R, MID_APPLY>(P, sm, saT<R>(P), sbT<R>(P), nullptr, nullptr, nullptr);
+    passB<R, MID_APPLY, KP>(P, sm, saT<R>(P), sbT<R>(P), nullptr, nullptr, nullptr);
     if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
     const R* sh = prec ? V.sh : V.s;
     {
@@ -590,7 +593,7 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
         att += ti * ti;
         return R(0);
       };
-      passCA_real<R, false>(P, sm, epi);
+      passCA_real<R, false, KP>(P, sm, epi);
       put_partial(P, SL_TS, block_sum((double)ats, sm.red));
       put_partial(P, SL_TT, block_sum((double)att, sm.red));
     }

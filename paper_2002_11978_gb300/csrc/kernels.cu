@@ -82,9 +82,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_level_mixed(LevelArgs A) {
 // solve resolves the operator, so each sweep asks for the whole remaining
 // reduction (half the target, at most max_it iterations, not below 1e-13)
 // instead of restarting every 1e-2: a level takes one sweep plus a short
-// second one.
+// second one.  KP: elements per thread of the inner passes' work items
+// (2 when the real-geometry items have <= 512 elements, else 4).
+template <int KP>
 __global__ void __launch_bounds__(kThreads, 2) k_level_mixed_ds(LevelArgs A) {
   const DevPlan& P = A.P;
+  if ((P.gr.N1 << P.gr.lgct64) > KP * kThreads || 2 * P.gr.N2 > KP * kThreads) {
+    write_stat(A.stat, TSFDE_EINVAL, 0, 0, 0.0);  // launched with the wrong KP
+    return;
+  }
   SmemAll S = smem_setup(P);
   auto conv = [&](int k) {
     if (k < P.n) A.kappads[k] = dsf(A.kappa64[k]);
@@ -95,7 +101,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_level_mixed_ds(LevelArgs A) {
   auto inner = [&](double sc, double target, SolveRes& ir) -> bool {
     auto binit = [&](int i) -> dsf { return dsf(A.r64[i] * sc); };
     const double tin = fmax(0.5 * target, 1e-13);
-    ir = bicgstab<dsf>(P, S.s, A.kds, A.kappads, A.ahat, A.precond != 0, tin, A.max_it, binit);
+    ir = bicgstab<dsf, decltype(binit), false, KP>(P, S.s, A.kds, A.kappads, A.ahat, A.precond != 0,
+                                                   tin, A.max_it, binit);
     return ir.status != TSFDE_ETIMEOUT;
   };
   mixed_level(A, S, conv, inner, A.kds.x);
@@ -328,7 +335,8 @@ static size_t g_smem_limit = 0;
 static cudaError_t set_attrs(size_t smem) {
   cudaError_t e = cudaSuccess;
   if (smem <= g_smem_limit) return e;
-  const void* ks[] = {(const void*)k_level64, (const void*)k_level_mixed, (const void*)k_level_mixed_ds,
+  const void* ks[] = {(const void*)k_level64, (const void*)k_level_mixed, (const void*)k_level_mixed_ds<2>,
+                      (const void*)k_level_mixed_ds<4>,
                       (const void*)k_apply64, (const void*)k_apply32, (const void*)k_apply_ds,
                       (const void*)k_level_adj};
   for (const void* k : ks) {
@@ -342,7 +350,8 @@ static cudaError_t set_attrs(size_t smem) {
 int coop_blocks_per_sm(size_t smem) {
   if (set_attrs(smem) != cudaSuccess) return 0;
   int best = 1 << 30;
-  const void* ks[] = {(const void*)k_level64, (const void*)k_level_mixed, (const void*)k_level_mixed_ds,
+  const void* ks[] = {(const void*)k_level64, (const void*)k_level_mixed, (const void*)k_level_mixed_ds<2>,
+                      (const void*)k_level_mixed_ds<4>,
                       (const void*)k_apply64, (const void*)k_apply32, (const void*)k_apply_ds,
                       (const void*)k_level_adj};
   for (const void* k : ks) {
@@ -374,7 +383,9 @@ cudaError_t launch_level(const LevelArgs& a, int precision, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(a.P.bar, 0, sizeof(GridBarrier), s);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&a};
-  const void* k = precision == TSFDE_MIXED_DS ? (const void*)k_level_mixed_ds
+  const bool kp2 = (a.P.gr.N1 << a.P.gr.lgct64) <= 2 * kThreads && 2 * a.P.gr.N2 <= 2 * kThreads;
+  const void* k = precision == TSFDE_MIXED_DS ? (kp2 ? (const void*)k_level_mixed_ds<2>
+                                                     : (const void*)k_level_mixed_ds<4>)
                   : precision == TSFDE_MIXED  ? (const void*)k_level_mixed
                                               : (const void*)k_level64;
   return cudaLaunchCooperativeKernel(k, dim3(a.P.G), dim3(kThreads), args, smem, s);
