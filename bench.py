@@ -181,7 +181,8 @@ def run_arm(torch, pkg, prob, precision, W, K, flush, stream, e2e=False, warm=Fa
     s.set_problem_from(prob)
     n = prob.n
     dev = torch.device("cuda")
-    tot = {"its": 0, "outer": 0, "E_active_sum": 0, "status": 0, "fallback": 0}
+    tot = {"its": 0, "outer": 0, "E_active_sum": 0, "status": 0, "fallback": 0, "max_relres": 0.0,
+           "above_tol": 0}
     if e2e:
         kap_h = torch.from_numpy(prob.kappa0.copy()).pin_memory()
         f_h = torch.from_numpy(prob.f_at(0.0)).pin_memory()
@@ -199,6 +200,8 @@ def run_arm(torch, pkg, prob, precision, W, K, flush, stream, e2e=False, warm=Fa
                 tot["fallback"] += rec["outer"] < 0
                 tot["E_active_sum"] += rec["E_active"]
                 tot["status"] = tot["status"] or rec["status"]
+                tot["max_relres"] = max(tot["max_relres"], rec["rel_residual"])
+                tot["above_tol"] += rec["rel_residual"] > 1e-12
 
     def one_level(timed):
         if s.m == prob.M:
@@ -440,6 +443,7 @@ def ours(args):
         rel = float(torch.max(torch.abs(u_mx - u64)) / torch.max(torch.abs(u64)))
         t64 = sum(ms64) / 1e3
         fp64 = {"steps_per_s": K / t64, "ms_per_step": 1e3 * t64 / K,
+                "max_final_rel_residual_recursive": st64["max_relres"],
                 "iterations_per_step": st64["its"] / K, "krylov_its_per_s": st64["its"] / t64,
                 "kernel_ms": {"k_rhs": tim64["rhs_ms"] / K, "k_level64": tim64["level_ms"] / K},
                 "status": st64["status"],
@@ -504,6 +508,7 @@ def ours(args):
                        "parallelism": f"replicas x{world}"},
             "status": st_mx["status"],
             "iterations_per_step": st_mx["its"] / K, "outer_per_step": st_mx["outer"] / K, "fp64_fallback_levels": st_mx.get("fallback", 0),
+            "max_final_rel_residual": st_mx["max_relres"], "levels_above_tol": st_mx["above_tol"],
             "krylov_its_per_s": world * st_mx["its"] / t_mx,
             "kernels": {"k_rhs": {"ms": rhs_ms, "bytes": rhs_bytes, "GB/s": rhs_gbs, "frac": rhs_gbs / peak},
                         kname: {"ms": lvl_ms, "bytes": lvl_bytes, "GB/s": lvl_gbs,

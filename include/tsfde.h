@@ -87,9 +87,11 @@ typedef struct tsfde_opts {
   int precond;          /* TSFDE_STRANG (default) or TSFDE_PRECOND_NONE     */
   double inner_tol;     /* MIXED: FP32 inner relative tolerance (default
                            1e-2).  MIXED_DS ignores it and inner_max_it:
-                           each of its inner solves asks for the
-                           whole remaining reduction, tol ||b|| / ||r|| / 2
-                           (not below 1e-13), within max_it iterations      */
+                           its first inner solve of a level stops at
+                           100 tol ||b|| (near the double-single residual
+                           floor), every later one asks for the whole
+                           remaining reduction (to tol ||b|| / 2), each
+                           within max_it iterations                         */
   int max_outer;        /* mixed: FP64 refinement cap (default 60)          */
   int inner_max_it;     /* MIXED: inner BiCGSTAB iterations per refinement
                            sweep (default 40).  The inner solve stops there

@@ -151,6 +151,13 @@ __device__ __forceinline__ bool gsync_sum3(const DevPlan& P, double* red, int s0
   return ok;
 }
 
+// True when the real-geometry work items (column tiles, row pairs) have at
+// most KP * kThreads elements, so that solvers instantiated with that
+// prefetch depth cover them.
+__host__ __device__ inline bool kp_fits(const DevPlan& P, int KP) {
+  return (P.gr.N1 << P.gr.lgct64) <= KP * kThreads && 2 * P.gr.N2 <= KP * kThreads;
+}
+
 // ------------------------------------------------------------------ passes
 // Each thread handles at most KP elements of a work item (tile or row
 // pair); their store twiddles and spectral coefficients are loaded into

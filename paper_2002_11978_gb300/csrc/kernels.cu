@@ -1,7 +1,9 @@
-// kernels.cu -- grid-engine kernels of the FIDS hot path (sm_103a): the
-// level solves (FP64 and mixed), single products, the SOE history / RHS
-// update, and their launchers.  The device code they share with the cluster
-// engine is in grid.cuh.
+// kernels.cu -- grid-engine kernels of the FIDS hot path (sm_103a): single
+// products, the SOE history / RHS update (forward and adjoint), and the
+// launchers of every grid kernel.  The level kernels live in level64.cu,
+// level32.cu and levelds.cu (one translation unit each, compiled in
+// parallel); the device code they share with the cluster engine is in
+// grid.cuh.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -21,127 +23,12 @@ size_t plan_smem_bytes(const DevPlan& P) {
 }
 
 
-// ---------------------------------------------------------- level kernels
-// FP64 level solve: preconditioner build and PBiCGSTAB, all in FP64.
-__global__ void __launch_bounds__(kThreads, 2) k_level64(LevelArgs A) {
-  const DevPlan& P = A.P;
-  SmemAll S = smem_setup(P);
-  const double kbar = mean_kappa(P, A.kappa64, S.d.red);
-  if (kbar < 0.0) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
-  if (A.precond && !build_precond<double>(P, S.d, A.ahat, kbar)) {
-    write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0);
-    return;
-  }
-  if (!A.u_prev) {
-    KVecs<double> V = A.k64;
-    V.x = A.u;
-    auto binit = [&](int i) -> double { return A.b[i]; };
-    SolveRes r = bicgstab<double>(P, S.d, V, A.kappa64, A.ahat, A.precond != 0, A.tol, A.max_it, binit);
-    write_stat(A.stat, r.status, r.iters, 0, r.relres);
-    return;
-  }
-  // warm start: solve M d = b - M u_prev to ||r|| < tol ||b||, u = u_prev + d
-  double bb, rr;
-  if (!warm_residual(A, S, bb, rr)) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
-  if (!isfinite(bb) || !isfinite(rr)) { write_stat(A.stat, TSFDE_ENONFINITE, 0, 0, 0.0); return; }
-  if (bb == 0.0 || rr == 0.0) { write_stat(A.stat, TSFDE_OK, 0, 0, 0.0); return; }
-  const double scale = sqrt(rr / bb);
-  KVecs<double> V = A.k64;  // V.x: the correction d
-  auto binit = [&](int i) -> double { return A.r64[i]; };
-  SolveRes r = bicgstab<double>(P, S.d, V, A.kappa64, A.ahat, A.precond != 0, A.tol / scale, A.max_it, binit);
-  if (r.status == TSFDE_OK) {
-    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    for (int i = gtid; i < P.n; i += gridDim.x * blockDim.x) A.u[i] += V.x[i];
-  }
-  write_stat(A.stat, r.status, r.iters, 0, r.relres * scale);
-}
+// Level kernels: level64.cu (FP64, adjoint), level32.cu (FP32 inner),
+// levelds.cu (double-single inner).
 
-// Mixed level solve on the grid engine: the refinement loop of mixed_level
-// (grid.cuh) with the FP32 PBiCGSTAB spread over the whole cooperative grid.
-__global__ void __launch_bounds__(kThreads, 2) k_level_mixed(LevelArgs A) {
-  const DevPlan& P = A.P;
-  SmemAll S = smem_setup(P);
-  auto conv = [&](int k) {
-    if (!A.precond) return;
-    P.saG32[k] = (float)P.saG64[k];
-    P.sbG32[k] = (float)P.sbG64[k];
-  };
-  auto inner = [&](double sc, double, SolveRes& ir) -> bool {
-    auto binit = [&](int i) -> float { return (float)(A.r64[i] * sc); };
-    ir = bicgstab<float>(P, S.f, A.k32, A.kappa32, A.ahat, A.precond != 0, A.inner_tol,
-                         A.inner_max_it, binit);
-    return ir.status != TSFDE_ETIMEOUT;
-  };
-  mixed_level(A, S, conv, inner, A.k32.x);
-}
 
-// Mixed level solve with the inner PBiCGSTAB in double-single arithmetic
-// (dsf.cuh): the same refinement loop, every inner vector, product and
-// scalar update carried as FP32 pairs.  kappa^m and the preconditioner
-// spectrum are rounded from FP64 once per level.  With ~48 bits the inner
-// solve resolves the operator, so each sweep asks for the whole remaining
-// reduction (half the target, at most max_it iterations, not below 1e-13)
-// instead of restarting every 1e-2: a level takes one sweep plus a short
-// second one.  KP: elements per thread of the inner passes' work items
-// (2 when the real-geometry items have <= 512 elements, else 4).
-template <int KP>
-__global__ void __launch_bounds__(kThreads, 2) k_level_mixed_ds(LevelArgs A) {
-  const DevPlan& P = A.P;
-  if ((P.gr.N1 << P.gr.lgct64) > KP * kThreads || 2 * P.gr.N2 > KP * kThreads) {
-    write_stat(A.stat, TSFDE_EINVAL, 0, 0, 0.0);  // launched with the wrong KP
-    return;
-  }
-  SmemAll S = smem_setup(P);
-  auto conv = [&](int k) {
-    if (k < P.n) A.kappads[k] = dsf(A.kappa64[k]);
-    if (!A.precond) return;
-    P.saGds[k] = dsf(P.saG64[k]);
-    P.sbGds[k] = dsf(P.sbG64[k]);
-  };
-  auto inner = [&](double sc, double target, SolveRes& ir) -> bool {
-    auto binit = [&](int i) -> dsf { return dsf(A.r64[i] * sc); };
-    const double tin = fmax(0.5 * target, 1e-13);
-    ir = bicgstab<dsf, decltype(binit), false, KP>(P, S.s, A.kds, A.kappads, A.ahat, A.precond != 0,
-                                                   tin, A.max_it, binit);
-    return ir.status != TSFDE_ETIMEOUT;
-  };
-  mixed_level(A, S, conv, inner, A.kds.x);
-}
 
-// Adjoint level solve: (ahat I + A K) lambda = g in FP64 (transposed
-// operator; the Strang preconditioner is symmetric, so the same P serves),
-// then y = A u^m with grad_kappa -= lambda .* y and grad_f += lambda in the
-// product's epilogue.
-__global__ void __launch_bounds__(kThreads, 2) k_level_adj(LevelArgs A, AdjGradArgs Gd) {
-  const DevPlan& P = A.P;
-  SmemAll S = smem_setup(P);
-  const double kbar = mean_kappa(P, A.kappa64, S.d.red);
-  if (kbar < 0.0) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
-  if (A.precond && !build_precond<double>(P, S.d, A.ahat, kbar)) {
-    write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0);
-    return;
-  }
-  KVecs<double> V = A.k64;
-  V.x = A.u;
-  auto binit = [&](int i) -> double { return A.b[i]; };
-  SolveRes r = bicgstab<double, decltype(binit), true>(P, S.d, V, A.kappa64, A.ahat, A.precond != 0,
-                                                       A.tol, A.max_it, binit);
-  if (r.status == TSFDE_OK) {
-    auto pro = [&](int i) -> double { return Gd.um[i]; };
-    passA_real<double, false>(P, S.d, P.n, pro);
-    if (!gsync(P, S.d.red)) { write_stat(A.stat, TSFDE_ETIMEOUT, r.iters, 0, r.relres); return; }
-    passB<double, MID_APPLY>(P, S.d, P.saT64, P.sbT64, nullptr, nullptr, nullptr);
-    if (!gsync(P, S.d.red)) { write_stat(A.stat, TSFDE_ETIMEOUT, r.iters, 0, r.relres); return; }
-    auto epi = [&](int i, double y) -> double {
-      const double li = A.u[i];
-      Gd.grad_kappa[i] -= li * y;
-      Gd.grad_f[i] += li;
-      return 0.0;
-    };
-    passCA_real<double, false>(P, S.d, epi);
-  }
-  write_stat(A.stat, r.status, r.iters, 0, r.relres);
-}
+
 
 // Reversed SOE recurrence and adjoint right-hand side (see AdjRhsArgs).
 __global__ void __launch_bounds__(kThreads) k_adj_rhs(AdjRhsArgs a) {
@@ -335,10 +222,9 @@ static size_t g_smem_limit = 0;
 static cudaError_t set_attrs(size_t smem) {
   cudaError_t e = cudaSuccess;
   if (smem <= g_smem_limit) return e;
-  const void* ks[] = {(const void*)k_level64, (const void*)k_level_mixed, (const void*)k_level_mixed_ds<2>,
-                      (const void*)k_level_mixed_ds<4>,
-                      (const void*)k_apply64, (const void*)k_apply32, (const void*)k_apply_ds,
-                      (const void*)k_level_adj};
+  const void* ks[] = {level64_kernel(2), level64_kernel(4), level32_kernel(2), level32_kernel(4),
+                      levelds_kernel(2), levelds_kernel(4), (const void*)k_apply64,
+                      (const void*)k_apply32, (const void*)k_apply_ds, level_adj_kernel()};
   for (const void* k : ks) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -350,10 +236,9 @@ static cudaError_t set_attrs(size_t smem) {
 int coop_blocks_per_sm(size_t smem) {
   if (set_attrs(smem) != cudaSuccess) return 0;
   int best = 1 << 30;
-  const void* ks[] = {(const void*)k_level64, (const void*)k_level_mixed, (const void*)k_level_mixed_ds<2>,
-                      (const void*)k_level_mixed_ds<4>,
-                      (const void*)k_apply64, (const void*)k_apply32, (const void*)k_apply_ds,
-                      (const void*)k_level_adj};
+  const void* ks[] = {level64_kernel(2), level64_kernel(4), level32_kernel(2), level32_kernel(4),
+                      levelds_kernel(2), levelds_kernel(4), (const void*)k_apply64,
+                      (const void*)k_apply32, (const void*)k_apply_ds, level_adj_kernel()};
   for (const void* k : ks) {
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, smem) != cudaSuccess) return 0;
@@ -383,11 +268,11 @@ cudaError_t launch_level(const LevelArgs& a, int precision, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(a.P.bar, 0, sizeof(GridBarrier), s);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&a};
-  const bool kp2 = (a.P.gr.N1 << a.P.gr.lgct64) <= 2 * kThreads && 2 * a.P.gr.N2 <= 2 * kThreads;
-  const void* k = precision == TSFDE_MIXED_DS ? (kp2 ? (const void*)k_level_mixed_ds<2>
-                                                     : (const void*)k_level_mixed_ds<4>)
-                  : precision == TSFDE_MIXED  ? (const void*)k_level_mixed
-                                              : (const void*)k_level64;
+  const bool kp2 = kp_fits(a.P, 2);
+  const int kp = kp2 ? 2 : 4;
+  const void* k = precision == TSFDE_MIXED_DS ? levelds_kernel(kp)
+                  : precision == TSFDE_MIXED  ? level32_kernel(kp)
+                                              : level64_kernel(kp);
   return cudaLaunchCooperativeKernel(k, dim3(a.P.G), dim3(kThreads), args, smem, s);
 }
 
@@ -404,7 +289,7 @@ cudaError_t launch_level_adj(const LevelArgs& a, const AdjGradArgs& g, cudaStrea
   cudaError_t e = cudaMemsetAsync(a.P.bar, 0, sizeof(GridBarrier), s);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&a, (void*)&g};
-  return cudaLaunchCooperativeKernel((const void*)k_level_adj, dim3(a.P.G), dim3(kThreads), args, smem, s);
+  return cudaLaunchCooperativeKernel(level_adj_kernel(), dim3(a.P.G), dim3(kThreads), args, smem, s);
 }
 
 cudaError_t launch_apply(const ApplyArgs& a, int precision, cudaStream_t s) {

@@ -281,6 +281,11 @@ struct ApplyArgs {
 cudaError_t launch_rhs(const RhsArgs& a, cudaStream_t s);
 // precision: TSFDE_FP64, TSFDE_MIXED (FP32 inner) or TSFDE_MIXED_DS
 cudaError_t launch_level(const LevelArgs& a, int precision, cudaStream_t s);
+// level kernels by prefetch depth kp (2 or 4): level64.cu, level32.cu, levelds.cu
+const void* level64_kernel(int kp);
+const void* level32_kernel(int kp);
+const void* levelds_kernel(int kp);
+const void* level_adj_kernel();
 // cluster engine (cluster.cu): mixed level solve with the FP32 inner solves
 // on one thread-block cluster; a.P.G must equal a.P.cl.G.
 cudaError_t launch_level_cluster(const LevelArgs& a, cudaStream_t s);
