@@ -149,12 +149,12 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------- our arm
-# DRAM bytes per launch from one ncu capture (profiles/k_level_mixed_n131071_launches_traffic.md),
+# DRAM bytes per launch from one ncu capture (profiles/k_level_mixed_ds_n131071_launches_traffic.md),
 # valid only for the kernel sources they were taken with: the digest of those sources is kept
 # beside the figure, and a changed source makes the figure null.
-TRAFFIC = {"k_level_mixed": {"bytes": 76.63e6, "note": "dram read+write, levels 9-11, ncu",
-                             "sources": ["grid.cuh", "kernels.cu", "dev.cuh", "plan.h"],
-                             "sha1": "b603c732d0a5710bf248043f3115f175dfc2a3f5"}}
+TRAFFIC = {"k_level_mixed_ds": {"bytes": 144.33e6, "note": "dram read+write, levels 9-11, ncu",
+                                "sources": ['grid.cuh', 'levelds.cu', 'dev.cuh', 'dsf.cuh', 'plan.h'],
+                                "sha1": "4945e13e5516bec616f2b8db534e99c7efa881bc"}}
 
 
 def measured_traffic(kernel):
