@@ -56,6 +56,8 @@ def parse():
                     help="x0 = 0 for every level as in the paper's experiments (default: start "
                          "from u^{m-1}, same stopping rule ||r|| < tol ||b||)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
+    ap.add_argument("--dids-levels", type=int, default=None,
+                    help="levels of the DIDS (direct history) march to time; default M, 0 skips it")
     ap.add_argument("--flush-mb", type=int, default=256,
                     help="L2 flush buffer size (MB, twice L2 by default); smaller only for profiler runs")
     ap.add_argument("--inner", choices=["fp32", "ds"], default="ds",
@@ -339,6 +341,56 @@ def paper_table11(torch, pkg, ti):
     return rows
 
 
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor), nominal
+
+
+def dids_sample(torch, pkg, prob, stream, levels, warm, u_fids_M):
+    """The direct-history scheme DIDS (Eq. (4.1)) on the headline workload
+    with the double-single mixed solve: all levels resident, the history sum
+    over every earlier level formed by k_rhs_direct.  Times `levels` levels
+    from level 1 (CUDA events on the solver's stream; no L2 flush: the
+    history read, up to 4.3 GB per level, is far larger than L2) and reports
+    the history kernel's algorithmic bytes (8 n m per level m, plus 32 n of
+    b, kappa and f) and its FP64 FMA rate (one per history entry)."""
+    n = prob.n
+    s = pkg.Solver(prob.alpha, prob.gamma, prob.l, prob.T, n, prob.M, prob.r, prob.soe_tol,
+                   precision="mixed_ds", krylov_tol=1e-12, profile=True, stream=stream,
+                   warm_start=warm, history="direct")
+    s.set_problem_from(prob)
+    with torch.cuda.stream(stream):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(levels):
+            s.step(sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    tim = s.timing()
+    st = s.level_stats(1, levels)
+    hist = sum(m for m in range(1, levels + 1)) * n
+    rhs_s = tim["rhs_ms"] / 1e3
+    byts = 8.0 * hist + 32.0 * n * levels
+    out = {"workload": f"fids-dids n={n} M={prob.M} levels 1..{levels}, mixed_ds solve",
+           "levels_per_s": levels / t, "s": t,
+           "history_kernel": {"ms_per_level": 1e3 * rhs_s / levels,
+                              "GB/s": byts / rhs_s / 1e9, "hbm_frac": byts / rhs_s / 1e9 / measured_peaks()[0],
+                              "fp64_tflops": 2.0 * hist / rhs_s / 1e12,
+                              "fp64_frac_of_nominal": 2.0 * hist / rhs_s / 1e12 / FP64_NOMINAL_TFLOPS},
+           "level_kernel_ms_per_level": tim["level_ms"] / levels,
+           "iterations_per_level": sum(r["iterations"] for r in st) / levels,
+           "max_final_rel_residual": max(r["rel_residual"] for r in st),
+           "status": max(r["status"] for r in st)}
+    if u_fids_M is not None and levels == prob.M:
+        u = torch.empty(n, dtype=torch.float64, device="cuda")
+        s.current_solution(u)
+        out["dids_vs_fids_max_rel_diff_at_M"] = float(torch.max(torch.abs(u - u_fids_M)) /
+                                                      torch.max(torch.abs(u_fids_M)))
+    s.close()
+    return out
+
+
 def adjoint_sample(torch, pkg, ti, stream):
     """The adjoint workload: n = 4095, M = 1024, J = 1/2 ||u^M - u_obs||^2
     with u_obs from another kappa; forward march (FP64, all levels kept) and
@@ -486,6 +538,12 @@ def ours(args):
                 batched[prec]["s_max_over_ranks"] = tm[k]
                 batched[prec]["instance_levels_per_s"] = 512 * args.batched_levels / tm[k]
 
+    dids = None
+    dl = prob.M if args.dids_levels is None else min(args.dids_levels, prob.M)
+    if rank == 0 and dl > 0:
+        u_f = u_mx if s_mx.m == prob.M else None
+        dids = dids_sample(torch, pkg, prob, stream, dl, not args.cold_start, u_f)
+
     adjoint = None
     if rank == 0 and not args.no_adjoint:
         adjoint = adjoint_sample(torch, pkg, ti, stream)
@@ -514,7 +572,7 @@ def ours(args):
                         kname: {"ms": lvl_ms, "bytes": lvl_bytes, "GB/s": lvl_gbs,
                                 "frac": lvl_gbs / peak}},
             "fp64": fp64, "e2e": e2e, "gpu_launches": 2 * K, "roofline": roof,
-            "cpu_baseline": cpu, "clocks": clk, "batched": batched, "adjoint": adjoint,
+            "cpu_baseline": cpu, "clocks": clk, "batched": batched, "adjoint": adjoint, "dids": dids,
         }
         print(json.dumps(line), flush=True)
     s_mx.close()

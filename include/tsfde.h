@@ -60,6 +60,13 @@ typedef enum tsfde_status {
  * preconditioner is always built in FP64 and rounded. */
 enum { TSFDE_FP64 = 0, TSFDE_MIXED = 1, TSFDE_MIXED_DS = 2 };
 enum { TSFDE_STRANG = 0, TSFDE_PRECOND_NONE = 1 }; /* tsfde_opts.precond */
+/* tsfde_opts.history: how the Caputo history term of the right-hand side is
+ * formed.  SOE: the fast scheme FIDS (Eq. (3.16gu)), a sum-of-exponentials
+ * recurrence over E exponentials, O(n E) per level.  DIRECT: the direct
+ * scheme DIDS (Eq. (4.1)), the L1 sum over every earlier level, O(n m) per
+ * level m; the context then keeps all M+1 levels on the device
+ * ((M+1) x n doubles) and a table of the M(M+1)/2 direct weights. */
+enum { TSFDE_HISTORY_SOE = 0, TSFDE_HISTORY_DIRECT = 1 };
 /* tsfde_opts.engine: how a mixed level solve runs its FP32 inner solves.
  * GRID: spread over the whole cooperative grid (grid barriers between the
  * FFT passes).  CLUSTER: on one thread-block cluster of up to 16 CTAs that
@@ -120,6 +127,9 @@ typedef struct tsfde_opts {
                            at ||r|| < krylov_tol ||b^m|| (mixed: same
                            refinement rules); 0 (default): x0 = 0 and the
                            residual relative to ||r_0|| = ||b^m|| (Sec. 5)   */
+  int history;          /* TSFDE_HISTORY_SOE (default, FIDS) or
+                           TSFDE_HISTORY_DIRECT (DIDS); the batched solve
+                           accepts SOE only                                 */
 } tsfde_opts;
 
 typedef struct tsfde_step_info {
@@ -252,7 +262,8 @@ int tsfde_get_symbol(const tsfde_ctx* ctx, double* t);
  * Uses the context's krylov_tol / max_it / precond (always FP64).  Does not
  * change the forward state (tsfde_step continues where it was).  Device
  * work buffers are allocated on the first call.  Synchronises the stream.
- * Errors: TSFDE_ESTATE without a problem, TSFDE_ENOTSUP if kappa1 was set,
+ * Errors: TSFDE_ESTATE without a problem, TSFDE_ENOTSUP if kappa1 was set or
+ * the context uses the direct history (the sweep is the adjoint of FIDS),
  * TSFDE_EINVAL for NULL pointers, else the first failing level's status. */
 int tsfde_adjoint(tsfde_ctx* ctx, const double* u_all, const double* dJ_duM,
                   double* grad_kappa, double* grad_f, tsfde_adjoint_info* info);

@@ -43,6 +43,10 @@ struct tsfde_ctx {
   KVecs<dsf> kds{};        // TSFDE_MIXED_DS inner vectors
   dsf* kappads = nullptr;
   double* r64 = nullptr;
+  // direct history (DIDS): every level u^0..u^M (rows of ld doubles) and the
+  // packed weights, row m (m entries) at offset m(m-1)/2
+  double* Uh = nullptr;
+  double* wdir = nullptr;
   StepStat* stats = nullptr;
   int* status = nullptr;
   int engine = TSFDE_ENGINE_GRID;  // engine of the mixed level solves
@@ -80,6 +84,13 @@ template <typename T> bool dalloc(tsfde_ctx* c, T** p, size_t count) {
 template <typename T> cudaError_t upload(T* dst, const std::vector<T>& src) {
   return cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
+
+// Device vector of level m: a row of the stored levels with the direct
+// history, else one of three rotating buffers.
+double* ulev(tsfde_ctx* c, int64_t m) {
+  return c->Uh ? c->Uh + (size_t)m * c->ld : c->u[m % 3];
+}
+
 
 int ilog2(int64_t x) {
   int k = 0;
@@ -129,6 +140,7 @@ int tsfde_default_opts(tsfde_opts* o) {
   o->engine = TSFDE_ENGINE_AUTO;
   o->cluster_size = 0;
   o->warm_start = 0;
+  o->history = TSFDE_HISTORY_SOE;
   return TSFDE_OK;
 }
 
@@ -187,6 +199,8 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
   if (o.barrier_timeout_cycles < 0) return fail(c, TSFDE_EINVAL, "barrier_timeout_cycles < 0");
   if (o.engine != TSFDE_ENGINE_AUTO && o.engine != TSFDE_ENGINE_GRID && o.engine != TSFDE_ENGINE_CLUSTER)
     return fail(c, TSFDE_EINVAL, "engine must be TSFDE_ENGINE_AUTO, _GRID or _CLUSTER");
+  if (o.history != TSFDE_HISTORY_SOE && o.history != TSFDE_HISTORY_DIRECT)
+    return fail(c, TSFDE_EINVAL, "history must be TSFDE_HISTORY_SOE or TSFDE_HISTORY_DIRECT");
   c->alpha = alpha; c->gamma = gamma; c->l = l; c->T = T; c->n = n; c->M = M; c->r = r;
   c->soe_tol = soe_tol; c->mu = mu; c->kappa_mu = kmu;
   c->stream = static_cast<cudaStream_t>(o.stream);
@@ -369,7 +383,27 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
                    &c->kds.ph, &c->kds.sh};
     for (dsf** p : vds) ok &= dalloc(c, p, ld);
   }
+  // direct history: all levels and the weights of Eq. (4.1),
+  // w_0 = a_1/Gamma(1-g), w_k = (a_{k+1} - a_k)/Gamma(1-g) (k = 1..m-1)
+  std::vector<double> wdir_h;
+  if (o.history == TSFDE_HISTORY_DIRECT) {
+    ok &= dalloc(c, &c->Uh, (size_t)(M + 1) * ld) && dalloc(c, &c->wdir, (size_t)M * (M + 1) / 2);
+    wdir_h.assign((size_t)M * (M + 1) / 2, 0.0);
+    const double G1h = std::tgamma(1.0 - gamma);
+    std::vector<double> a(M + 2);
+    for (int64_t m = 1; m <= M; ++m) {
+      for (int64_t k = 1; k <= m; ++k) a[k] = l1_weight(T, M, r, gamma, m, k);
+      double* w = wdir_h.data() + (size_t)m * (m - 1) / 2;
+      w[0] = a[1] / G1h;
+      for (int64_t k = 1; k < m; ++k) w[k] = (a[k + 1] - a[k]) / G1h;
+    }
+  }
   if (!ok) return fail(c, TSFDE_ENOMEM, "cudaMalloc failed");
+  if (c->Uh) {
+    if ((e = upload(c->wdir, wdir_h)) != cudaSuccess) return cuda_fail(c, e, "upload");
+    if ((e = cudaMemset(c->Uh, 0, sizeof(double) * (size_t)(M + 1) * ld)) != cudaSuccess)
+      return cuda_fail(c, e, "cudaMemset");
+  }
   if (ds) {
     std::vector<dsf2> twds(L);
     for (int64_t k = 0; k < L; ++k) {
@@ -500,7 +534,7 @@ int tsfde_reset(tsfde_ctx* c) {
   if (!c) return TSFDE_EINVAL;
   if (!c->have_problem) return fail(c, TSFDE_ESTATE, "no problem set");
   cudaError_t e;
-  if ((e = cudaMemcpyAsync(c->u[0], c->phi, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
+  if ((e = cudaMemcpyAsync(ulev(c, 0), c->phi, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "reset copy");
   if ((e = cudaMemsetAsync(c->G, 0, sizeof(double) * (size_t)std::max(c->E, 1) * c->ld, c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "reset memset");
@@ -564,8 +598,8 @@ static int enqueue_level(tsfde_ctx* c, const double* kappa_m, const double* f_m,
   R.Gm = c->G;
   R.eps = c->eps + m * c->E;
   R.cw = c->cw + m * c->E;
-  R.u1 = c->u[(m - 1) % 3];
-  R.u2 = (m >= 2) ? c->u[(m - 2) % 3] : c->u[(m - 1) % 3];
+  R.u1 = ulev(c, m - 1);
+  R.u2 = (m >= 2) ? ulev(c, m - 2) : ulev(c, m - 1);
   R.kap_m = kappa_m;
   R.kap0 = c->kap0;
   R.kap1 = c->kap1 ? c->kap1d : nullptr;
@@ -578,12 +612,18 @@ static int enqueue_level(tsfde_ctx* c, const double* kappa_m, const double* f_m,
   R.rhs_copy = rhs_out;
   R.kappa64 = c->kappa64;
   R.kappa32 = c->kappa32;
+  if (c->Uh) {
+    R.U_hist = c->Uh;
+    R.w_dir = c->wdir + (size_t)m * (m - 1) / 2;
+    R.m_hist = (int)m;
+    R.Eact = 0;
+  }
   cudaError_t e = record(c);
-  if (e == cudaSuccess) e = launch_rhs(R, c->stream);
+  if (e == cudaSuccess) e = c->Uh ? launch_rhs_direct(R, c->stream) : launch_rhs(R, c->stream);
   if (e == cudaSuccess) e = record(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "rhs kernel");
-  LevelArgs A = level_args(c, c->ahat[m], c->b, c->u[m % 3], c->stats + m);
-  A.u_prev = c->opts.warm_start ? c->u[(m - 1) % 3] : nullptr;
+  LevelArgs A = level_args(c, c->ahat[m], c->b, ulev(c, m), c->stats + m);
+  A.u_prev = c->opts.warm_start ? ulev(c, m - 1) : nullptr;
   A.prev = (m >= 2) ? c->stats + (m - 1) : nullptr;
   A.retry_mixed = (m % 64 == 0) ? 1 : 0;
   e = launch_level_ctx(c, A);
@@ -602,7 +642,7 @@ int tsfde_step(tsfde_ctx* c, const double* kappa_m, const double* f_m, double* u
   if (st != TSFDE_OK) return st;
   const int64_t m = c->m;
   cudaError_t e;
-  if (u_out && (e = cudaMemcpyAsync(u_out, c->u[m % 3], sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
+  if (u_out && (e = cudaMemcpyAsync(u_out, ulev(c, m), sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "u copy");
   if (info) {
     StepStat s{};
@@ -626,15 +666,15 @@ int tsfde_solve(tsfde_ctx* c, double* u_final, double* u_all, tsfde_solve_info* 
   const int64_t m0 = c->m;
   const size_t nb = sizeof(double) * c->n;
   cudaError_t e;
-  if (u_all && m0 == 0 && (e = cudaMemcpyAsync(u_all, c->u[0], nb, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
+  if (u_all && m0 == 0 && (e = cudaMemcpyAsync(u_all, ulev(c, 0), nb, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "u copy");
   while (c->m < c->M) {
     int st = enqueue_level(c, nullptr, nullptr, nullptr);
     if (st != TSFDE_OK) return st;
-    if (u_all && (e = cudaMemcpyAsync(u_all + c->m * c->n, c->u[c->m % 3], nb, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
+    if (u_all && (e = cudaMemcpyAsync(u_all + c->m * c->n, ulev(c, c->m), nb, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
       return cuda_fail(c, e, "u copy");
   }
-  if (u_final && (e = cudaMemcpyAsync(u_final, c->u[c->m % 3], nb, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
+  if (u_final && (e = cudaMemcpyAsync(u_final, ulev(c, c->m), nb, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "u copy");
   if (info) {
     std::vector<StepStat> s(c->M + 1);
@@ -687,7 +727,7 @@ int tsfde_get_level_stats(tsfde_ctx* c, int64_t m0, int64_t m1, tsfde_step_info*
 int tsfde_get_solution(tsfde_ctx* c, double* u) {
   if (!c || !u) return TSFDE_EINVAL;
   if (!c->have_problem) return fail(c, TSFDE_ESTATE, "no problem set");
-  cudaError_t e = cudaMemcpyAsync(u, c->u[c->m % 3], sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream);
+  cudaError_t e = cudaMemcpyAsync(u, ulev(c, c->m), sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "solution copy");
   return TSFDE_OK;
 }
@@ -781,6 +821,7 @@ int tsfde_adjoint(tsfde_ctx* c, const double* u_all, const double* dJ, double* g
   if (!c || !u_all || !dJ || !grad_kappa || !grad_f) return TSFDE_EINVAL;
   if (!c->have_problem) return fail(c, TSFDE_ESTATE, "no problem set");
   if (c->kap1) return fail(c, TSFDE_ENOTSUP, "adjoint needs a time-independent kappa (kappa1 = NULL)");
+  if (c->Uh) return fail(c, TSFDE_ENOTSUP, "the adjoint sweep is that of FIDS (history = SOE)");
   const int64_t n = c->n, M = c->M;
   const int E = std::max(c->E, 1);
   if (!c->adjY) {

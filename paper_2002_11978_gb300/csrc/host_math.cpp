@@ -20,6 +20,16 @@ double mesh_gap(double T, int64_t M, double r, int64_t m, int64_t k) {
   return -tm * std::expm1(r * std::log((double)k / (double)m));
 }
 
+double l1_weight(double T, int64_t M, double r, double gamma, int64_t m, int64_t k) {
+  const double tau = mesh_gap(T, M, r, k, k - 1);
+  const double g1 = 1.0 - gamma;
+  if (k == m) return std::pow(tau, -gamma) / g1;
+  // (D_{k-1}^{g1} - D_k^{g1}) / (g1 tau) with D_{k-1} = D_k + tau, written
+  // D_k^{g1} ((1 + tau/D_k)^{g1} - 1) so that nothing cancels when tau << D_k
+  const double D = mesh_gap(T, M, r, m, k);
+  return std::pow(D, g1) * std::expm1(g1 * std::log1p(tau / D)) / (g1 * tau);
+}
+
 double c1alpha(double alpha) {
   return std::pow(2.0, alpha - 1.0) * alpha * std::tgamma(0.5 * (alpha + 1.0)) /
          (std::sqrt(kPi) * std::tgamma(1.0 - 0.5 * alpha));

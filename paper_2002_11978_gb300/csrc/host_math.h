@@ -16,6 +16,10 @@ double mesh_t(double T, int64_t M, double r, int64_t m);
 // t_m - t_k, 0 <= k <= m, via -t_m expm1(r log(k/m)) (no cancellation).
 double mesh_gap(double T, int64_t M, double r, int64_t m, int64_t k);
 
+// a_k^{(m)} of Eq. (2.8), 1 <= k <= m: the L1 weight of the interval
+// [t_{k-1}, t_k] at level m, (1/tau_k) int (t_m - s)^{-gamma} ds.
+double l1_weight(double T, int64_t M, double r, double gamma, int64_t m, int64_t k);
+
 // c_{1,alpha} of Eq. (1.4).
 double c1alpha(double alpha);
 

@@ -206,6 +206,85 @@ __global__ void __launch_bounds__(kThreads) k_rhs(RhsArgs a) {
   }
 }
 
+// ------------------------------------------ direct history (DIDS) and RHS
+// b = sum_{k<m} w_k u^k + f^m (Eq. (4.1): w_0 = a_1/Gamma(1-gamma),
+// w_k = (a_{k+1} - a_k)/Gamma(1-gamma)), from every stored level.  Same
+// block shape as k_rhs: 64 entry pairs x 4 row groups, 16-byte loads of the
+// history rows (streamed: each is read once per level, and the level solve's
+// vectors should keep L2), kDirU rows in flight per thread; the weights are
+// staged in shared memory kDirChunk at a time; the groups' partial sums are
+// added in a fixed order.  One FP64 FMA per 8 bytes read.
+constexpr int kDirU = 8;
+constexpr int kDirChunk = 2048;
+
+__global__ void __launch_bounds__(kThreads) k_rhs_direct(RhsArgs a) {
+  extern __shared__ double sh[];
+  double* s_w = sh;
+  double2* s_part = reinterpret_cast<double2*>(sh + kDirChunk);  // 16-byte aligned
+  const int npair = (a.n + 1) >> 1;
+  const size_t ld2 = (size_t)a.ld >> 1;
+  const int lane = threadIdx.x % kRhsPairs, grp = threadIdx.x / kRhsPairs;
+  for (int base = blockIdx.x * kRhsPairs; base < npair; base += gridDim.x * kRhsPairs) {
+    const int pp = base + lane;
+    const int i = 2 * pp;
+    const bool in = pp < npair;
+    const bool two = i + 1 < a.n;
+    double sx = 0.0, sy = 0.0;
+    for (int k0 = 0; k0 < a.m_hist; k0 += kDirChunk) {
+      const int kn = min(kDirChunk, a.m_hist - k0);
+      __syncthreads();  // the previous chunk's weights are no longer read
+      for (int q = threadIdx.x; q < kn; q += blockDim.x) s_w[q] = a.w_dir[k0 + q];
+      __syncthreads();
+      const int chunk = (kn + kRhsGroups - 1) / kRhsGroups;
+      const int j0 = grp * chunk, j1 = min(kn, j0 + chunk);
+      if (!in) continue;
+      const double2* Ub = reinterpret_cast<const double2*>(a.U_hist + i) + (size_t)k0 * ld2;
+      for (int j = j0; j < j1; j += kDirU) {
+        double2 g[kDirU];
+#pragma unroll
+        for (int u = 0; u < kDirU; ++u)
+          if (j + u < j1) g[u] = __ldcs(Ub + (size_t)(j + u) * ld2);
+#pragma unroll
+        for (int u = 0; u < kDirU; ++u) {
+          if (j + u < j1) {
+            const double w = s_w[j + u];
+            sx = fma(w, g[u].x, sx);
+            sy = fma(w, g[u].y, sy);
+          }
+        }
+      }
+    }
+    s_part[threadIdx.x] = make_double2(sx, sy);
+    __syncthreads();
+    if (grp == 0 && in) {
+      for (int q = 1; q < kRhsGroups; ++q) {
+        const double2 v = s_part[q * kRhsPairs + lane];
+        sx += v.x;
+        sy += v.y;
+      }
+      for (int h = 0; h < (two ? 2 : 1); ++h) {
+        const int ii = i + h;
+        double f;
+        if (a.f_m) {
+          f = a.f_m[ii];
+        } else {
+          f = 0.0;
+          for (int q = 0; q < a.rank; ++q) f += a.Gr[q] * a.F[(size_t)q * a.n + ii];
+        }
+        const double bi = (h ? sy : sx) + f;
+        a.b[ii] = bi;
+        if (a.rhs_copy) a.rhs_copy[ii] = bi;
+        double k;
+        if (a.kap_m) k = a.kap_m[ii];
+        else k = a.kap0[ii] + (a.kap1 ? a.theta * a.kap1[ii] : 0.0);
+        a.kappa64[ii] = k;
+        a.kappa32[ii] = (float)k;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void k_convert(const double* in, double* o64, float* o32, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double v = in[i];
@@ -254,6 +333,15 @@ cudaError_t launch_rhs(const RhsArgs& a, cudaStream_t s) {
   const size_t smem = (2 * (size_t)(a.Eact > 0 ? a.Eact : 1) + 1) * sizeof(double) +
                       kThreads * sizeof(double2);
   k_rhs<<<grid, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_direct(const RhsArgs& a, cudaStream_t s) {
+  const int npair = (a.n + 1) / 2;
+  int grid = (npair + kRhsPairs - 1) / kRhsPairs;
+  if (grid < 1) grid = 1;
+  const size_t smem = kDirChunk * sizeof(double) + kThreads * sizeof(double2);
+  k_rhs_direct<<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

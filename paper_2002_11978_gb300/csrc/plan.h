@@ -239,6 +239,10 @@ struct RhsArgs {
   double* rhs_copy;        // NULL or user buffer
   double* kappa64;
   float* kappa32;
+  // direct history (DIDS, Eq. (4.1)); used by k_rhs_direct only
+  const double* U_hist;    // (m_hist rows) x ld: u^0 .. u^{m-1}
+  const double* w_dir;     // m_hist weights: b = sum_k w_k u^k + f^m
+  int m_hist;
 };
 
 // Adjoint sweep (reverse time): the right-hand side g^m of the transposed
@@ -279,6 +283,8 @@ struct ApplyArgs {
 
 // launchers (kernels.cu)
 cudaError_t launch_rhs(const RhsArgs& a, cudaStream_t s);
+// DIDS right-hand side from the stored levels (a.U_hist, a.w_dir, a.m_hist)
+cudaError_t launch_rhs_direct(const RhsArgs& a, cudaStream_t s);
 // precision: TSFDE_FP64, TSFDE_MIXED (FP32 inner) or TSFDE_MIXED_DS
 cudaError_t launch_level(const LevelArgs& a, int precision, cudaStream_t s);
 // level kernels by prefetch depth kp (2 or 4): level64.cu, level32.cu, levelds.cu

@@ -92,3 +92,31 @@ def test_setup_rejects_unknown_engine(lib):
                            ctypes.byref(o)) == pkg.TSFDE_EINVAL
     assert not ctx
     assert lib.tsfde_get_engine(None) == -1
+
+
+def test_setup_validates_history_and_precision(lib):
+    import paper_2002_11978_gb300 as pkg
+    ctx = ctypes.c_void_p()
+    o = pkg.default_opts()
+    assert o.history == pkg.TSFDE_HISTORY_SOE
+    o.history = 5
+    assert lib.tsfde_setup(ctypes.byref(ctx), 1.5, 0.5, 1.0, 1.0, 7, 4, 3.0, 1e-12,
+                           ctypes.byref(o)) == pkg.TSFDE_EINVAL
+    o = pkg.default_opts()
+    o.precision = 3
+    assert lib.tsfde_setup(ctypes.byref(ctx), 1.5, 0.5, 1.0, 1.0, 7, 4, 3.0, 1e-12,
+                           ctypes.byref(o)) == pkg.TSFDE_EINVAL
+    assert not ctx
+
+
+def test_batch_rejects_direct_history(lib):
+    """The batched solve is FIDS only: the direct history is refused before
+    any device work."""
+    import paper_2002_11978_gb300 as pkg
+    o = pkg.default_opts()
+    o.history = pkg.TSFDE_HISTORY_DIRECT
+    inst = (pkg.tsfde_instance * 1)()
+    inst[0] = pkg.tsfde_instance(1.5, 0.5, 1.0, 1.0, 3.0, 63, 1e-12, None, None, None)
+    b = ctypes.c_void_p()
+    assert lib.tsfde_batch_setup(ctypes.byref(b), 1, inst, 8, ctypes.byref(o)) == pkg.TSFDE_ENOTSUP
+    assert not b
