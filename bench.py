@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
     ap.add_argument("--dids-levels", type=int, default=None,
                     help="levels of the DIDS (direct history) march to time; default M, 0 skips it")
+    ap.add_argument("--krylov", choices=["bicgstab", "pcg"], default="pcg",
+                    help="level solver of the mixed and FP64 arms: PCG on the symmetrised system, or "
+                         "the paper's BiCGSTAB (with pcg an extra FP64 BiCGSTAB arm is reported)")
     ap.add_argument("--flush-mb", type=int, default=256,
                     help="L2 flush buffer size (MB, twice L2 by default); smaller only for profiler runs")
     ap.add_argument("--inner", choices=["fp32", "ds"], default="ds",
@@ -171,7 +174,7 @@ def measured_traffic(kernel):
     return t["bytes"] if h.hexdigest() == t["sha1"] else None
 
 
-def run_arm(torch, pkg, prob, precision, W, K, flush, stream, e2e=False, warm=False):
+def run_arm(torch, pkg, prob, precision, W, K, flush, stream, e2e=False, warm=False, krylov="bicgstab"):
     """March W untimed levels, then K timed levels (restarting the march
     after level M).  Each timed level is bracketed by CUDA events on the
     solver's stream, with an L2 flush before it.  Returns the solver, the
@@ -179,7 +182,7 @@ def run_arm(torch, pkg, prob, precision, W, K, flush, stream, e2e=False, warm=Fa
     totals of the timed levels."""
     s = pkg.Solver(prob.alpha, prob.gamma, prob.l, prob.T, prob.n, prob.M, prob.r, prob.soe_tol,
                    precision=precision, krylov_tol=1e-12, profile=True, stream=stream,
-                   warm_start=warm)
+                   warm_start=warm, krylov=krylov)
     s.set_problem_from(prob)
     n = prob.n
     dev = torch.device("cuda")
@@ -344,7 +347,7 @@ def paper_table11(torch, pkg, ti):
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor), nominal
 
 
-def dids_sample(torch, pkg, prob, stream, levels, warm, u_fids_M):
+def dids_sample(torch, pkg, prob, stream, levels, warm, u_fids_M, krylov):
     """The direct-history scheme DIDS (Eq. (4.1)) on the headline workload
     with the double-single mixed solve: all levels resident, the history sum
     over every earlier level formed by k_rhs_direct.  Times `levels` levels
@@ -355,7 +358,7 @@ def dids_sample(torch, pkg, prob, stream, levels, warm, u_fids_M):
     n = prob.n
     s = pkg.Solver(prob.alpha, prob.gamma, prob.l, prob.T, n, prob.M, prob.r, prob.soe_tol,
                    precision="mixed_ds", krylov_tol=1e-12, profile=True, stream=stream,
-                   warm_start=warm, history="direct")
+                   warm_start=warm, history="direct", krylov=krylov)
     s.set_problem_from(prob)
     with torch.cuda.stream(stream):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -372,7 +375,7 @@ def dids_sample(torch, pkg, prob, stream, levels, warm, u_fids_M):
     hist = sum(m for m in range(1, levels + 1)) * n
     rhs_s = tim["rhs_ms"] / 1e3
     byts = 8.0 * hist + 32.0 * n * levels
-    out = {"workload": f"fids-dids n={n} M={prob.M} levels 1..{levels}, mixed_ds solve",
+    out = {"workload": f"fids-dids n={n} M={prob.M} levels 1..{levels}, mixed_ds {krylov} solve",
            "levels_per_s": levels / t, "s": t,
            "history_kernel": {"ms_per_level": 1e3 * rhs_s / levels,
                               "GB/s": byts / rhs_s / 1e9, "hbm_frac": byts / rhs_s / 1e9 / measured_peaks()[0],
@@ -481,7 +484,9 @@ def ours(args):
     clocks.start()
     ds = args.inner == "ds"
     prec_mx = "mixed_ds" if ds else "mixed"
-    s_mx, ms_mx, tim_mx, st_mx = run_arm(torch, pkg, prob, prec_mx, W, K, flush, stream, warm=(not args.cold_start))
+    kry = args.krylov
+    s_mx, ms_mx, tim_mx, st_mx = run_arm(torch, pkg, prob, prec_mx, W, K, flush, stream,
+                                         warm=(not args.cold_start), krylov=kry)
     barrier()
     clk = clocks.stop()
     t_mx = max_over_ranks([sum(ms_mx) / 1e3], "cuda")[0]
@@ -490,7 +495,8 @@ def ours(args):
     # ---- plain FP64 arm on the same levels: the comparison
     fp64 = None
     if not args.no_fp64:
-        s64, ms64, tim64, st64 = run_arm(torch, pkg, prob, "fp64", W, K, flush, stream, warm=(not args.cold_start))
+        s64, ms64, tim64, st64 = run_arm(torch, pkg, prob, "fp64", W, K, flush, stream,
+                                         warm=(not args.cold_start), krylov=kry)
         u64 = current_u(torch, s64)
         rel = float(torch.max(torch.abs(u_mx - u64)) / torch.max(torch.abs(u64)))
         t64 = sum(ms64) / 1e3
@@ -500,14 +506,28 @@ def ours(args):
                 "kernel_ms": {"k_rhs": tim64["rhs_ms"] / K, "k_level64": tim64["level_ms"] / K},
                 "status": st64["status"],
                 "mixed_vs_fp64_max_rel_err_at_last_level": rel,
-                "mixed_speedup": (K / t_mx * (1 if world == 1 else 1)) / (K / t64)}
+                "mixed_speedup": (K / t_mx * (1 if world == 1 else 1)) / (K / t64),
+                "krylov": kry}
         s64.close()
+        if kry == "pcg":
+            # the paper's solver, FP64 right-preconditioned BiCGSTAB, on the same levels
+            sb, msb, timb, stb = run_arm(torch, pkg, prob, "fp64", W, K, flush, stream,
+                                         warm=(not args.cold_start), krylov="bicgstab")
+            ub = current_u(torch, sb)
+            tb = sum(msb) / 1e3
+            fp64["paper_bicgstab"] = {
+                "steps_per_s": K / tb, "iterations_per_step": stb["its"] / K,
+                "level_kernel_ms": timb["level_ms"] / K,
+                "mixed_vs_bicgstab_max_rel_err_at_last_level":
+                    float(torch.max(torch.abs(u_mx - ub)) / torch.max(torch.abs(ub))),
+                "mixed_speedup": tb / t_mx}
+            sb.close()
 
     # ---- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
         se, ms_e2e, _, _ = run_arm(torch, pkg, prob, prec_mx, W, K, flush, stream, e2e=True,
-                                    warm=(not args.cold_start))
+                                    warm=(not args.cold_start), krylov=kry)
         se.close()
         e2e = {"value": world * K / (sum(ms_e2e) / 1e3), "unit": "steps/s",
                "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n,
@@ -518,10 +538,11 @@ def ours(args):
     rhs_ms = tim_mx["rhs_ms"] / K
     lvl_ms = tim_mx["level_ms"] / K
     rhs_bytes = (16.0 * n * st_mx["E_active_sum"] + K * 8.0 * n * (3 + 1)) / K
-    # 22 inner-vector accesses per inner iteration (4 or 8 bytes per entry),
-    # 5 FP64 vector accesses per refinement sweep
-    lvl_bytes = ((176.0 if ds else 88.0) * n * st_mx["its"] + 40.0 * n * st_mx["outer"]) / K
-    kname = "k_level_mixed_ds" if ds else "k_level_mixed"
+    # inner-vector accesses per inner iteration: 22 for BiCGSTAB, 15 for PCG
+    # (4 or 8 bytes per entry); 5 FP64 vector accesses per refinement sweep
+    acc_it = 15 if kry == "pcg" else 22
+    lvl_bytes = (acc_it * (8.0 if ds else 4.0) * n * st_mx["its"] + 40.0 * n * st_mx["outer"]) / K
+    kname = ("k_level_mixed_ds" if ds else "k_level_mixed") + ("/pcg" if kry == "pcg" else "")
     rhs_gbs = rhs_bytes / (rhs_ms * 1e-3) / 1e9
     lvl_gbs = lvl_bytes / (lvl_ms * 1e-3) / 1e9
     dom = (kname, lvl_gbs) if lvl_ms >= rhs_ms else ("k_rhs", rhs_gbs)
@@ -542,7 +563,7 @@ def ours(args):
     dl = prob.M if args.dids_levels is None else min(args.dids_levels, prob.M)
     if rank == 0 and dl > 0:
         u_f = u_mx if s_mx.m == prob.M else None
-        dids = dids_sample(torch, pkg, prob, stream, dl, not args.cold_start, u_f)
+        dids = dids_sample(torch, pkg, prob, stream, dl, not args.cold_start, u_f, kry)
 
     adjoint = None
     if rank == 0 and not args.no_adjoint:
@@ -558,8 +579,10 @@ def ours(args):
             "steps": K, "warmup": W, "ms_per_step": t_mx * 1e3 / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "M": prob.M, "first_timed_level": W + 1,
-                       "precision": ("mixed: double-single (FP32-pair) inner PBiCGSTAB" if ds else
-                                     "mixed: FP32 inner PBiCGSTAB") + ", FP64 refinement/residual/SOE",
+                       "precision": ("mixed: double-single (FP32-pair) inner " if ds else "mixed: FP32 inner ")
+                                    + ("PCG on the symmetrised system" if kry == "pcg" else "PBiCGSTAB")
+                                    + ", FP64 refinement/residual/SOE",
+                       "krylov": kry,
                        "krylov_tol": 1e-12, "inner_tol": 1e-2,
                        "initial_guess": "u^{m-1}" if (not args.cold_start) else "0 (Sec. 5)",
                        "l2": f"flushed before every timed level ({args.flush_mb} MB write, then {args.flush_mb} MB read, outside the events)",

@@ -67,6 +67,19 @@ enum { TSFDE_STRANG = 0, TSFDE_PRECOND_NONE = 1 }; /* tsfde_opts.precond */
  * level m; the context then keeps all M+1 levels on the device
  * ((M+1) x n doubles) and a table of the M(M+1)/2 direct weights. */
 enum { TSFDE_HISTORY_SOE = 0, TSFDE_HISTORY_DIRECT = 1 };
+/* tsfde_opts.krylov: the level solver.  BICGSTAB: the paper's
+ * right-preconditioned BiCGSTAB on (a I + K A) x = b (Sec. 4.1, Sec. 5).
+ * PCG: conjugate gradients on the equivalent symmetric positive definite
+ * system (a K^{-1} + A) x = K^{-1} b (K = diag(kappa); A is SPD by the
+ * proposition after Eq. (3.16x)), preconditioned by a/kbar I + s(A), the
+ * Strang preconditioner of Eq. (4.3) up to a constant factor.  Sec. 4.2
+ * proposes PCG for kappa independent of x; the symmetrisation extends it to
+ * any kappa > 0.  One product with A and one with the preconditioner per
+ * iteration instead of two of each; the stopping test is the same, on the
+ * residual of the original system.  The mixed paths use it for their inner
+ * solves and their FP64 finish.  Grid engine only; the adjoint sweep and the
+ * batched solve use BiCGSTAB. */
+enum { TSFDE_KRYLOV_BICGSTAB = 0, TSFDE_KRYLOV_PCG = 1 };
 /* tsfde_opts.engine: how a mixed level solve runs its FP32 inner solves.
  * GRID: spread over the whole cooperative grid (grid barriers between the
  * FFT passes).  CLUSTER: on one thread-block cluster of up to 16 CTAs that
@@ -130,6 +143,9 @@ typedef struct tsfde_opts {
   int history;          /* TSFDE_HISTORY_SOE (default, FIDS) or
                            TSFDE_HISTORY_DIRECT (DIDS); the batched solve
                            accepts SOE only                                 */
+  int krylov;           /* TSFDE_KRYLOV_BICGSTAB (default) or
+                           TSFDE_KRYLOV_PCG; the batched solve accepts
+                           BICGSTAB only                                    */
 } tsfde_opts;
 
 typedef struct tsfde_step_info {

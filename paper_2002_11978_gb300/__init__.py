@@ -25,6 +25,7 @@ TSFDE_EBREAKDOWN, TSFDE_ETIMEOUT, TSFDE_ESTATE, TSFDE_ENONFINITE, TSFDE_ENOTSUP 
 TSFDE_FP64, TSFDE_MIXED, TSFDE_MIXED_DS = 0, 1, 2
 TSFDE_STRANG, TSFDE_PRECOND_NONE = 0, 1
 TSFDE_HISTORY_SOE, TSFDE_HISTORY_DIRECT = 0, 1
+TSFDE_KRYLOV_BICGSTAB, TSFDE_KRYLOV_PCG = 0, 1
 TSFDE_ENGINE_AUTO, TSFDE_ENGINE_GRID, TSFDE_ENGINE_CLUSTER = 0, 1, 2
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -39,7 +40,7 @@ class tsfde_opts(ctypes.Structure):
                 ("soe_E", ctypes.c_int), ("soe_s", _dp), ("soe_w", _dp), ("profile", ctypes.c_int),
                 ("barrier_timeout_cycles", ctypes.c_longlong), ("stream", ctypes.c_void_p),
                 ("engine", ctypes.c_int), ("cluster_size", ctypes.c_int),
-                ("warm_start", ctypes.c_int), ("history", ctypes.c_int)]
+                ("warm_start", ctypes.c_int), ("history", ctypes.c_int), ("krylov", ctypes.c_int)]
 
 
 class tsfde_step_info(ctypes.Structure):
@@ -192,9 +193,11 @@ class Solver:
     def __init__(self, alpha, gamma, l, T, n, M, r, soe_tol=1e-12, *, precision="fp64",
                  precond="strang", krylov_tol=1e-12, max_it=2000, inner_tol=1e-2,
                  max_outer=60, inner_max_it=40, mu=None, kappa_mu=None, soe=None, barrier_timeout_cycles=0,
-                 profile=False, stream=None, engine="auto", warm_start=False, history="soe"):
+                 profile=False, stream=None, engine="auto", warm_start=False, history="soe",
+                 krylov="bicgstab"):
         lib = load_library()
         o = default_opts()
+        o.krylov = {"bicgstab": TSFDE_KRYLOV_BICGSTAB, "pcg": TSFDE_KRYLOV_PCG}[krylov]
         o.history = {"soe": TSFDE_HISTORY_SOE, "direct": TSFDE_HISTORY_DIRECT}[history]
         o.warm_start = 1 if warm_start else 0
         o.engine = {"auto": TSFDE_ENGINE_AUTO, "grid": TSFDE_ENGINE_GRID,

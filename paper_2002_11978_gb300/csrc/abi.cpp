@@ -42,6 +42,9 @@ struct tsfde_ctx {
   KVecs<float> k32{};
   KVecs<dsf> kds{};        // TSFDE_MIXED_DS inner vectors
   dsf* kappads = nullptr;
+  double* hinv64 = nullptr;  // PCG: 1/kappa^m
+  float* hinv32 = nullptr;
+  dsf* hinvds = nullptr;
   double* r64 = nullptr;
   // direct history (DIDS): every level u^0..u^M (rows of ld doubles) and the
   // packed weights, row m (m entries) at offset m(m-1)/2
@@ -141,6 +144,7 @@ int tsfde_default_opts(tsfde_opts* o) {
   o->cluster_size = 0;
   o->warm_start = 0;
   o->history = TSFDE_HISTORY_SOE;
+  o->krylov = TSFDE_KRYLOV_BICGSTAB;
   return TSFDE_OK;
 }
 
@@ -201,6 +205,10 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
     return fail(c, TSFDE_EINVAL, "engine must be TSFDE_ENGINE_AUTO, _GRID or _CLUSTER");
   if (o.history != TSFDE_HISTORY_SOE && o.history != TSFDE_HISTORY_DIRECT)
     return fail(c, TSFDE_EINVAL, "history must be TSFDE_HISTORY_SOE or TSFDE_HISTORY_DIRECT");
+  if (o.krylov != TSFDE_KRYLOV_BICGSTAB && o.krylov != TSFDE_KRYLOV_PCG)
+    return fail(c, TSFDE_EINVAL, "krylov must be TSFDE_KRYLOV_BICGSTAB or TSFDE_KRYLOV_PCG");
+  if (o.krylov == TSFDE_KRYLOV_PCG && o.precision == TSFDE_MIXED && o.engine == TSFDE_ENGINE_CLUSTER)
+    return fail(c, TSFDE_ENOTSUP, "the cluster engine runs BiCGSTAB only");
   c->alpha = alpha; c->gamma = gamma; c->l = l; c->T = T; c->n = n; c->M = M; c->r = r;
   c->soe_tol = soe_tol; c->mu = mu; c->kappa_mu = kmu;
   c->stream = static_cast<cudaStream_t>(o.stream);
@@ -325,7 +333,8 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
   // ---- cluster engine (mixed level solves only): one cooperative launch of
   // whole clusters; cluster 0 runs the FP32 inner solves
   bool use_cluster = false;
-  if (o.precision == TSFDE_MIXED && o.engine == TSFDE_ENGINE_CLUSTER && cluster_geometry(P)) {
+  if (o.precision == TSFDE_MIXED && o.krylov == TSFDE_KRYLOV_BICGSTAB &&
+      o.engine == TSFDE_ENGINE_CLUSTER && cluster_geometry(P)) {
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const size_t csmem = std::max(plan_smem_bytes(P), cluster_smem_bytes(P));
@@ -382,6 +391,10 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
     dsf** vds[] = {&c->kds.x, &c->kds.r, &c->kds.rh, &c->kds.p, &c->kds.v, &c->kds.s, &c->kds.t,
                    &c->kds.ph, &c->kds.sh};
     for (dsf** p : vds) ok &= dalloc(c, p, ld);
+  }
+  if (o.krylov == TSFDE_KRYLOV_PCG) {
+    ok &= dalloc(c, &c->hinv64, n) && dalloc(c, &c->hinv32, ld);
+    if (ds) ok &= dalloc(c, &c->hinvds, ld);
   }
   // direct history: all levels and the weights of Eq. (4.1),
   // w_0 = a_1/Gamma(1-g), w_k = (a_{k+1} - a_k)/Gamma(1-g) (k = 1..m-1)
@@ -560,6 +573,10 @@ static LevelArgs level_args(tsfde_ctx* c, double ahat, const double* b, double* 
   A.k32 = c->k32;
   A.kds = c->kds;
   A.kappads = c->kappads;
+  A.krylov = c->opts.krylov;
+  A.hinv64 = c->hinv64;
+  A.hinv32 = c->hinv32;
+  A.hinvds = c->hinvds;
   A.r64 = c->r64;
   A.stat = st;
   return A;

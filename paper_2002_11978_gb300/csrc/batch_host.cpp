@@ -265,6 +265,8 @@ int tsfde_batch_setup(tsfde_batch** out, int B, const tsfde_instance* inst, int6
   if (opts) o = *opts; else tsfde_default_opts(&o);
   if (o.precision != TSFDE_FP64 && o.precision != TSFDE_MIXED) return TSFDE_EINVAL;
   if (o.history == TSFDE_HISTORY_DIRECT) return TSFDE_ENOTSUP;  // FIDS only
+  if (o.krylov == TSFDE_KRYLOV_PCG) return TSFDE_ENOTSUP;        // BiCGSTAB only
+  if (o.krylov != TSFDE_KRYLOV_BICGSTAB) return TSFDE_EINVAL;
   if (o.history != TSFDE_HISTORY_SOE) return TSFDE_EINVAL;
   if (o.precond != TSFDE_STRANG && o.precond != TSFDE_PRECOND_NONE) return TSFDE_EINVAL;
   if (!(o.krylov_tol > 0.0) || o.max_it < 1) return TSFDE_EINVAL;

@@ -626,6 +626,167 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
   }
 }
 
+// ------------------------------------------------------------------ PCG
+// Preconditioned conjugate gradients on the symmetrised level system.
+// Sec. 4.2 proposes PCG for kappa(x, t) = kappa(t), where the level matrix
+// itself is SPD.  For a general kappa, with K = diag(kappa) > 0,
+// (ahat I + K A) x = b is equivalent to S x = K^{-1} b with
+// S = ahat K^{-1} + A, which is symmetric positive definite (A is, by the
+// proposition after Eq. (3.16x); ahat K^{-1} is a positive diagonal), so CG
+// applies with the SPD circulant preconditioner
+// ahat/kbar I + s(A) = (ahat I + kbar s(A))/kbar: the Strang preconditioner
+// of Eq. (4.3) up to a constant factor, which leaves the CG iterates
+// unchanged, so its spectrum tables serve as they are.  One product with A
+// and one with P^{-1} per iteration (BiCGSTAB needs two of each).  The
+// residual r of S relates to the original one by b - (ahat I + K A) x =
+// K r, and the stopping test is on that: ||K r|| < tol ||b||, the same
+// criterion as bicgstab's.  hinv = 1/kappa.  Per iteration six grid phases:
+// p = z + beta p with its forward column FFTs | row pass (A) | q = S p,
+// (p, q) | x += alpha p, r -= alpha q, ||K r||, forward column FFTs of r |
+// row pass (P^{-1}) | z = P^{-1} r, (r, z).
+template <typename R, class BInit, int KP = kPre>
+__device__ SolveRes pcg(const DevPlan& P, const Smem<R>& sm, const KVecs<R>& V,
+                        const R* __restrict__ kap, const R* __restrict__ hinv, double ahat,
+                        bool prec, double tol, int max_it, BInit& binit) {
+  const int n = P.n;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gstr = gridDim.x * blockDim.x;
+  const R a = (R)ahat;
+  SolveRes out{TSFDE_OK, 0, 0.0};
+  // x = 0, r = K^{-1} b (and its forward column FFTs), ||b||
+  {
+    R acc = 0;
+    auto pro = [&](int i) -> R {
+      const R bi = binit(i);
+      const R ri = bi * hinv[i];
+      V.x[i] = R(0);
+      V.r[i] = ri;
+      acc += bi * bi;
+      return ri;
+    };
+    if (prec) {
+      passA_real<R, false, KP>(P, sm, n, pro);
+    } else {
+      for (int i = gtid; i < n; i += gstr) pro(i);
+    }
+    put_partial(P, SL_BB, block_sum((double)acc, sm.red));
+  }
+  double bb;
+  if (!gsync_sum(P, sm.red, SL_BB, bb)) { out.status = TSFDE_ETIMEOUT; return out; }
+  if (!isfinite(bb)) { out.status = TSFDE_ENONFINITE; return out; }
+  if (bb == 0.0) return out;
+  const double nb = sqrt(bb);
+  // z = P^{-1} r (the forward column FFTs of r are in S1), rho = (r, z)
+  auto precond = [&](double& rho_out) -> bool {
+    R acc = 0;
+    if (prec) {
+      passB<R, MID_APPLY, KP>(P, sm, saG<R>(P), sbG<R>(P), nullptr, nullptr, nullptr);
+      if (!gsync(P, sm.red)) return false;
+      auto epi = [&](int i, R y) -> R {
+        V.s[i] = y;
+        acc += V.r[i] * y;
+        return R(0);
+      };
+      passCA_real<R, false, KP>(P, sm, epi);
+    } else {
+      for (int i = gtid; i < n; i += gstr) {
+        const R ri = V.r[i];
+        V.s[i] = ri;
+        acc += ri * ri;
+      }
+    }
+    put_partial(P, SL_RR0, block_sum((double)acc, sm.red));
+    return gsync_sum(P, sm.red, SL_RR0, rho_out);
+  };
+  double rho;
+  if (!precond(rho)) { out.status = TSFDE_ETIMEOUT; return out; }
+  double rr = bb, beta = 0.0;
+  int it = 0;
+  for (;;) {
+    const double relres = sqrt(rr) / nb;
+    out.relres = relres;
+    out.iters = it;
+    if (!isfinite(relres) || !isfinite(rho)) { out.status = TSFDE_ENONFINITE; return out; }
+    if (relres < tol) return out;
+    if (it >= max_it) { out.status = TSFDE_ENOCONV; return out; }
+    if (!(rho > 0.0)) { out.status = TSFDE_EBREAKDOWN; return out; }
+    ++it;
+    // p = z + beta p, forward column FFTs of p
+    {
+      const R bR = (R)beta;
+      auto pro = [&](int i) -> R {
+        const R pi = V.s[i] + bR * V.p[i];
+        V.p[i] = pi;
+        return pi;
+      };
+      passA_real<R, false, KP>(P, sm, n, pro);
+    }
+    if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
+    passB<R, MID_APPLY, KP>(P, sm, saT<R>(P), sbT<R>(P), nullptr, nullptr, nullptr);
+    if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
+    // q = S p = ahat K^{-1} p + A p, (p, q)
+    {
+      R acc = 0;
+      auto epi = [&](int i, R y) -> R {
+        const R pi = V.p[i];
+        const R qi = a * hinv[i] * pi + y;
+        V.v[i] = qi;
+        acc += pi * qi;
+        return R(0);
+      };
+      passCA_real<R, false, KP>(P, sm, epi);
+      put_partial(P, SL_RV, block_sum((double)acc, sm.red));
+    }
+    double pq;
+    if (!gsync_sum(P, sm.red, SL_RV, pq)) { out.status = TSFDE_ETIMEOUT; return out; }
+    if (!isfinite(pq)) { out.status = TSFDE_ENONFINITE; return out; }
+    if (!(pq > 0.0)) { out.status = TSFDE_EBREAKDOWN; return out; }
+    const double alpha = rho / pq;
+    // x += alpha p, r -= alpha q, ||K r||^2, forward column FFTs of r
+    {
+      const R aR = (R)alpha;
+      R acc = 0;
+      auto pro = [&](int i) -> R {
+        V.x[i] = V.x[i] + aR * V.p[i];
+        const R ri = V.r[i] - aR * V.v[i];
+        V.r[i] = ri;
+        const R kr = kap[i] * ri;
+        acc += kr * kr;
+        return ri;
+      };
+      if (prec) {
+        passA_real<R, false, KP>(P, sm, n, pro);
+      } else {
+        for (int i = gtid; i < n; i += gstr) pro(i);
+      }
+      put_partial(P, SL_RR, block_sum((double)acc, sm.red));
+    }
+    if (!gsync_sum(P, sm.red, SL_RR, rr)) { out.status = TSFDE_ETIMEOUT; return out; }
+    if (sqrt(rr) / nb < tol) {
+      out.relres = sqrt(rr) / nb;
+      out.iters = it;
+      if (!isfinite(out.relres)) out.status = TSFDE_ENONFINITE;
+      return out;
+    }
+    double rho_new;
+    if (!precond(rho_new)) { out.status = TSFDE_ETIMEOUT; return out; }
+    beta = rho_new / rho;
+    rho = rho_new;
+  }
+}
+
+// The Krylov solve of a level, (ahat I + K A) x = b in arithmetic R: PCG on
+// the symmetrised system, or the paper's BiCGSTAB (hinv unused).
+template <bool PCG, int KP, typename R, class BInit>
+__device__ SolveRes level_krylov(const DevPlan& P, const Smem<R>& sm, const KVecs<R>& V,
+                                 const R* __restrict__ kap, const R* __restrict__ hinv, double ahat,
+                                 bool prec, double tol, int max_it, BInit& binit) {
+  if constexpr (PCG)
+    return pcg<R, BInit, KP>(P, sm, V, kap, hinv, ahat, prec, tol, max_it, binit);
+  else
+    return bicgstab<R, BInit, false, KP>(P, sm, V, kap, ahat, prec, tol, max_it, binit);
+}
+
 static __device__ double mean_kappa(const DevPlan& P, const double* kap, double* red) {
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int gstr = gridDim.x * blockDim.x;
@@ -694,8 +855,9 @@ static __device__ bool warm_residual(const LevelArgs& A, SmemAll& S, double& bb,
 // 100 tol max|u|.  After three sweeps
 // without progress above that, or at max_outer, the level is finished by
 // FP64 PBiCGSTAB on the remaining residual, so a level never returns an
-// unconverged answer.
-template <typename RI, class Conv, class Inner>
+// unconverged answer.  PCG selects the Krylov method of that FP64 finish
+// (the inner solves choose their own).
+template <bool PCG = false, typename RI, class Conv, class Inner>
 __device__ void mixed_level(const LevelArgs& A, SmemAll& S, Conv& conv, Inner& inner, const RI* e) {
   const DevPlan& P = A.P;
   const int n = P.n;
@@ -812,8 +974,8 @@ __device__ void mixed_level(const LevelArgs& A, SmemAll& S, Conv& conv, Inner& i
     KVecs<double> V = A.k64;
     auto binit = [&](int i) -> double { return A.r64[i]; };
     const double tol_d = fmax(A.tol * nb / nr, 1e-14);
-    SolveRes fr = bicgstab<double>(P, S.d, V, A.kappa64, A.ahat, A.precond != 0, tol_d,
-                                   A.max_it, binit);
+    SolveRes fr = level_krylov<PCG, kPre>(P, S.d, V, A.kappa64, A.hinv64, A.ahat, A.precond != 0,
+                                          tol_d, A.max_it, binit);
     if (fr.status == TSFDE_OK) {
       for (int i = gtid; i < n; i += gstr) A.u[i] += V.x[i];
       relres = fr.relres * nr / nb;

@@ -301,9 +301,12 @@ static size_t g_smem_limit = 0;
 static cudaError_t set_attrs(size_t smem) {
   cudaError_t e = cudaSuccess;
   if (smem <= g_smem_limit) return e;
-  const void* ks[] = {level64_kernel(2), level64_kernel(4), level32_kernel(2), level32_kernel(4),
-                      levelds_kernel(2), levelds_kernel(4), (const void*)k_apply64,
-                      (const void*)k_apply32, (const void*)k_apply_ds, level_adj_kernel()};
+  const void* ks[] = {level64_kernel(2, 0), level64_kernel(4, 0), level32_kernel(2, 0),
+                      level32_kernel(4, 0), levelds_kernel(2, 0), levelds_kernel(4, 0),
+                      level64_kernel(2, 1), level64_kernel(4, 1), level32_kernel(2, 1),
+                      level32_kernel(4, 1), levelds_kernel(2, 1), levelds_kernel(4, 1),
+                      (const void*)k_apply64, (const void*)k_apply32, (const void*)k_apply_ds,
+                      level_adj_kernel()};
   for (const void* k : ks) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -315,9 +318,12 @@ static cudaError_t set_attrs(size_t smem) {
 int coop_blocks_per_sm(size_t smem) {
   if (set_attrs(smem) != cudaSuccess) return 0;
   int best = 1 << 30;
-  const void* ks[] = {level64_kernel(2), level64_kernel(4), level32_kernel(2), level32_kernel(4),
-                      levelds_kernel(2), levelds_kernel(4), (const void*)k_apply64,
-                      (const void*)k_apply32, (const void*)k_apply_ds, level_adj_kernel()};
+  const void* ks[] = {level64_kernel(2, 0), level64_kernel(4, 0), level32_kernel(2, 0),
+                      level32_kernel(4, 0), levelds_kernel(2, 0), levelds_kernel(4, 0),
+                      level64_kernel(2, 1), level64_kernel(4, 1), level32_kernel(2, 1),
+                      level32_kernel(4, 1), levelds_kernel(2, 1), levelds_kernel(4, 1),
+                      (const void*)k_apply64, (const void*)k_apply32, (const void*)k_apply_ds,
+                      level_adj_kernel()};
   for (const void* k : ks) {
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, smem) != cudaSuccess) return 0;
@@ -358,9 +364,10 @@ cudaError_t launch_level(const LevelArgs& a, int precision, cudaStream_t s) {
   void* args[] = {(void*)&a};
   const bool kp2 = kp_fits(a.P, 2);
   const int kp = kp2 ? 2 : 4;
-  const void* k = precision == TSFDE_MIXED_DS ? levelds_kernel(kp)
-                  : precision == TSFDE_MIXED  ? level32_kernel(kp)
-                                              : level64_kernel(kp);
+  const int pcg = a.krylov == TSFDE_KRYLOV_PCG ? 1 : 0;
+  const void* k = precision == TSFDE_MIXED_DS ? levelds_kernel(kp, pcg)
+                  : precision == TSFDE_MIXED  ? level32_kernel(kp, pcg)
+                                              : level64_kernel(kp, pcg);
   return cudaLaunchCooperativeKernel(k, dim3(a.P.G), dim3(kThreads), args, smem, s);
 }
 

@@ -1,0 +1,133 @@
+// levels.cuh -- the level kernels of the grid engine, templated on the
+// prefetch depth KP of their Krylov passes (see kPre) and on the Krylov
+// method: PCG (CG on the symmetrised system, see pcg in grid.cuh) or the
+// paper's right-preconditioned BiCGSTAB.  Each (arithmetic, method) pair is
+// instantiated in a translation unit of its own (level64.cu,
+// level64_pcg.cu, level32.cu, level32_pcg.cu, levelds.cu, levelds_pcg.cu)
+// so that they compile in parallel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "../../include/tsfde.h"
+#include "dev.cuh"
+#include "grid.cuh"
+#include "plan.h"
+
+namespace tsfde {
+
+// FP64 level solve: preconditioner build and the Krylov solve, all in FP64.
+template <int KP, bool PCG>
+__global__ void __launch_bounds__(kThreads, 2) k_level64(LevelArgs A) {
+  const DevPlan& P = A.P;
+  if (!kp_fits(P, KP)) { write_stat(A.stat, TSFDE_EINVAL, 0, 0, 0.0); return; }
+  SmemAll S = smem_setup(P);
+  if constexpr (PCG) {
+    // 1/kappa for the symmetrised system; ordered by mean_kappa's barrier
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x)
+      A.hinv64[i] = 1.0 / A.kappa64[i];
+  }
+  const double kbar = mean_kappa(P, A.kappa64, S.d.red);
+  if (kbar < 0.0) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
+  if (A.precond && !build_precond<double>(P, S.d, A.ahat, kbar)) {
+    write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0);
+    return;
+  }
+  if (!A.u_prev) {
+    KVecs<double> V = A.k64;
+    V.x = A.u;
+    auto binit = [&](int i) -> double { return A.b[i]; };
+    SolveRes r = level_krylov<PCG, KP>(P, S.d, V, A.kappa64, A.hinv64, A.ahat, A.precond != 0,
+                                       A.tol, A.max_it, binit);
+    write_stat(A.stat, r.status, r.iters, 0, r.relres);
+    return;
+  }
+  // warm start: solve M d = b - M u_prev to ||r|| < tol ||b||, u = u_prev + d
+  double bb, rr;
+  if (!warm_residual(A, S, bb, rr)) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
+  if (!isfinite(bb) || !isfinite(rr)) { write_stat(A.stat, TSFDE_ENONFINITE, 0, 0, 0.0); return; }
+  if (bb == 0.0 || rr == 0.0) { write_stat(A.stat, TSFDE_OK, 0, 0, 0.0); return; }
+  const double scale = sqrt(rr / bb);
+  KVecs<double> V = A.k64;  // V.x: the correction d
+  auto binit = [&](int i) -> double { return A.r64[i]; };
+  SolveRes r = level_krylov<PCG, KP>(P, S.d, V, A.kappa64, A.hinv64, A.ahat, A.precond != 0,
+                                     A.tol / scale, A.max_it, binit);
+  if (r.status == TSFDE_OK) {
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int i = gtid; i < P.n; i += gridDim.x * blockDim.x) A.u[i] += V.x[i];
+  }
+  write_stat(A.stat, r.status, r.iters, 0, r.relres * scale);
+}
+
+// Mixed level solve on the grid engine: the refinement loop of mixed_level
+// (grid.cuh) with the FP32 inner solve spread over the whole cooperative grid.
+template <int KP, bool PCG>
+__global__ void __launch_bounds__(kThreads, 2) k_level_mixed(LevelArgs A) {
+  const DevPlan& P = A.P;
+  if (!kp_fits(P, KP)) { write_stat(A.stat, TSFDE_EINVAL, 0, 0, 0.0); return; }
+  SmemAll S = smem_setup(P);
+  auto conv = [&](int k) {
+    if (PCG && k < P.n) {
+      const double h = 1.0 / A.kappa64[k];
+      A.hinv64[k] = h;
+      A.hinv32[k] = (float)h;
+    }
+    if (!A.precond) return;
+    P.saG32[k] = (float)P.saG64[k];
+    P.sbG32[k] = (float)P.sbG64[k];
+  };
+  auto inner = [&](double sc, double, SolveRes& ir) -> bool {
+    auto binit = [&](int i) -> float { return (float)(A.r64[i] * sc); };
+    ir = level_krylov<PCG, KP>(P, S.f, A.k32, A.kappa32, A.hinv32, A.ahat, A.precond != 0,
+                               A.inner_tol, A.inner_max_it, binit);
+    return ir.status != TSFDE_ETIMEOUT;
+  };
+  mixed_level<PCG>(A, S, conv, inner, A.k32.x);
+}
+
+// Mixed level solve with the inner solve in double-single arithmetic
+// (dsf.cuh): the same refinement loop, every inner vector, product and
+// scalar update carried as FP32 pairs.  kappa^m (and 1/kappa^m for PCG) and
+// the preconditioner spectrum are rounded from FP64 once per level.  With
+// ~48 bits the inner solve resolves the operator, but its true residual
+// cannot go below ~u_ds ||M|| ||u|| (u_ds ~ 2^-47), which at the late levels
+// of large problems is above tol ||b||.  So the first sweep stops near that
+// floor, at kFirstSweep tol ||b|| (never asking for less than a 10x
+// reduction), and every later sweep asks for the whole remaining reduction
+// (half the target), within max_it iterations and not below 1e-13.  A
+// level takes one long sweep and a short one that restarts from the true
+// FP64 residual.
+constexpr double kFirstSweep = 100.0;
+
+template <int KP, bool PCG>
+__global__ void __launch_bounds__(kThreads, 2) k_level_mixed_ds(LevelArgs A) {
+  const DevPlan& P = A.P;
+  if (!kp_fits(P, KP)) { write_stat(A.stat, TSFDE_EINVAL, 0, 0, 0.0); return; }
+  SmemAll S = smem_setup(P);
+  auto conv = [&](int k) {
+    if (k < P.n) {
+      A.kappads[k] = dsf(A.kappa64[k]);
+      if (PCG) {
+        const double h = 1.0 / A.kappa64[k];
+        A.hinv64[k] = h;
+        A.hinvds[k] = dsf(h);
+      }
+    }
+    if (!A.precond) return;
+    P.saGds[k] = dsf(P.saG64[k]);
+    P.sbGds[k] = dsf(P.sbG64[k]);
+  };
+  int sweep = 0;
+  auto inner = [&](double sc, double target, SolveRes& ir) -> bool {
+    auto binit = [&](int i) -> dsf { return dsf(A.r64[i] * sc); };
+    const double tin = sweep++ == 0 ? fmax(fmin(kFirstSweep * target, 0.1), 1e-13)
+                                    : fmax(0.5 * target, 1e-13);
+    ir = level_krylov<PCG, KP>(P, S.s, A.kds, A.kappads, A.hinvds, A.ahat, A.precond != 0, tin,
+                               A.max_it, binit);
+    return ir.status != TSFDE_ETIMEOUT;
+  };
+  mixed_level<PCG>(A, S, conv, inner, A.kds.x);
+}
+
+}  // namespace tsfde

@@ -162,6 +162,10 @@ struct LevelArgs {
   KVecs<float> k32;
   KVecs<dsf> kds;     // double-single inner solver (TSFDE_MIXED_DS)
   dsf* kappads;       // kappa^m rounded to double-single (written by the level kernel)
+  int krylov;         // TSFDE_KRYLOV_BICGSTAB or TSFDE_KRYLOV_PCG
+  double* hinv64;     // PCG: 1/kappa^m in FP64 (n), FP32 and double-single (ld),
+  float* hinv32;      //   written by the level kernel
+  dsf* hinvds;
   double* r64;        // mixed: FP64 residual
   StepStat* stat;
   int probe;          // cluster engine: return at once (launch check)
@@ -287,10 +291,12 @@ cudaError_t launch_rhs(const RhsArgs& a, cudaStream_t s);
 cudaError_t launch_rhs_direct(const RhsArgs& a, cudaStream_t s);
 // precision: TSFDE_FP64, TSFDE_MIXED (FP32 inner) or TSFDE_MIXED_DS
 cudaError_t launch_level(const LevelArgs& a, int precision, cudaStream_t s);
-// level kernels by prefetch depth kp (2 or 4): level64.cu, level32.cu, levelds.cu
-const void* level64_kernel(int kp);
-const void* level32_kernel(int kp);
-const void* levelds_kernel(int kp);
+// level kernels by prefetch depth kp (2 or 4) and Krylov method (pcg = 1:
+// PCG on the symmetrised system, 0: BiCGSTAB): level64*.cu, level32*.cu,
+// levelds*.cu
+const void* level64_kernel(int kp, int pcg);
+const void* level32_kernel(int kp, int pcg);
+const void* levelds_kernel(int kp, int pcg);
 const void* level_adj_kernel();
 // cluster engine (cluster.cu): mixed level solve with the FP32 inner solves
 // on one thread-block cluster; a.P.G must equal a.P.cl.G.

@@ -120,3 +120,32 @@ def test_batch_rejects_direct_history(lib):
     b = ctypes.c_void_p()
     assert lib.tsfde_batch_setup(ctypes.byref(b), 1, inst, 8, ctypes.byref(o)) == pkg.TSFDE_ENOTSUP
     assert not b
+
+
+def test_setup_validates_krylov(lib):
+    """An unknown method is refused, and PCG with the cluster engine (which
+    runs BiCGSTAB only) is not supported; both before any device work."""
+    import paper_2002_11978_gb300 as pkg
+    ctx = ctypes.c_void_p()
+    o = pkg.default_opts()
+    assert o.krylov == pkg.TSFDE_KRYLOV_BICGSTAB
+    o.krylov = 4
+    assert lib.tsfde_setup(ctypes.byref(ctx), 1.5, 0.5, 1.0, 1.0, 7, 4, 3.0, 1e-12,
+                           ctypes.byref(o)) == pkg.TSFDE_EINVAL
+    o = pkg.default_opts()
+    o.krylov = pkg.TSFDE_KRYLOV_PCG
+    o.precision = pkg.TSFDE_MIXED
+    o.engine = pkg.TSFDE_ENGINE_CLUSTER
+    assert lib.tsfde_setup(ctypes.byref(ctx), 1.5, 0.5, 1.0, 1.0, 7, 4, 3.0, 1e-12,
+                           ctypes.byref(o)) == pkg.TSFDE_ENOTSUP
+    assert not ctx
+
+
+def test_batch_rejects_pcg(lib):
+    import paper_2002_11978_gb300 as pkg
+    o = pkg.default_opts()
+    o.krylov = pkg.TSFDE_KRYLOV_PCG
+    inst = (pkg.tsfde_instance * 1)()
+    inst[0] = pkg.tsfde_instance(1.5, 0.5, 1.0, 1.0, 3.0, 63, 1e-12, None, None, None)
+    b = ctypes.c_void_p()
+    assert lib.tsfde_batch_setup(ctypes.byref(b), 1, inst, 8, ctypes.byref(o)) == pkg.TSFDE_ENOTSUP

@@ -1,0 +1,156 @@
+"""GPU parity of the PCG level solver (krylov = "pcg": conjugate gradients on
+the symmetrised system (ahat K^{-1} + A) x = K^{-1} b, preconditioned by the
+Strang circulant of Eq. (4.3) up to a constant) in FP64 and in both mixed
+arithmetics: against dense LU, the oracle's marches, and the paper's
+BiCGSTAB path."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import tsfde_inputs as ti
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+    assert T.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2002_11978_gb300 import build
+    build.build()
+    return T
+
+
+def cuda(torch, a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def solver(alpha=1.5, gamma=0.5, n=127, M=8, r=3.0, **kw):
+    import paper_2002_11978_gb300 as pkg
+    return pkg.Solver(alpha, gamma, 1.0, 1.0, n, M, r, kw.pop("soe_tol", 1e-12), krylov="pcg", **kw)
+
+
+@pytest.mark.parametrize("n", [1, 2, 63, 127, 1023, 4095])
+@pytest.mark.parametrize("a", [1.0e3, 18.0])
+@pytest.mark.parametrize("precision", ["fp64", "mixed_ds", "mixed"])
+def test_pcg_linear_solve_matches_dense_lu(torch, n, a, precision):
+    """Both solvers stop at ||b - M x|| < 1e-12 ||b||, so x is within
+    cond(M) 1e-12 of the LU solution: 1e-10 up to n = 1023 (as the BiCGSTAB
+    test), 1e-9 at n = 4095, ahat = 18, where cond(M) is ~5e4."""
+    alpha = 1.6
+    s = solver(alpha=alpha, n=n, precision=precision)
+    t = oracle.ifl_symbol(alpha, n)
+    kap = ti.log_minmax(ti.gaussian_field(n, 3), 0.2, 5.0) if n > 2 else np.array([0.4, 2.5])[:n]
+    b = np.random.default_rng(5).standard_normal(n) * 10
+    ref = oracle.lu_solve(a * np.eye(n) + kap[:, None] * oracle.dense_A(t), b)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    info = s.linear_solve(a, cuda(torch, kap), cuda(torch, b), x)
+    err = np.max(np.abs(x.cpu().numpy() - ref)) / np.max(np.abs(ref))
+    assert err < (1e-10 if n <= 1023 else 1e-9), (err, info)
+    assert info["status"] == 0 and info["iterations"] > 0, info
+
+
+def test_pcg_without_preconditioner(torch):
+    n, a, alpha = 127, 50.0, 1.5
+    s = solver(alpha=alpha, n=n, precond="none")
+    t = oracle.ifl_symbol(alpha, n)
+    kap = 1.0 + 0.5 * np.sin(np.pi * ti.interior_nodes(n))
+    b = np.random.default_rng(9).standard_normal(n)
+    ref = oracle.lu_solve(a * np.eye(n) + kap[:, None] * oracle.dense_A(t), b)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    info = s.linear_solve(a, cuda(torch, kap), cuda(torch, b), x)
+    assert np.max(np.abs(x.cpu().numpy() - ref)) / np.max(np.abs(ref)) < 1e-10
+    info_p = solver(alpha=alpha, n=n).linear_solve(a, cuda(torch, kap), cuda(torch, b), x)
+    assert info_p["iterations"] < info["iterations"]
+
+
+@pytest.mark.parametrize("precision,warm,history", [("fp64", False, "soe"), ("fp64", True, "soe"),
+                                                    ("mixed_ds", False, "soe"), ("mixed_ds", True, "soe"),
+                                                    ("mixed", False, "soe"), ("fp64", False, "direct")])
+def test_pcg_march_matches_oracle(torch, precision, warm, history):
+    """n = 127, M = 64: every level within 1e-10 of the oracle's march (FIDS
+    with the oracle's SOE table, or DIDS)."""
+    import paper_2002_11978_gb300 as pkg
+    prob = ti.config_smallest()
+    tm, tau = oracle.graded_mesh(prob.T, prob.M, prob.r)
+    soe = oracle.soe_build(prob.gamma, tau[1], prob.T, prob.soe_tol) if history == "soe" else None
+    s = pkg.Solver(prob.alpha, prob.gamma, prob.l, prob.T, prob.n, prob.M, prob.r, prob.soe_tol,
+                   precision=precision, soe=soe, krylov_tol=prob.krylov_tol, warm_start=warm,
+                   history=history, krylov="pcg")
+    s.set_problem_from(prob)
+    U = torch.zeros((prob.M + 1, prob.n), dtype=torch.float64, device="cuda")
+    uf = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    info = s.solve(uf, U)
+    assert info["status"] == 0, info
+    ref = oracle.march("FIDS" if history == "soe" else "DIDS", prob.alpha, prob.gamma, prob.l, prob.T,
+                       prob.r, prob.n, prob.M, prob.phi, prob.kappa_table(tm), prob.f_table(tm), soe=soe)
+    err = np.max(np.abs(U.cpu().numpy() - ref)) / np.max(np.abs(ref))
+    assert err < 1e-10, (err, info)
+
+
+def _sampled_residual(t, a, kap, u, b, rows):
+    n = len(u)
+    worst = 0.0
+    for i in rows:
+        Au = np.dot(t[np.abs(i - np.arange(n))], u)
+        worst = max(worst, abs(b[i] - (a * u[i] + kap[i] * Au)))
+    return worst / np.max(np.abs(b))
+
+
+def test_pcg_full_size_levels_vs_bicgstab(torch):
+    """n = 2^17 - 1, M = 4096, first 6 levels (x0 = 0): PCG in FP64 and with
+    the double-single mixed solve agree with the paper's FP64 BiCGSTAB to
+    1e-10, and their levels satisfy their equations on 64 rows summed
+    directly with the oracle's symbol.  (These levels have ahat ~1e6, where
+    ahat K^{-1} dominates and the circulant preconditioner of the symmetrised
+    system is weak: PCG takes more iterations there than BiCGSTAB.)"""
+    import paper_2002_11978_gb300 as pkg
+    prob = ti.config_mixed()
+    n, levels = prob.n, 6
+    t = oracle.ifl_symbol(prob.alpha, n)
+    rows = np.random.default_rng(0).choice(n, 64, replace=False)
+    rows[:2] = [0, n - 1]
+    sols, its = {}, {}
+    for key, prec, kry in (("bicg64", "fp64", "bicgstab"), ("pcg64", "fp64", "pcg"), ("pcgds", "mixed_ds", "pcg")):
+        s = pkg.Solver(prob.alpha, prob.gamma, prob.l, prob.T, n, prob.M, prob.r, prob.soe_tol,
+                       precision=prec, krylov_tol=prob.krylov_tol, krylov=kry)
+        s.set_problem_from(prob)
+        u = torch.zeros(n, dtype=torch.float64, device="cuda")
+        rhs = torch.zeros(n, dtype=torch.float64, device="cuda")
+        out, it = [], 0
+        for m in range(1, levels + 1):
+            info = s.step(u_out=u, rhs_out=rhs)
+            assert info["status"] == 0, (key, info)
+            it += info["iterations"]
+            out.append((u.cpu().numpy().copy(), rhs.cpu().numpy().copy()))
+        sols[key], its[key] = out, it
+    for key in ("pcg64", "pcgds"):
+        for (ub, _), (up, _) in zip(sols["bicg64"], sols[key]):
+            assert np.max(np.abs(up - ub)) / np.max(np.abs(ub)) < 1e-10, key
+        for m, (up, bp) in enumerate(sols[key], start=1):
+            ahat_m = oracle.l1_weight(prob.T, prob.M, prob.r, prob.gamma, m, m) / math.gamma(1 - prob.gamma)
+            assert _sampled_residual(t, ahat_m, prob.kappa0, up, bp, rows) < 1e-9, key
+
+
+def test_pcg_mid_size_late_levels(torch):
+    """n = 2^14 - 1, gamma = 0.7, alpha = 1.8 on a 64-level mesh (ahat from
+    ~250 down to ~11, where A dominates and PCG gains most): PCG and
+    BiCGSTAB in FP64 agree to 1e-10 at every level, and PCG takes fewer
+    iterations over the march (each costing half the products)."""
+    import paper_2002_11978_gb300 as pkg
+    prob = ti.config_mid(0.7, 1.8, M=64)
+    out, its = {}, {}
+    for kry in ("bicgstab", "pcg"):
+        s = pkg.Solver(prob.alpha, prob.gamma, prob.l, prob.T, prob.n, prob.M, prob.r, prob.soe_tol,
+                       krylov_tol=prob.krylov_tol, krylov=kry)
+        s.set_problem_from(prob)
+        U = torch.zeros((prob.M + 1, prob.n), dtype=torch.float64, device="cuda")
+        info = s.solve(torch.zeros(prob.n, dtype=torch.float64, device="cuda"), U)
+        assert info["status"] == 0, info
+        out[kry] = U.cpu().numpy()
+        its[kry] = info["iterations"]
+    err = np.max(np.abs(out["pcg"] - out["bicgstab"])) / np.max(np.abs(out["bicgstab"]))
+    assert err < 1e-10, err
+    assert its["pcg"] < its["bicgstab"], its
