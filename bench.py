@@ -154,12 +154,15 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------- our arm
-# DRAM bytes per launch from one ncu capture (profiles/k_level_mixed_ds_n131071_launches_traffic.md),
+# DRAM bytes per launch from one ncu capture (profiles/k_level_mixed_ds_pcg_n131071_launches_traffic.md),
 # valid only for the kernel sources they were taken with: the digest of those sources is kept
 # beside the figure, and a changed source makes the figure null.
-TRAFFIC = {"k_level_mixed_ds": {"bytes": 144.33e6, "note": "dram read+write, levels 9-11, ncu",
-                                "sources": ['grid.cuh', 'levelds.cu', 'dev.cuh', 'dsf.cuh', 'plan.h'],
-                                "sha1": "4945e13e5516bec616f2b8db534e99c7efa881bc"}}
+TRAFFIC = {"k_level_mixed_ds/pcg": {
+    "bytes": 57.72e6,
+    "note": "dram read+write per launch at levels 9-11, ncu; those early levels (ahat ~1e6) take ~60 "
+            "PCG iterations against 22 on average over the march, so an average launch moves less",
+    "sources": ['grid.cuh', 'levels.cuh', 'levelds_pcg.cu', 'dev.cuh', 'dsf.cuh', 'plan.h'],
+    "sha1": "e8c601ddc538ccb76be6a86d1e1152ff88bceb06"}}
 
 
 def measured_traffic(kernel):
