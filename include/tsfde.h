@@ -11,7 +11,9 @@
  *   (a_m/Gamma(1-gamma) I + diag(kappa^m) A) u^m = b^m,
  * where A is the symmetric Toeplitz IFL matrix of Eq. (3.16x) and b^m is
  * built from the sum-of-exponentials history (Lemma 2.2, Eq. (lem2.3)), by
- * Strang-circulant-preconditioned BiCGSTAB (Sec. 4.1, Eq. (4.3); Sec. 5).
+ * Strang-circulant-preconditioned BiCGSTAB (Sec. 4.1, Eq. (4.3); Sec. 5) or,
+ * with tsfde_opts.krylov = TSFDE_KRYLOV_PCG, by preconditioned CG on the
+ * equivalent symmetric positive definite system.
  *
  * Conventions for every entry point:
  *  - Return value: a tsfde_status (0 = TSFDE_OK).  No C++ exception crosses
@@ -42,16 +44,18 @@ typedef enum tsfde_status {
   TSFDE_ENOMEM = 2,      /* device or host allocation failed               */
   TSFDE_ECUDA = 3,       /* a CUDA runtime call failed                     */
   TSFDE_ENOCONV = 4,     /* Krylov iteration cap reached                   */
-  TSFDE_EBREAKDOWN = 5,  /* BiCGSTAB breakdown (rho, (r0,v) or (t,t) = 0)  */
+  TSFDE_EBREAKDOWN = 5,  /* Krylov breakdown: BiCGSTAB rho, (r0,v) or (t,t)
+                            = 0; PCG (p,Sp) or (r,z) not positive          */
   TSFDE_ETIMEOUT = 6,    /* a device-side grid barrier gave up waiting     */
   TSFDE_ESTATE = 7,      /* call not valid in the context's current state  */
   TSFDE_ENONFINITE = 8,  /* NaN or Inf met in a residual or scalar         */
   TSFDE_ENOTSUP = 9      /* option not supported by this build             */
 } tsfde_status;
 
-/* tsfde_opts.precision.  FP64: PBiCGSTAB in FP64.  MIXED and MIXED_DS: FP64
- * iterative refinement (FP64 residual b - M u and update) around an inner
- * PBiCGSTAB that runs in FP32 (MIXED) or in double-single arithmetic
+/* tsfde_opts.precision.  FP64: the Krylov solve (tsfde_opts.krylov) in FP64.
+ * MIXED and MIXED_DS: FP64 iterative refinement (FP64 residual b - M u and
+ * update) around an inner Krylov solve that runs in FP32 (MIXED) or in
+ * double-single arithmetic
  * (MIXED_DS: every value an unevaluated sum of two FP32 numbers, about 48
  * significant bits, computed on the FP32 pipes).  FP32 products cannot
  * resolve a spectral range of ~1e8 (the IFL symbol at n ~ 1e5), so MIXED
@@ -101,7 +105,7 @@ typedef struct tsfde_opts {
                            the last correction max|e| <= tol * max|u|, or a
                            sweep no longer halves the FP64 residual (it has
                            reached its rounding floor).  Default 1e-12      */
-  int max_it;           /* BiCGSTAB iteration cap per solve (default 2000)  */
+  int max_it;           /* Krylov iteration cap per solve (default 2000)    */
   int precision;        /* TSFDE_FP64 (default), TSFDE_MIXED or
                            TSFDE_MIXED_DS                                   */
   int precond;          /* TSFDE_STRANG (default) or TSFDE_PRECOND_NONE     */
@@ -151,10 +155,11 @@ typedef struct tsfde_opts {
 typedef struct tsfde_step_info {
   int64_t m;            /* time level just computed (1..M)                  */
   int status;           /* tsfde_status of this level                       */
-  int iterations;       /* BiCGSTAB iterations (mixed: summed inner ones)   */
+  int iterations;       /* Krylov iterations (mixed: summed inner ones)     */
   int outer;            /* mixed: FP64 refinement sweeps (0 for FP64 path);
                            negative: the level was finished (or, after such
-                           a level, solved directly) by FP64 PBiCGSTAB      */
+                           a level, solved directly) by the FP64 Krylov
+                           solve                                            */
   int E_active;         /* exponentials still non-zero at this level        */
   double rel_residual;  /* FP64 path: recursive ||r||/||b||; mixed: last
                            computed FP64 ||b - M u||/||b||                  */
@@ -164,7 +169,7 @@ typedef struct tsfde_solve_info {
   int status;           /* first non-OK level status, else TSFDE_OK          */
   int64_t failed_level; /* level of that status, 0 if none                  */
   int64_t levels;       /* levels computed by this call                     */
-  int64_t iterations;   /* total BiCGSTAB iterations over those levels      */
+  int64_t iterations;   /* total Krylov iterations over those levels        */
   int min_iterations, max_iterations;
   int64_t outer;        /* total refinement sweeps (mixed)                  */
   double max_rel_residual;
@@ -365,7 +370,8 @@ int tsfde_precond_apply(tsfde_ctx* ctx, double a, double kbar, const double* v,
                         double* z, int precision);
 
 /* Solve (a I + diag(kappa) A) x = b with the level solver selected by the
- * context options (PBiCGSTAB, or mixed refinement).  kappa, b, x: dev n. */
+ * context options (BiCGSTAB or PCG, FP64 or mixed refinement).  kappa, b,
+ * x: dev n. */
 int tsfde_linear_solve(tsfde_ctx* ctx, double a, const double* kappa,
                        const double* b, double* x, tsfde_step_info* info);
 
