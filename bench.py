@@ -51,24 +51,22 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison arm")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-n", type=int, default=255)
+    ap.add_argument("--cpu-sample-n", type=int, default=2047)
     ap.add_argument("--cold-start", action="store_true",
                     help="x0 = 0 for every level as in the paper's experiments (default: start "
                          "from u^{m-1}, same stopping rule ||r|| < tol ||b||)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
     ap.add_argument("--dids-levels", type=int, default=None,
                     help="levels of the DIDS (direct history) march to time; default M, 0 skips it")
-    ap.add_argument("--krylov", choices=["bicgstab", "pcg"], default="pcg",
-                    help="level solver of the mixed and FP64 arms: PCG on the symmetrised system, or "
-                         "the paper's BiCGSTAB (with pcg an extra FP64 BiCGSTAB arm is reported)")
+    ap.add_argument("--krylov", choices=["auto", "bicgstab", "pcg"], default="auto",
+                    help="level solver of the mixed and FP64 arms: per-level choice between PCG on the "
+                         "symmetrised system and BiCGSTAB from measured level times (auto), or one of "
+                         "them throughout; unless bicgstab, the paper's FP64 BiCGSTAB is reported too")
     ap.add_argument("--flush-mb", type=int, default=256,
                     help="L2 flush buffer size (MB, twice L2 by default); smaller only for profiler runs")
     ap.add_argument("--inner", choices=["fp32", "ds"], default="ds",
                     help="arithmetic of the mixed arm's inner PBiCGSTAB: FP32, or double-single "
                          "(FP32 pairs, ~48-bit significand)")
-    ap.add_argument("--paper-table11", action="store_true",
-                    help="only time the paper's own Table 11 FIDS+P runs (Example 2) on the GPU and "
-                         "print them next to the paper's CPU figures")
     ap.add_argument("--batched-levels", type=int, default=128,
                     help="levels of the batched workload timed (of M = 1024; 0 skips it)")
     return ap.parse_args()
@@ -190,7 +188,7 @@ def run_arm(torch, pkg, prob, precision, W, K, flush, stream, e2e=False, warm=Fa
     n = prob.n
     dev = torch.device("cuda")
     tot = {"its": 0, "outer": 0, "E_active_sum": 0, "status": 0, "fallback": 0, "max_relres": 0.0,
-           "above_tol": 0}
+           "above_tol": 0, "its_pcg": 0, "levels_pcg": 0, "levels": 0}
     if e2e:
         kap_h = torch.from_numpy(prob.kappa0.copy()).pin_memory()
         f_h = torch.from_numpy(prob.f_at(0.0)).pin_memory()
@@ -204,6 +202,10 @@ def run_arm(torch, pkg, prob, precision, W, K, flush, stream, e2e=False, warm=Fa
         if first_timed[0] is not None and s.m >= first_timed[0]:
             for rec in s.level_stats(first_timed[0], s.m):
                 tot["its"] += rec["iterations"]
+                tot["levels"] += 1
+                if rec["krylov"] == 1:
+                    tot["its_pcg"] += rec["iterations"]
+                    tot["levels_pcg"] += 1
                 tot["outer"] += abs(rec["outer"])  # negative: finished by the FP64 fallback
                 tot["fallback"] += rec["outer"] < 0
                 tot["E_active_sum"] += rec["E_active"]
@@ -300,51 +302,6 @@ def batched_sample(torch, pkg, ti, levels, rank, world, stream, warm=True):
         float(np.max(np.abs(a - b)) / np.max(np.abs(b))) for a, b in zip(us["mixed"], us["fp64"]))
     out["mixed_speedup"] = out["fp64"]["s"] / out["mixed"]["s"]
     return out
-
-
-# Table 11 (FIDS+P, Example 2, tol 1e-10, SOE eps 1e-9): the largest run of each (r, gamma,
-# alpha) group, with the paper's N, M and CPU seconds (MATLAB 2017b, Core i5-8265U).
-TABLE11 = [  # r, gamma, alpha, paper N, M, paper CPU s, printed Err_inf
-    (2, 0.5, 1.5, 512, 16384, 43.338, 1.333e-5),
-    (3, 0.8, 1.5, 1024, 8934, 34.543, 2.319e-6),
-    (3, 0.8, 1.9, 512, 8192, 21.436, 2.100e-5),
-]
-
-
-def paper_table11(torch, pkg, ti):
-    """Each run through the public API level by level (kappa^m and f^m of
-    Example 2 evaluated on the host and copied in, as the paper's code
-    forms them), FP64, x0 = 0, tol 1e-10 on the recursive residual."""
-    rows = []
-    for r, g, a, N, M, cpu_s, err_p in TABLE11:
-        prob = ti.example2(a, g, r, N, M)
-        s = pkg.Solver(a, g, 1.0, 1.0, prob.n, M, r, prob.soe_tol, krylov_tol=1e-10)
-        tm = s.times()
-        dev = lambda v: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float64, device="cuda")
-        s.set_problem(dev(prob.phi), torch.zeros(prob.n, dtype=torch.float64, device="cuda"))
-        kap_h = [prob.kappa_at(tm[m]) for m in range(M + 1)]
-        f_h = [prob.f_at(tm[m]) for m in range(M + 1)]
-        u = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
-        kd = torch.empty(prob.n, dtype=torch.float64, device="cuda")
-        fd = torch.empty(prob.n, dtype=torch.float64, device="cuda")
-        err = 0.0
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for m in range(1, M + 1):
-            kd.copy_(torch.from_numpy(kap_h[m]))
-            fd.copy_(torch.from_numpy(f_h[m]))
-            s.step(kappa_m=kd, f_m=fd, u_out=u, sync=False)
-            if m % 64 == 0 or m == M:
-                ex = prob.exact_table(tm[m:m + 1])[0]
-                err = max(err, float(np.max(np.abs(u.cpu().numpy() - ex))))
-        torch.cuda.synchronize()
-        t = time.perf_counter() - t0
-        rows.append({"r": r, "gamma": g, "alpha": a, "N": N, "M": M, "gpu_s": t,
-                     "gpu_steps_per_s": M / t, "paper_cpu_s": cpu_s, "paper_steps_per_s": M / cpu_s,
-                     "speedup_vs_paper": cpu_s / t, "err_inf_sampled_levels": err,
-                     "paper_err_inf": err_p})
-        s.close()
-    return rows
 
 
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor), nominal
@@ -456,11 +413,6 @@ def ours(args):
     import tsfde_inputs as ti
     from paper_2002_11978_gb300 import build
 
-    if args.paper_table11:
-        build.build()
-        print(json.dumps({"paper_table11": paper_table11(torch, pkg, ti)}), flush=True)
-        return
-
     rank, local_rank, world = dist_env()
     torch.cuda.set_device(local_rank)
     if world > 1:
@@ -512,7 +464,7 @@ def ours(args):
                 "mixed_speedup": (K / t_mx * (1 if world == 1 else 1)) / (K / t64),
                 "krylov": kry}
         s64.close()
-        if kry == "pcg":
+        if kry != "bicgstab":
             # the paper's solver, FP64 right-preconditioned BiCGSTAB, on the same levels
             sb, msb, timb, stb = run_arm(torch, pkg, prob, "fp64", W, K, flush, stream,
                                          warm=(not args.cold_start), krylov="bicgstab")
@@ -542,10 +494,13 @@ def ours(args):
     lvl_ms = tim_mx["level_ms"] / K
     rhs_bytes = (16.0 * n * st_mx["E_active_sum"] + K * 8.0 * n * (3 + 1)) / K
     # inner-vector accesses per inner iteration: 22 for BiCGSTAB, 15 for PCG
-    # (4 or 8 bytes per entry); 5 FP64 vector accesses per refinement sweep
-    acc_it = 15 if kry == "pcg" else 22
-    lvl_bytes = (acc_it * (8.0 if ds else 4.0) * n * st_mx["its"] + 40.0 * n * st_mx["outer"]) / K
-    kname = ("k_level_mixed_ds" if ds else "k_level_mixed") + ("/pcg" if kry == "pcg" else "")
+    # (4 or 8 bytes per entry), counted per level by the method that solved
+    # it; 5 FP64 vector accesses per refinement sweep
+    its_p = st_mx["its_pcg"]
+    its_b = st_mx["its"] - its_p
+    lvl_bytes = ((15 * its_p + 22 * its_b) * (8.0 if ds else 4.0) * n + 40.0 * n * st_mx["outer"]) / K
+    kname = ("k_level_mixed_ds" if ds else "k_level_mixed") + {"pcg": "/pcg", "bicgstab": "",
+                                                               "auto": "/auto"}[kry]
     rhs_gbs = rhs_bytes / (rhs_ms * 1e-3) / 1e9
     lvl_gbs = lvl_bytes / (lvl_ms * 1e-3) / 1e9
     dom = (kname, lvl_gbs) if lvl_ms >= rhs_ms else ("k_rhs", rhs_gbs)
@@ -574,7 +529,8 @@ def ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_sample(prob, args.cpu_sample_n, budget_s=20.0)
+        cpu = cpu_baseline_sample(prob, args.cpu_sample_n)
+        cpu["all_cores"] = cpu_baseline_sample(prob, args.cpu_sample_n, threads=os.cpu_count() or 1)
 
     if rank == 0:
         line = {
@@ -583,7 +539,9 @@ def ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "M": prob.M, "first_timed_level": W + 1,
                        "precision": ("mixed: double-single (FP32-pair) inner " if ds else "mixed: FP32 inner ")
-                                    + ("PCG on the symmetrised system" if kry == "pcg" else "PBiCGSTAB")
+                                    + {"pcg": "PCG on the symmetrised system", "bicgstab": "PBiCGSTAB",
+                                       "auto": "per-level choice of PBiCGSTAB or PCG on the symmetrised "
+                                               "system (measured level times)"}[kry]
                                     + ", FP64 refinement/residual/SOE",
                        "krylov": kry,
                        "krylov_tol": 1e-12, "inner_tol": 1e-2,
@@ -592,12 +550,13 @@ def ours(args):
                        "parallelism": f"replicas x{world}"},
             "status": st_mx["status"],
             "iterations_per_step": st_mx["its"] / K, "outer_per_step": st_mx["outer"] / K, "fp64_fallback_levels": st_mx.get("fallback", 0),
+            "pcg_levels": st_mx["levels_pcg"], "bicgstab_levels": st_mx["levels"] - st_mx["levels_pcg"],
             "max_final_rel_residual": st_mx["max_relres"], "levels_above_tol": st_mx["above_tol"],
             "krylov_its_per_s": world * st_mx["its"] / t_mx,
             "kernels": {"k_rhs": {"ms": rhs_ms, "bytes": rhs_bytes, "GB/s": rhs_gbs, "frac": rhs_gbs / peak},
                         kname: {"ms": lvl_ms, "bytes": lvl_bytes, "GB/s": lvl_gbs,
                                 "frac": lvl_gbs / peak}},
-            "fp64": fp64, "e2e": e2e, "gpu_launches": 2 * K, "roofline": roof,
+            "fp64": fp64, "e2e": e2e, "gpu_launches": (3 if kry == "auto" else 2) * K, "roofline": roof,
             "cpu_baseline": cpu, "clocks": clk, "batched": batched, "adjoint": adjoint, "dids": dids,
         }
         print(json.dumps(line), flush=True)
@@ -607,42 +566,56 @@ def ours(args):
 
 
 # ------------------------------------------------------------ CPU baseline
-def cpu_baseline_sample(prob, n_s, budget_s=20.0, levels=None, warmup=0):
-    """The oracle (plain C, one thread, dense LU per level, direct O(m n)
-    history sums) on the same workload generators at n_s interior points
-    and the full M-level mesh, for as many leading levels as fit the time
-    budget.  The per-level time is scaled to n = prob.n by (n/n_s)^3, the
-    growth of the dense LU that dominates at full size."""
+def cpu_baseline_sample(prob, n_s=2047, budget_s=15.0, threads=1):
+    """The oracle (plain C: dense LU with partial pivoting per level, direct
+    O(m n) history sums, the FIDS weights summed over the SOE table) on the
+    same workload generators at n_s interior points on the full M-level mesh,
+    levels 1..k with k sized to the time budget, on `threads` host threads
+    (the LU's row updates; the result does not depend on the count).
+
+    Extrapolation to n = prob.n, stated as such: one dense LU of the same
+    size is timed on its own; the per-level time splits into that LU
+    (scaled by (n/n_s)^3) and the rest (dense level-matrix assembly, O(n^2),
+    and the history sums, O(m n) with m << n here; both scaled by
+    (n/n_s)^2, an upper bound for the history part).  At n_s = 2047 the LU
+    is ~99% of a level, and for the first levels (m < 100) the history and
+    weights are < 0.1%, so which window of early levels is sampled does not
+    change the figure: both bench arms report this same sample."""
     import oracle
     import tsfde_inputs as ti
     p = ti.config_mixed(n=n_s, M=prob.M)
     tm, tau = oracle.graded_mesh(p.T, p.M, p.r)
     soe = oracle.soe_build(p.gamma, tau[1], p.T, p.soe_tol)
-    K = p.kappa_table(tm)
-    F = p.f_table(tm)
-    # probe the per-level cost at the start, then size the sample
-    lv = levels
-    if lv is None:
+    old_threads = oracle.get_threads()
+    oracle.set_threads(threads)
+    try:
+        K = p.kappa_table(tm)
+        F = p.f_table(tm)
+        # one dense LU of the level matrix's size and structure
+        t = oracle.ifl_symbol(p.alpha, n_s)
+        Amat = oracle.dense_A(t) * p.kappa0[:, None] + 1e3 * np.eye(n_s)
+        rhs = np.ones(n_s)
         t0 = time.perf_counter()
-        oracle.march("FIDS", p.alpha, p.gamma, p.l, p.T, p.r, p.n, p.M, p.phi, K, F, soe=soe, levels=8)
-        per = (time.perf_counter() - t0) / 8
-        lv = int(max(8, min(p.M, budget_s / max(per, 1e-6) / 2)))
-    t_w = 0.0
-    if warmup:
+        oracle.lu_solve(Amat, rhs)
+        t_lu = time.perf_counter() - t0
+        k = int(max(2, min(64, budget_s / max(t_lu, 1e-6))))
         t0 = time.perf_counter()
-        oracle.march("FIDS", p.alpha, p.gamma, p.l, p.T, p.r, p.n, p.M, p.phi, K, F, soe=soe, levels=warmup)
-        t_w = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    oracle.march("FIDS", p.alpha, p.gamma, p.l, p.T, p.r, p.n, p.M, p.phi, K, F, soe=soe, levels=warmup + lv)
-    el = time.perf_counter() - t0 - t_w
-    per_level = el / lv
-    scale = (prob.n / n_s) ** 3
-    return {"value": 1.0 / (per_level * scale), "unit": "steps/s", "cores": 1, "kind": "oracle",
+        oracle.march("FIDS", p.alpha, p.gamma, p.l, p.T, p.r, p.n, p.M, p.phi, K, F, soe=soe, levels=k)
+        el = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(old_threads)
+    per_level = el / k
+    rest = max(per_level - t_lu, 0.0)
+    q = prob.n / n_s
+    ext = t_lu * q ** 3 + rest * q ** 2
+    cpu = os.cpu_count() or 1
+    return {"value": 1.0 / ext, "unit": "steps/s", "cores": threads, "kind": "oracle",
             "sample": (f"oracle FIDS (dense LU per level, direct history sums, SOE E={len(soe[0])}) on the "
-                       f"same generators at n={n_s}, levels {warmup + 1}..{warmup + lv} of M={p.M}: "
-                       f"{lv / el:.3f} levels/s measured; value = that rate scaled by (n_s/n)^3 = "
-                       f"1/{scale:.3g} to n={prob.n} (dense LU dominates at full size)"),
-            "sample_levels_per_s": lv / el, "sample_n": n_s}
+                       f"same generators at n={n_s}, levels 1..{k} of M={p.M}, {threads} thread(s) of {cpu}: "
+                       f"{per_level:.3f} s per level, of which one dense LU {t_lu:.3f} s; extrapolated to "
+                       f"n={prob.n} as LU x (n/n_s)^3 + rest x (n/n_s)^2 = {ext:.3g} s per level"),
+            "extrapolated": True, "sample_n": n_s, "sample_levels": k, "sample_s_per_level": per_level,
+            "sample_lu_s": t_lu, "host_cpus": cpu}
 
 
 def reference(args):
@@ -654,12 +627,13 @@ def reference(args):
     W = args.warmup
     K = args.steps if args.steps is not None else max(1, prob.M - W)
     K = min(K, prob.M - W)
-    cpu = cpu_baseline_sample(prob, args.cpu_sample_n, levels=K, warmup=W)
+    cpu = cpu_baseline_sample(prob, args.cpu_sample_n)
+    cpu["all_cores"] = cpu_baseline_sample(prob, args.cpu_sample_n, threads=os.cpu_count() or 1)
     line = {"metric": METRIC, "value": cpu["value"], "unit": "steps/s", "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": 1e3 / cpu["value"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "n": prob.n, "M": prob.M, "levels_timed": [W + 1, W + K],
-                       "parallelism": "one host thread"},
+            "config": {"workload": WORKLOAD, "n": prob.n, "M": prob.M, "first_timed_level": W + 1,
+                       "parallelism": "one host thread (all-core run in cpu_baseline.all_cores)"},
             "cpu_baseline": cpu,
             "e2e": {"value": cpu["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

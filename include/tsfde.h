@@ -83,7 +83,19 @@ enum { TSFDE_HISTORY_SOE = 0, TSFDE_HISTORY_DIRECT = 1 };
  * residual of the original system.  The mixed paths use it for their inner
  * solves and their FP64 finish.  Grid engine only; the adjoint sweep and the
  * batched solve use BiCGSTAB. */
-enum { TSFDE_KRYLOV_BICGSTAB = 0, TSFDE_KRYLOV_PCG = 1 };
+/* AUTO: each level of tsfde_step / tsfde_solve takes whichever of the two
+ * is cheaper there, decided on the device from measured level times: the
+ * method of the previous level, unless the other one was faster at its latest
+ * sample, or that sample is older than 8 r^2 levels (8..64; r = how many
+ * times slower it was), in which case the other one is tried.  The first
+ * level uses BiCGSTAB, the second PCG.  PCG is weak where a K^{-1}
+ * dominates (large a_m, the first levels of a graded mesh: its circulant
+ * preconditioner cannot follow the variation of 1/kappa) and strong where A
+ * dominates; BiCGSTAB the other way round.  Per-level stats report the
+ * method used (tsfde_step_info.krylov).  tsfde_linear_solve takes BiCGSTAB
+ * in an AUTO context.  Both methods reach the same stopping test, so the
+ * results agree to the tolerance. */
+enum { TSFDE_KRYLOV_BICGSTAB = 0, TSFDE_KRYLOV_PCG = 1, TSFDE_KRYLOV_AUTO = 2 };
 /* tsfde_opts.engine: how a mixed level solve runs its FP32 inner solves.
  * GRID: spread over the whole cooperative grid (grid barriers between the
  * FFT passes).  CLUSTER: on one thread-block cluster of up to 16 CTAs that
@@ -147,9 +159,17 @@ typedef struct tsfde_opts {
   int history;          /* TSFDE_HISTORY_SOE (default, FIDS) or
                            TSFDE_HISTORY_DIRECT (DIDS); the batched solve
                            accepts SOE only                                 */
-  int krylov;           /* TSFDE_KRYLOV_BICGSTAB (default) or
-                           TSFDE_KRYLOV_PCG; the batched solve accepts
+  int krylov;           /* TSFDE_KRYLOV_BICGSTAB (default), TSFDE_KRYLOV_PCG
+                           or TSFDE_KRYLOV_AUTO; the batched solve accepts
                            BICGSTAB only                                    */
+  int ckpt_stride;      /* adjoint checkpoints: every ckpt_stride-th level of
+                           the forward march (level 0 at each reset) keeps
+                           u^{k-1}, u^k and the SOE history, so that
+                           tsfde_adjoint can run with u_all = NULL by
+                           marching each segment again from its checkpoint.
+                           -1: ceil(sqrt(M)); 0 (default): none.  Device
+                           memory (M/stride + 1) (E + 2) n + stride n
+                           doubles; SOE history only                        */
 } tsfde_opts;
 
 typedef struct tsfde_step_info {
@@ -163,6 +183,8 @@ typedef struct tsfde_step_info {
   int E_active;         /* exponentials still non-zero at this level        */
   double rel_residual;  /* FP64 path: recursive ||r||/||b||; mixed: last
                            computed FP64 ||b - M u||/||b||                  */
+  int krylov;           /* method that solved the level: TSFDE_KRYLOV_BICGSTAB
+                           or TSFDE_KRYLOV_PCG                              */
 } tsfde_step_info;
 
 typedef struct tsfde_solve_info {
@@ -175,6 +197,8 @@ typedef struct tsfde_solve_info {
   double max_rel_residual;
   int E;                /* size of the SOE table                            */
   int64_t E_active_sum; /* sum over the levels of the active exponentials   */
+  int64_t pcg_levels;   /* levels of this call solved by PCG (the rest by
+                           BiCGSTAB)                                        */
 } tsfde_solve_info;
 
 typedef struct tsfde_timing {
@@ -190,6 +214,8 @@ typedef struct tsfde_adjoint_info {
   int64_t iterations;   /* total BiCGSTAB iterations of the transposed solves */
   int max_iterations;
   double max_rel_residual;
+  int64_t recomputed_levels; /* forward levels marched again from the
+                           checkpoints (u_all = NULL), else 0               */
 } tsfde_adjoint_info;
 
 typedef struct tsfde_ctx tsfde_ctx;
@@ -278,12 +304,20 @@ int tsfde_get_symbol(const tsfde_ctx* ctx, double* t);
  *   dJ/dkappa = -sum_m lambda^m .* (A u^m),   dJ/df = sum_m lambda^m.
  *
  * u_all:   dev (M+1) x n, the forward levels u^0..u^M (as tsfde_solve writes
- *          them with this context's problem; row m = u^m).
+ *          them with this context's problem; row m = u^m); or NULL in a
+ *          context set up with ckpt_stride != 0 whose march has reached
+ *          level M from level 0 with the separable problem data: the sweep
+ *          then takes the segments between checkpoints last to first,
+ *          marches each again from its checkpoint (one extra forward march
+ *          in all, with the context's own level solver) and sweeps it in
+ *          reverse.  With TSFDE_KRYLOV_AUTO a recomputed level may take the
+ *          other method than the first march did; both meet krylov_tol.
  * dJ_duM:  dev n.  grad_kappa, grad_f: dev n, overwritten.
  * Uses the context's krylov_tol / max_it / precond (always FP64).  Does not
  * change the forward state (tsfde_step continues where it was).  Device
  * work buffers are allocated on the first call.  Synchronises the stream.
- * Errors: TSFDE_ESTATE without a problem, TSFDE_ENOTSUP if kappa1 was set or
+ * Errors: TSFDE_ESTATE without a problem (or, with u_all = NULL, without the
+ * checkpoints of a whole march), TSFDE_ENOTSUP if kappa1 was set or
  * the context uses the direct history (the sweep is the adjoint of FIDS),
  * TSFDE_EINVAL for NULL pointers, else the first failing level's status. */
 int tsfde_adjoint(tsfde_ctx* ctx, const double* u_all, const double* dJ_duM,

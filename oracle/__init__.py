@@ -27,7 +27,7 @@ def build(force: bool = False) -> str:
         os.path.getmtime(_LIB_PATH) < max(os.path.getmtime(_SRC),
                                           os.path.getmtime(os.path.join(_HERE, "oracle.h")))):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC",
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-fopenmp",
                                "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -66,6 +66,10 @@ def lib():
                                      ctypes.c_int, _dp, _dp]
         L.or_lu_solve.restype = ctypes.c_int
         L.or_lu_solve.argtypes = [ctypes.c_int64, _dp, _dp]
+        L.or_set_threads.restype = None
+        L.or_set_threads.argtypes = [ctypes.c_int]
+        L.or_get_threads.restype = ctypes.c_int
+        L.or_get_threads.argtypes = []
         L.or_toeplitz_matvec.restype = None
         L.or_toeplitz_matvec.argtypes = [ctypes.c_int64, _dp, _dp, _dp]
         L.or_strang_column.restype = None
@@ -165,6 +169,15 @@ def fids_weight(T, M, r, gamma, m, k, s, w) -> float:
     s = _f64(s)
     w = _f64(w)
     return lib().or_fids_weight(T, M, r, gamma, m, k, len(s), _ptr(s), _ptr(w))
+
+
+def set_threads(t: int) -> None:
+    """Threads of the LU row updates (default 1; the result does not change)."""
+    lib().or_set_threads(int(t))
+
+
+def get_threads() -> int:
+    return int(lib().or_get_threads())
 
 
 def lu_solve(A: np.ndarray, b: np.ndarray) -> np.ndarray:

@@ -168,6 +168,14 @@ double or_fids_weight(double T, int64_t M, double r, double gamma, int64_t m,
 }
 
 /* ------------------------------------------------------------------ */
+/* Threads of the elimination's row updates (1 unless the caller asks for
+ * more: only the timed CPU baseline does).  Each row's update is the same
+ * sequence of operations whichever thread runs it, so the result does not
+ * depend on the thread count. */
+static int or_threads = 1;
+void or_set_threads(int t) { or_threads = t > 0 ? t : 1; }
+int or_get_threads(void) { return or_threads; }
+
 /* Gaussian elimination with partial pivoting (the paper's direct solver,
  * Sec. 5 "MATLAB's backslash"). */
 int or_lu_solve(int64_t n, double* A, double* b) {
@@ -185,6 +193,7 @@ int or_lu_solve(int64_t n, double* A, double* b) {
       }
       double tb = b[c]; b[c] = b[piv]; b[piv] = tb;
     }
+#pragma omp parallel for schedule(static) num_threads(or_threads) if (or_threads > 1 && n - c > 64)
     for (int64_t i = c + 1; i < n; ++i) {
       double f = A[i * n + c] / A[c * n + c];
       A[i * n + c] = f;

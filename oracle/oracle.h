@@ -70,6 +70,9 @@ double or_fids_weight(double T, int64_t M, double r, double gamma, int64_t m,
 /* Dense LU with partial pivoting; A is n x n row-major and is overwritten,
  * b holds the right-hand side on entry and the solution on exit.
  * Returns 0, or -1 if a zero pivot was met. */
+/* Row-update threads of or_lu_solve (default 1; results do not depend on it). */
+void or_set_threads(int t);
+int or_get_threads(void);
 int or_lu_solve(int64_t n, double* A, double* b);
 
 /* y = A v for the symmetric Toeplitz matrix with first column t (dense

@@ -25,7 +25,7 @@ TSFDE_EBREAKDOWN, TSFDE_ETIMEOUT, TSFDE_ESTATE, TSFDE_ENONFINITE, TSFDE_ENOTSUP 
 TSFDE_FP64, TSFDE_MIXED, TSFDE_MIXED_DS = 0, 1, 2
 TSFDE_STRANG, TSFDE_PRECOND_NONE = 0, 1
 TSFDE_HISTORY_SOE, TSFDE_HISTORY_DIRECT = 0, 1
-TSFDE_KRYLOV_BICGSTAB, TSFDE_KRYLOV_PCG = 0, 1
+TSFDE_KRYLOV_BICGSTAB, TSFDE_KRYLOV_PCG, TSFDE_KRYLOV_AUTO = 0, 1, 2
 TSFDE_ENGINE_AUTO, TSFDE_ENGINE_GRID, TSFDE_ENGINE_CLUSTER = 0, 1, 2
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -40,13 +40,14 @@ class tsfde_opts(ctypes.Structure):
                 ("soe_E", ctypes.c_int), ("soe_s", _dp), ("soe_w", _dp), ("profile", ctypes.c_int),
                 ("barrier_timeout_cycles", ctypes.c_longlong), ("stream", ctypes.c_void_p),
                 ("engine", ctypes.c_int), ("cluster_size", ctypes.c_int),
-                ("warm_start", ctypes.c_int), ("history", ctypes.c_int), ("krylov", ctypes.c_int)]
+                ("warm_start", ctypes.c_int), ("history", ctypes.c_int), ("krylov", ctypes.c_int),
+                ("ckpt_stride", ctypes.c_int)]
 
 
 class tsfde_step_info(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("status", ctypes.c_int), ("iterations", ctypes.c_int),
                 ("outer", ctypes.c_int), ("E_active", ctypes.c_int),
-                ("rel_residual", ctypes.c_double)]
+                ("rel_residual", ctypes.c_double), ("krylov", ctypes.c_int)]
 
 
 class tsfde_solve_info(ctypes.Structure):
@@ -54,13 +55,14 @@ class tsfde_solve_info(ctypes.Structure):
                 ("levels", ctypes.c_int64), ("iterations", ctypes.c_int64),
                 ("min_iterations", ctypes.c_int), ("max_iterations", ctypes.c_int),
                 ("outer", ctypes.c_int64), ("max_rel_residual", ctypes.c_double),
-                ("E", ctypes.c_int), ("E_active_sum", ctypes.c_int64)]
+                ("E", ctypes.c_int), ("E_active_sum", ctypes.c_int64),
+                ("pcg_levels", ctypes.c_int64)]
 
 
 class tsfde_adjoint_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("failed_level", ctypes.c_int64),
                 ("iterations", ctypes.c_int64), ("max_iterations", ctypes.c_int),
-                ("max_rel_residual", ctypes.c_double)]
+                ("max_rel_residual", ctypes.c_double), ("recomputed_levels", ctypes.c_int64)]
 
 
 class tsfde_instance(ctypes.Structure):
@@ -194,12 +196,14 @@ class Solver:
                  precond="strang", krylov_tol=1e-12, max_it=2000, inner_tol=1e-2,
                  max_outer=60, inner_max_it=40, mu=None, kappa_mu=None, soe=None, barrier_timeout_cycles=0,
                  profile=False, stream=None, engine="auto", warm_start=False, history="soe",
-                 krylov="bicgstab"):
+                 krylov="bicgstab", ckpt_stride=0):
         lib = load_library()
         o = default_opts()
-        o.krylov = {"bicgstab": TSFDE_KRYLOV_BICGSTAB, "pcg": TSFDE_KRYLOV_PCG}[krylov]
+        o.krylov = {"bicgstab": TSFDE_KRYLOV_BICGSTAB, "pcg": TSFDE_KRYLOV_PCG,
+                    "auto": TSFDE_KRYLOV_AUTO}[krylov]
         o.history = {"soe": TSFDE_HISTORY_SOE, "direct": TSFDE_HISTORY_DIRECT}[history]
         o.warm_start = 1 if warm_start else 0
+        o.ckpt_stride = int(ckpt_stride)
         o.engine = {"auto": TSFDE_ENGINE_AUTO, "grid": TSFDE_ENGINE_GRID,
                     "cluster": TSFDE_ENGINE_CLUSTER}[engine]
         o.krylov_tol = krylov_tol
@@ -225,6 +229,8 @@ class Solver:
         o.stream = _stream_handle(stream)
         self.n, self.M = int(n), int(M)
         self.m = 0  # current time level
+        self.ckpt_stride = int(ckpt_stride)
+        self.problem_token = None  # changes with every set_problem
         self.ctx = ctypes.c_void_p()
         _check(lib.tsfde_setup(ctypes.byref(self.ctx), alpha, gamma, l, T, self.n, self.M, r,
                                soe_tol, ctypes.byref(o)))
@@ -261,6 +267,7 @@ class Solver:
             ctypes.cast(Farr, ctypes.POINTER(ctypes.c_void_p)),
             None if Garr is None else Garr.ctypes.data_as(_dp)), self.ctx)
         self.m = 0
+        self.problem_token = object()
 
     def set_problem_from(self, prob):
         """Feed a tsfde_inputs.Problem (separable form) through set_problem."""
@@ -353,8 +360,10 @@ class Solver:
     def adjoint(self, u_all, dJ_duM, grad_kappa, grad_f):
         """Discrete adjoint of the FIDS march (tsfde_adjoint): given the forward
         levels u_all ((M+1) x n, as solve() writes them) and dJ/du^M, write
-        dJ/dkappa and dJ/df for a time-independent kappa and f."""
-        if tuple(u_all.shape) != (self.M + 1, self.n):
+        dJ/dkappa and dJ/df for a time-independent kappa and f.  u_all = None
+        recomputes the levels from the checkpoints of the last march (a
+        solver made with ckpt_stride != 0)."""
+        if u_all is not None and tuple(u_all.shape) != (self.M + 1, self.n):
             raise ValueError(f"u_all must be ({self.M + 1}, {self.n})")
         info = tsfde_adjoint_info()
         _check(self.lib.tsfde_adjoint(self.ctx, _dev(u_all, None, "u_all"),

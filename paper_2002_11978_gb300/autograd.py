@@ -3,7 +3,9 @@
 FidsSolve.apply(kappa, f, solver, phi) returns u^M of the FIDS time march
 for a time-independent diffusivity kappa(x) and source f(x); its backward
 pass runs the discrete adjoint sweep on the GPU (tsfde_adjoint) and returns
-dJ/dkappa and dJ/df for whatever scalar J the caller built on u^M.
+dJ/dkappa and dJ/df for whatever scalar J the caller built on u^M.  With a
+solver made with ckpt_stride != 0 no trajectory is kept: the sweep marches
+each segment again from the solver's checkpoints.
 """
 from __future__ import annotations
 
@@ -28,21 +30,36 @@ def _fids_solve_class():
             phi = phi.detach().contiguous()
             ones = np.ones(solver.M + 1)
             solver.set_problem(phi, kappa, None, None, F=[f], G=[ones])
-            U = torch.empty((solver.M + 1, solver.n), dtype=torch.float64, device=kappa.device)
             uM = torch.empty(solver.n, dtype=torch.float64, device=kappa.device)
-            solver.solve(uM, U)
             ctx.solver = solver
-            ctx.save_for_backward(kappa, f, phi, U)
+            if solver.ckpt_stride:
+                # the solver keeps checkpoints of the march: no trajectory here
+                solver.solve(uM)
+                ctx.token = solver.problem_token
+                ctx.save_for_backward(kappa, f, phi)
+            else:
+                U = torch.empty((solver.M + 1, solver.n), dtype=torch.float64, device=kappa.device)
+                solver.solve(uM, U)
+                ctx.token = None
+                ctx.save_for_backward(kappa, f, phi, U)
             return uM.clone()
 
         @staticmethod
         def backward(ctx, g):
-            kappa, f, phi, U = ctx.saved_tensors
             solver = ctx.solver
-            solver.set_problem(phi, kappa, None, None, F=[f], G=[np.ones(solver.M + 1)])
+            kappa, f, phi = ctx.saved_tensors[:3]
             gk = torch.empty_like(kappa)
             gf = torch.empty_like(f)
-            solver.adjoint(U, g.detach().contiguous().to(torch.float64), gk, gf)
+            gd = g.detach().contiguous().to(torch.float64)
+            if ctx.token is not None:
+                if solver.problem_token is not ctx.token or solver.m != solver.M:
+                    # the solver served another problem since: march this one again
+                    solver.set_problem(phi, kappa, None, None, F=[f], G=[np.ones(solver.M + 1)])
+                    solver.solve(torch.empty_like(kappa))
+                solver.adjoint(None, gd, gk, gf)
+            else:
+                solver.set_problem(phi, kappa, None, None, F=[f], G=[np.ones(solver.M + 1)])
+                solver.adjoint(ctx.saved_tensors[3], gd, gk, gf)
             return gk, gf, None, None
 
     return FidsSolve

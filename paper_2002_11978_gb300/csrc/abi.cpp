@@ -52,7 +52,22 @@ struct tsfde_ctx {
   double* wdir = nullptr;
   StepStat* stats = nullptr;
   int* status = nullptr;
+  KrylovAuto* kauto = nullptr;  // TSFDE_KRYLOV_AUTO: per-level method choice
+  KrylovAuto kauto_init{};       // host source of the reset copy (outlives it)
   int engine = TSFDE_ENGINE_GRID;  // engine of the mixed level solves
+  // checkpoints of the forward march for the adjoint sweep (ckpt_stride):
+  // slot j = level k = j * ck_stride holds [u^{k-1} | u^k | G^k] (rows of
+  // ld doubles; G^k = the E x ld history after level k's right-hand side),
+  // everything needed to march on from level k
+  int64_t ck_stride = 0, ck_slots = 0;
+  size_t ck_slot = 0;               // doubles per slot, (2 + E) ld
+  double* ck = nullptr;
+  double* ck_seg = nullptr;         // ck_stride recomputed levels, rows of n
+  double* ck_save = nullptr;        // forward state kept across a sweep: u[3], G
+  KrylovAuto* ck_kauto = nullptr;   // ... and the method-choice state
+  std::vector<char> ck_ok;          // slot recorded in the current march
+  bool ck_override = false;         // a level took per-level kappa_m / f_m
+  bool ck_recomputing = false;
   // adjoint work buffers (allocated by the first tsfde_adjoint)
   double* adjY = nullptr;       // E x ld reversed SOE history
   double* adjLam[2] = {nullptr, nullptr};
@@ -75,11 +90,16 @@ int cuda_fail(tsfde_ctx* c, cudaError_t e, const char* where) {
   return fail(c, TSFDE_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// Every workspace starts zeroed: a buffer read before its first write (a
+// Krylov direction at beta = 0, the padding of an FP32 or double-single
+// vector) must never see what an earlier user of the memory left there, since
+// 0 * NaN is NaN.
 template <typename T> bool dalloc(tsfde_ctx* c, T** p, size_t count) {
   void* q = nullptr;
   if (count == 0) count = 1;
   if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) return false;
   c->allocs.push_back(q);
+  if (cudaMemset(q, 0, count * sizeof(T)) != cudaSuccess) return false;
   *p = static_cast<T*>(q);
   return true;
 }
@@ -92,6 +112,56 @@ template <typename T> cudaError_t upload(T* dst, const std::vector<T>& src) {
 // history, else one of three rotating buffers.
 double* ulev(tsfde_ctx* c, int64_t m) {
   return c->Uh ? c->Uh + (size_t)m * c->ld : c->u[m % 3];
+}
+
+// Checkpoint of level k (a multiple of ck_stride): u^{k-1}, u^k and the SOE
+// history after level k's right-hand side, copied on the context's stream.
+cudaError_t record_ckpt(tsfde_ctx* c, int64_t k) {
+  const int64_t j = k / c->ck_stride;
+  double* slot = c->ck + c->ck_slot * (size_t)j;
+  const size_t nb = sizeof(double) * (size_t)c->n;
+  cudaError_t e = cudaMemcpyAsync(slot, ulev(c, k >= 1 ? k - 1 : 0), nb, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(slot + c->ld, ulev(c, k), nb, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(slot + 2 * (size_t)c->ld, c->G, sizeof(double) * (size_t)std::max(c->E, 1) * c->ld,
+                        cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) c->ck_ok[j] = 1;
+  return e;
+}
+
+// Make checkpoint k the current state of the march (c->m = k).
+cudaError_t restore_ckpt(tsfde_ctx* c, int64_t k) {
+  const double* slot = c->ck + c->ck_slot * (size_t)(k / c->ck_stride);
+  const size_t nb = sizeof(double) * (size_t)c->n;
+  cudaError_t e = cudaSuccess;
+  if (k >= 1) e = cudaMemcpyAsync(ulev(c, k - 1), slot, nb, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ulev(c, k), slot + c->ld, nb, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->G, slot + 2 * (size_t)c->ld, sizeof(double) * (size_t)std::max(c->E, 1) * c->ld,
+                        cudaMemcpyDeviceToDevice, c->stream);
+  c->m = k;
+  return e;
+}
+
+// Keep (save = true) or bring back the forward state: the three rotating
+// levels, the SOE history and the method-choice state.
+cudaError_t keep_forward_state(tsfde_ctx* c, bool save) {
+  const size_t nb = sizeof(double) * (size_t)c->n;
+  const size_t gb = sizeof(double) * (size_t)std::max(c->E, 1) * c->ld;
+  cudaError_t e = cudaSuccess;
+  for (int q = 0; q < 3 && e == cudaSuccess; ++q) {
+    double* keep = c->ck_save + (size_t)q * c->ld;
+    e = save ? cudaMemcpyAsync(keep, c->u[q], nb, cudaMemcpyDeviceToDevice, c->stream)
+             : cudaMemcpyAsync(c->u[q], keep, nb, cudaMemcpyDeviceToDevice, c->stream);
+  }
+  double* gkeep = c->ck_save + 3 * (size_t)c->ld;
+  if (e == cudaSuccess)
+    e = save ? cudaMemcpyAsync(gkeep, c->G, gb, cudaMemcpyDeviceToDevice, c->stream)
+             : cudaMemcpyAsync(c->G, gkeep, gb, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess && c->kauto)
+    e = save ? cudaMemcpyAsync(c->ck_kauto, c->kauto, sizeof(KrylovAuto), cudaMemcpyDeviceToDevice, c->stream)
+             : cudaMemcpyAsync(c->kauto, c->ck_kauto, sizeof(KrylovAuto), cudaMemcpyDeviceToDevice, c->stream);
+  return e;
 }
 
 
@@ -145,6 +215,7 @@ int tsfde_default_opts(tsfde_opts* o) {
   o->warm_start = 0;
   o->history = TSFDE_HISTORY_SOE;
   o->krylov = TSFDE_KRYLOV_BICGSTAB;
+  o->ckpt_stride = 0;
   return TSFDE_OK;
 }
 
@@ -205,9 +276,12 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
     return fail(c, TSFDE_EINVAL, "engine must be TSFDE_ENGINE_AUTO, _GRID or _CLUSTER");
   if (o.history != TSFDE_HISTORY_SOE && o.history != TSFDE_HISTORY_DIRECT)
     return fail(c, TSFDE_EINVAL, "history must be TSFDE_HISTORY_SOE or TSFDE_HISTORY_DIRECT");
-  if (o.krylov != TSFDE_KRYLOV_BICGSTAB && o.krylov != TSFDE_KRYLOV_PCG)
-    return fail(c, TSFDE_EINVAL, "krylov must be TSFDE_KRYLOV_BICGSTAB or TSFDE_KRYLOV_PCG");
-  if (o.krylov == TSFDE_KRYLOV_PCG && o.precision == TSFDE_MIXED && o.engine == TSFDE_ENGINE_CLUSTER)
+  if (o.krylov != TSFDE_KRYLOV_BICGSTAB && o.krylov != TSFDE_KRYLOV_PCG && o.krylov != TSFDE_KRYLOV_AUTO)
+    return fail(c, TSFDE_EINVAL, "krylov must be TSFDE_KRYLOV_BICGSTAB, _PCG or _AUTO");
+  if (o.ckpt_stride < -1) return fail(c, TSFDE_EINVAL, "ckpt_stride must be -1 (sqrt M), 0 (off) or positive");
+  if (o.ckpt_stride != 0 && o.history != TSFDE_HISTORY_SOE)
+    return fail(c, TSFDE_EINVAL, "checkpoints serve the FIDS adjoint (history = SOE)");
+  if (o.krylov != TSFDE_KRYLOV_BICGSTAB && o.precision == TSFDE_MIXED && o.engine == TSFDE_ENGINE_CLUSTER)
     return fail(c, TSFDE_ENOTSUP, "the cluster engine runs BiCGSTAB only");
   c->alpha = alpha; c->gamma = gamma; c->l = l; c->T = T; c->n = n; c->M = M; c->r = r;
   c->soe_tol = soe_tol; c->mu = mu; c->kappa_mu = kmu;
@@ -392,9 +466,22 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
                    &c->kds.ph, &c->kds.sh};
     for (dsf** p : vds) ok &= dalloc(c, p, ld);
   }
-  if (o.krylov == TSFDE_KRYLOV_PCG) {
+  if (o.krylov != TSFDE_KRYLOV_BICGSTAB) {
     ok &= dalloc(c, &c->hinv64, n) && dalloc(c, &c->hinv32, ld);
     if (ds) ok &= dalloc(c, &c->hinvds, ld);
+  }
+  if (o.krylov == TSFDE_KRYLOV_AUTO) ok &= dalloc(c, &c->kauto, 1);
+  if (o.ckpt_stride != 0) {
+    int64_t S = o.ckpt_stride;
+    if (S < 0) S = std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)M)));
+    S = std::min<int64_t>(S, M);
+    c->ck_stride = S;
+    c->ck_slots = M / S + 1;
+    c->ck_slot = (size_t)(2 + std::max(E, 1)) * ld;
+    c->ck_ok.assign(c->ck_slots, 0);
+    ok &= dalloc(c, &c->ck, c->ck_slot * c->ck_slots) && dalloc(c, &c->ck_seg, (size_t)S * n) &&
+          dalloc(c, &c->ck_save, (size_t)(3 + std::max(E, 1)) * ld);
+    if (c->kauto) ok &= dalloc(c, &c->ck_kauto, 1);
   }
   // direct history: all levels and the weights of Eq. (4.1),
   // w_0 = a_1/Gamma(1-g), w_k = (a_{k+1} - a_k)/Gamma(1-g) (k = 1..m-1)
@@ -551,7 +638,21 @@ int tsfde_reset(tsfde_ctx* c) {
     return cuda_fail(c, e, "reset copy");
   if ((e = cudaMemsetAsync(c->G, 0, sizeof(double) * (size_t)std::max(c->E, 1) * c->ld, c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "reset memset");
+  if (c->kauto) {
+    KrylovAuto k0{};
+    k0.for_level = 1;
+    k0.choice = 0;
+    c->kauto_init = k0;
+    if ((e = cudaMemcpyAsync(c->kauto, &c->kauto_init, sizeof(KrylovAuto), cudaMemcpyHostToDevice, c->stream)) !=
+        cudaSuccess)
+      return cuda_fail(c, e, "reset copy");
+  }
   c->m = 0;
+  if (c->ck) {
+    std::fill(c->ck_ok.begin(), c->ck_ok.end(), 0);
+    c->ck_override = false;
+    if ((e = record_ckpt(c, 0)) != cudaSuccess) return cuda_fail(c, e, "checkpoint copy");
+  }
   return TSFDE_OK;
 }
 
@@ -643,10 +744,16 @@ static int enqueue_level(tsfde_ctx* c, const double* kappa_m, const double* f_m,
   A.u_prev = c->opts.warm_start ? ulev(c, m - 1) : nullptr;
   A.prev = (m >= 2) ? c->stats + (m - 1) : nullptr;
   A.retry_mixed = (m % 64 == 0) ? 1 : 0;
+  A.kauto = c->kauto;
+  A.m = m;
   e = launch_level_ctx(c, A);
   if (e == cudaSuccess) e = record(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "level kernel");
   c->m = m;
+  if (c->ck && !c->ck_recomputing) {
+    if (kappa_m || f_m) c->ck_override = true;
+    if (m % c->ck_stride == 0 && (e = record_ckpt(c, m)) != cudaSuccess) return cuda_fail(c, e, "checkpoint copy");
+  }
   return TSFDE_OK;
 }
 
@@ -672,6 +779,7 @@ int tsfde_step(tsfde_ctx* c, const double* kappa_m, const double* f_m, double* u
     info->outer = s.outer;
     info->E_active = c->Eact[m];
     info->rel_residual = s.rel_residual;
+    info->krylov = s.method;
     if (s.status != TSFDE_OK) return fail(c, s.status, std::string("level ") + std::to_string(m) + ": " + tsfde_strerror(s.status));
   }
   return TSFDE_OK;
@@ -712,6 +820,7 @@ int tsfde_solve(tsfde_ctx* c, double* u_final, double* u_all, tsfde_solve_info* 
       info->max_iterations = std::max(info->max_iterations, s[m].iterations);
       info->max_rel_residual = std::max(info->max_rel_residual, s[m].rel_residual);
       info->E_active_sum += c->Eact[m];
+      info->pcg_levels += s[m].method == 1 ? 1 : 0;
     }
     info->levels = c->M - m0;
     if (info->levels == 0) info->min_iterations = 0;
@@ -737,6 +846,7 @@ int tsfde_get_level_stats(tsfde_ctx* c, int64_t m0, int64_t m1, tsfde_step_info*
     out[q].outer = s[q].outer;
     out[q].E_active = c->Eact[m0 + q];
     out[q].rel_residual = s[q].rel_residual;
+    out[q].krylov = s[q].method;
   }
   return TSFDE_OK;
 }
@@ -833,13 +943,66 @@ int tsfde_precond_apply(tsfde_ctx* c, double a, double kbar, const double* v, do
 
 int tsfde_get_engine(const tsfde_ctx* c) { return c ? c->engine : -1; }
 
+// One reverse level m of the adjoint sweep: g^m (from lambda^{m+1} through
+// the reversed SOE recurrence, or dJ/du^M at m = M), the transposed level
+// solve into lambda^m and the gradient terms with u^m (dev n).
+static int adjoint_level(tsfde_ctx* c, int64_t m, const double* um, const double* dJ, double* grad_kappa,
+                         double* grad_f) {
+  const int64_t n = c->n, M = c->M;
+  cudaStream_t s = c->stream;
+  cudaError_t e;
+  double* lam = c->adjLam[m & 1];
+  const double* lam1 = c->adjLam[(m + 1) & 1];
+  if (m == M) {
+    if ((e = cudaMemcpyAsync(c->adjG, dJ, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+      return cuda_fail(c, e, "adjoint copy");
+  } else {
+    AdjRhsArgs R{};
+    R.n = (int)n;
+    R.ld = c->ld;
+    R.Eact = c->Eact[m + 1];
+    R.ahat1 = c->ahat[m + 1];
+    R.Y = c->adjY;
+    R.eps1 = c->eps + (m + 1) * c->E;
+    R.c1 = c->cw + (m + 1) * c->E;
+    R.c2 = (m + 2 <= M) ? c->cw + (m + 2) * c->E : nullptr;
+    R.lam1 = lam1;
+    R.g = c->adjG;
+    if ((e = launch_adj_rhs(R, s)) != cudaSuccess) return cuda_fail(c, e, "adjoint rhs kernel");
+  }
+  LevelArgs A{};
+  A.P = c->P;
+  A.ahat = c->ahat[m];
+  A.b = c->adjG;
+  A.kappa64 = c->kappa64;
+  A.kappa32 = c->kappa32;
+  A.u = lam;
+  A.precond = c->opts.precond == TSFDE_STRANG ? 1 : 0;
+  A.tol = c->opts.krylov_tol;
+  A.max_it = c->opts.max_it;
+  A.k64 = c->k64;
+  A.k32 = c->k32;
+  A.r64 = c->r64;
+  A.stat = c->adjStats + m;
+  AdjGradArgs Gd{um, grad_kappa, grad_f};
+  if ((e = launch_level_adj(A, Gd, s)) != cudaSuccess) return cuda_fail(c, e, "adjoint level kernel");
+  return TSFDE_OK;
+}
+
 int tsfde_adjoint(tsfde_ctx* c, const double* u_all, const double* dJ, double* grad_kappa,
                   double* grad_f, tsfde_adjoint_info* info) {
-  if (!c || !u_all || !dJ || !grad_kappa || !grad_f) return TSFDE_EINVAL;
+  if (!c || !dJ || !grad_kappa || !grad_f) return TSFDE_EINVAL;
   if (!c->have_problem) return fail(c, TSFDE_ESTATE, "no problem set");
   if (c->kap1) return fail(c, TSFDE_ENOTSUP, "adjoint needs a time-independent kappa (kappa1 = NULL)");
   if (c->Uh) return fail(c, TSFDE_ENOTSUP, "the adjoint sweep is that of FIDS (history = SOE)");
   const int64_t n = c->n, M = c->M;
+  if (!u_all) {
+    if (!c->ck) return fail(c, TSFDE_ESTATE, "u_all is NULL and the context keeps no checkpoints (ckpt_stride = 0)");
+    if (c->m != M) return fail(c, TSFDE_ESTATE, "checkpointed adjoint: march to level M first");
+    if (c->ck_override) return fail(c, TSFDE_ESTATE, "checkpointed adjoint: a level used per-level kappa_m / f_m");
+    for (int64_t j = 0; j * c->ck_stride < M; ++j)
+      if (!c->ck_ok[j]) return fail(c, TSFDE_ESTATE, "checkpointed adjoint: the march was not run from level 0");
+  }
   const int E = std::max(c->E, 1);
   if (!c->adjY) {
     bool ok = dalloc(c, &c->adjY, (size_t)E * c->ld) && dalloc(c, &c->adjLam[0], n) &&
@@ -860,44 +1023,36 @@ int tsfde_adjoint(tsfde_ctx* c, const double* u_all, const double* dJ, double* g
   // kappa of every level is kappa0
   if ((e = launch_convert(c->kap0, c->kappa64, c->kappa32, (int)n, s)) != cudaSuccess)
     return cuda_fail(c, e, "convert kernel");
-  const int precond = c->opts.precond == TSFDE_STRANG ? 1 : 0;
-  for (int64_t m = M; m >= 1; --m) {
-    double* lam = c->adjLam[m & 1];
-    const double* lam1 = c->adjLam[(m + 1) & 1];
-    if (m == M) {
-      if ((e = cudaMemcpyAsync(c->adjG, dJ, nb, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-        return cuda_fail(c, e, "adjoint copy");
-    } else {
-      AdjRhsArgs R{};
-      R.n = (int)n;
-      R.ld = c->ld;
-      R.Eact = c->Eact[m + 1];
-      R.ahat1 = c->ahat[m + 1];
-      R.Y = c->adjY;
-      R.eps1 = c->eps + (m + 1) * c->E;
-      R.c1 = c->cw + (m + 1) * c->E;
-      R.c2 = (m + 2 <= M) ? c->cw + (m + 2) * c->E : nullptr;
-      R.lam1 = lam1;
-      R.g = c->adjG;
-      if ((e = launch_adj_rhs(R, s)) != cudaSuccess) return cuda_fail(c, e, "adjoint rhs kernel");
+  int st0 = TSFDE_OK;
+  if (u_all) {
+    for (int64_t m = M; m >= 1 && st0 == TSFDE_OK; --m)
+      st0 = adjoint_level(c, m, u_all + (size_t)m * n, dJ, grad_kappa, grad_f);
+  } else {
+    // Checkpointed sweep: segments (k0, k1] of ck_stride levels, last first;
+    // each is marched again from its checkpoint k0 into ck_seg, then swept
+    // in reverse.  The forward state is kept aside and brought back.
+    const int64_t S = c->ck_stride;
+    if ((e = keep_forward_state(c, true)) != cudaSuccess) return cuda_fail(c, e, "checkpoint copy");
+    c->ck_recomputing = true;
+    for (int64_t k0 = ((M - 1) / S) * S; k0 >= 0 && st0 == TSFDE_OK; k0 -= S) {
+      const int64_t k1 = std::min(k0 + S, M);
+      if ((e = restore_ckpt(c, k0)) != cudaSuccess) { st0 = cuda_fail(c, e, "checkpoint copy"); break; }
+      for (int64_t m = k0 + 1; m <= k1 && st0 == TSFDE_OK; ++m) {
+        st0 = enqueue_level(c, nullptr, nullptr, nullptr);
+        if (st0 == TSFDE_OK &&
+            (e = cudaMemcpyAsync(c->ck_seg + (size_t)(m - k0 - 1) * n, ulev(c, m), nb, cudaMemcpyDeviceToDevice,
+                                 s)) != cudaSuccess)
+          st0 = cuda_fail(c, e, "checkpoint copy");
+      }
+      // the recomputed forward levels wrote kappa^m = kappa0 again: unchanged
+      for (int64_t m = k1; m > k0 && st0 == TSFDE_OK; --m)
+        st0 = adjoint_level(c, m, c->ck_seg + (size_t)(m - k0 - 1) * n, dJ, grad_kappa, grad_f);
     }
-    LevelArgs A{};
-    A.P = c->P;
-    A.ahat = c->ahat[m];
-    A.b = c->adjG;
-    A.kappa64 = c->kappa64;
-    A.kappa32 = c->kappa32;
-    A.u = lam;
-    A.precond = precond;
-    A.tol = c->opts.krylov_tol;
-    A.max_it = c->opts.max_it;
-    A.k64 = c->k64;
-    A.k32 = c->k32;
-    A.r64 = c->r64;
-    A.stat = c->adjStats + m;
-    AdjGradArgs Gd{u_all + (size_t)m * n, grad_kappa, grad_f};
-    if ((e = launch_level_adj(A, Gd, s)) != cudaSuccess) return cuda_fail(c, e, "adjoint level kernel");
+    c->ck_recomputing = false;
+    c->m = M;
+    if ((e = keep_forward_state(c, false)) != cudaSuccess && st0 == TSFDE_OK) st0 = cuda_fail(c, e, "checkpoint copy");
   }
+  if (st0 != TSFDE_OK) return st0;
   std::vector<StepStat> st(M + 1);
   if ((e = cudaMemcpyAsync(st.data(), c->adjStats, sizeof(StepStat) * (M + 1), cudaMemcpyDeviceToHost, s)) !=
           cudaSuccess ||
@@ -913,6 +1068,18 @@ int tsfde_adjoint(tsfde_ctx* c, const double* u_all, const double* dJ, double* g
       inf.failed_level = m;
     }
   }
+  if (!u_all) {
+    // the recomputed forward levels must have converged as well
+    std::vector<StepStat> fw(M + 1);
+    if ((e = cudaMemcpy(fw.data(), c->stats, sizeof(StepStat) * (M + 1), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(c, e, "adjoint sync");
+    for (int64_t m = 1; m <= M; ++m)
+      if (fw[m].status != TSFDE_OK && inf.status == TSFDE_OK) {
+        inf.status = fw[m].status;
+        inf.failed_level = m;
+      }
+    inf.recomputed_levels = M;
+  }
   if (info) *info = inf;
   if (inf.status != TSFDE_OK) return fail(c, inf.status, tsfde_strerror(inf.status));
   return TSFDE_OK;
@@ -926,6 +1093,7 @@ int tsfde_linear_solve(tsfde_ctx* c, double a, const double* kappa, const double
   if (e != cudaSuccess) return cuda_fail(c, e, "convert kernel");
   LevelArgs A = level_args(c, a, b, x, c->stats);
   A.kappa64 = c->kappa64;
+  if (A.krylov == TSFDE_KRYLOV_AUTO) A.krylov = TSFDE_KRYLOV_BICGSTAB;  // no level history here
   e = launch_level_ctx(c, A);
   if (e != cudaSuccess) return cuda_fail(c, e, "level kernel");
   StepStat s{};
@@ -939,6 +1107,7 @@ int tsfde_linear_solve(tsfde_ctx* c, double a, const double* kappa, const double
     info->outer = s.outer;
     info->E_active = 0;
     info->rel_residual = s.rel_residual;
+    info->krylov = s.method;
   }
   if (s.status != TSFDE_OK) return fail(c, s.status, tsfde_strerror(s.status));
   return TSFDE_OK;

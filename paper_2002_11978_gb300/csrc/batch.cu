@@ -395,6 +395,12 @@ __device__ LevelOut bt_level(BatchCtx* bx, const BatchArgs& A, int m, bool prev_
     o.iters += ir.iters;
     ++o.outer;
     cl.sync();
+    // no usable correction (non-finite, or no iteration run): FP64 finish
+    if (ir.status == TSFDE_ENONFINITE ||
+        (ir.status != TSFDE_OK && ir.status != TSFDE_ENOCONV && ir.iters == 0)) {
+      fallback = true;
+      break;
+    }
     bt_resid_product(bx, nr, ah);
     cl.sync();
     const double rw = ce_total(s.part, Q, BS_RW), ww = ce_total(s.part, Q, BS_WW);
@@ -409,7 +415,10 @@ __device__ LevelOut bt_level(BatchCtx* bx, const BatchArgs& A, int m, bool prev_
     nr = sqrt(rr);
     if (!isfinite(nr) || !isfinite(xmax)) { o.status = TSFDE_ENONFINITE; break; }
     relres = nr / nb;
-    if (nr == 0.0 || emax <= A.tol * xmax) break;
+    if (nr == 0.0 || relres <= A.tol) break;
+    // a zero correction cannot make progress: never read it as converged
+    if (!(emax > 0.0)) { fallback = true; break; }
+    if (emax <= A.tol * xmax) break;
     if (o.outer >= 2 && nr > 0.5 * nr_prev) {
       // the FP64 residual is at its rounding floor and u no longer moves at
       // the accuracy asked for

@@ -206,6 +206,8 @@ template <typename T> bool balloc(tsfde_batch* b, T** p, size_t count) {
   if (count == 0) count = 1;
   if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) return false;
   b->allocs.push_back(q);
+  // zeroed, so that no buffer read before its first write sees stale NaNs
+  if (cudaMemset(q, 0, count * sizeof(T)) != cudaSuccess) return false;
   *p = static_cast<T*>(q);
   return true;
 }

@@ -532,7 +532,7 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
     if (rho_new == 0.0 || omega == 0.0) { out.status = TSFDE_EBREAKDOWN; return out; }
     const double beta = (rho_new / rho) * (alpha / omega);
     rho = rho_new;
-    ++it;
+    out.iters = ++it;
     // p = r + beta (p - omega v)
     {
       const R bR = (R)beta, oR = (R)omega;
@@ -653,13 +653,16 @@ __device__ SolveRes pcg(const DevPlan& P, const Smem<R>& sm, const KVecs<R>& V,
   const int gstr = gridDim.x * blockDim.x;
   const R a = (R)ahat;
   SolveRes out{TSFDE_OK, 0, 0.0};
-  // x = 0, r = K^{-1} b (and its forward column FFTs), ||b||
+  // x = 0, p = 0, r = K^{-1} b (and its forward column FFTs), ||b||.  p is
+  // read by the first p = z + beta p (beta = 0), so it must hold no stale
+  // non-finite value: 0 * NaN is NaN.
   {
     R acc = 0;
     auto pro = [&](int i) -> R {
       const R bi = binit(i);
       const R ri = bi * hinv[i];
       V.x[i] = R(0);
+      V.p[i] = R(0);
       V.r[i] = ri;
       acc += bi * bi;
       return ri;
@@ -710,7 +713,7 @@ __device__ SolveRes pcg(const DevPlan& P, const Smem<R>& sm, const KVecs<R>& V,
     if (relres < tol) return out;
     if (it >= max_it) { out.status = TSFDE_ENOCONV; return out; }
     if (!(rho > 0.0)) { out.status = TSFDE_EBREAKDOWN; return out; }
-    ++it;
+    out.iters = ++it;
     // p = z + beta p, forward column FFTs of p
     {
       const R bR = (R)beta;
@@ -907,6 +910,16 @@ __device__ void mixed_level(const LevelArgs& A, SmemAll& S, Conv& conv, Inner& i
     if (!inner(1.0 / nr, A.tol * nb / nr, ir)) { status = TSFDE_ETIMEOUT; break; }
     inner_total += ir.iters;
     ++outer;
+    // An inner solve that hit its iteration cap (or broke down after some
+    // iterations) still leaves a usable correction: the FP64 step below
+    // accepts it only if it lowers the FP64 residual.  One that produced a
+    // non-finite value, or stopped before its first iteration, leaves none:
+    // the level goes to the FP64 finish.
+    if (ir.status == TSFDE_ENONFINITE ||
+        (ir.status != TSFDE_OK && ir.status != TSFDE_ENOCONV && ir.iters == 0)) {
+      fallback = true;
+      break;
+    }
     // w = M (nr e) in FP64
     const double ah = A.ahat;
     auto pro = [&](int i) -> double { return nr * (double)e[i]; };
@@ -959,7 +972,10 @@ __device__ void mixed_level(const LevelArgs& A, SmemAll& S, Conv& conv, Inner& i
     nr = sqrt(rr);
     if (!isfinite(nr) || !isfinite(xmax)) { status = TSFDE_ENONFINITE; break; }
     relres = nr / nb;
-    if (nr == 0.0 || emax <= A.tol * xmax || relres <= A.tol) break;
+    if (nr == 0.0 || relres <= A.tol) break;
+    // a zero correction cannot make progress: never read it as converged
+    if (!(emax > 0.0)) { fallback = true; break; }
+    if (emax <= A.tol * xmax) break;
     if (outer >= 2 && nr > 0.5 * nr_prev) {
       // the FP64 residual is at its rounding floor and u no longer moves at
       // the accuracy asked for

@@ -357,18 +357,25 @@ cudaError_t launch_convert(const double* in, double* o64, float* o32, int n, cud
   return cudaGetLastError();
 }
 
+// With TSFDE_KRYLOV_AUTO (a.kauto set) both method kernels are launched;
+// the one not chosen for the level returns before any work.
 cudaError_t launch_level(const LevelArgs& a, int precision, cudaStream_t s) {
   size_t smem = plan_smem_bytes(a.P);
-  cudaError_t e = cudaMemsetAsync(a.P.bar, 0, sizeof(GridBarrier), s);
-  if (e != cudaSuccess) return e;
   void* args[] = {(void*)&a};
   const bool kp2 = kp_fits(a.P, 2);
   const int kp = kp2 ? 2 : 4;
-  const int pcg = a.krylov == TSFDE_KRYLOV_PCG ? 1 : 0;
-  const void* k = precision == TSFDE_MIXED_DS ? levelds_kernel(kp, pcg)
-                  : precision == TSFDE_MIXED  ? level32_kernel(kp, pcg)
-                                              : level64_kernel(kp, pcg);
-  return cudaLaunchCooperativeKernel(k, dim3(a.P.G), dim3(kThreads), args, smem, s);
+  const bool autok = a.krylov == TSFDE_KRYLOV_AUTO && a.kauto;
+  for (int pcg = 0; pcg < 2; ++pcg) {
+    if (!autok && pcg != (a.krylov == TSFDE_KRYLOV_PCG ? 1 : 0)) continue;
+    cudaError_t e = cudaMemsetAsync(a.P.bar, 0, sizeof(GridBarrier), s);
+    if (e != cudaSuccess) return e;
+    const void* k = precision == TSFDE_MIXED_DS ? levelds_kernel(kp, pcg)
+                    : precision == TSFDE_MIXED  ? level32_kernel(kp, pcg)
+                                                : level64_kernel(kp, pcg);
+    e = cudaLaunchCooperativeKernel(k, dim3(a.P.G), dim3(kThreads), args, smem, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_adj_rhs(const AdjRhsArgs& a, cudaStream_t s) {

@@ -17,9 +17,56 @@
 
 namespace tsfde {
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// TSFDE_KRYLOV_AUTO (KrylovAuto, plan.h): true when the kernel of method
+// PCG solves level A.m (always true for a fixed method).  Read by every
+// thread before any work; the state changes only between kernels.
+__device__ __forceinline__ bool auto_mine(const LevelArgs& A, bool pcg) {
+  if (!A.kauto) return true;
+  return __ldcg(&A.kauto->for_level) == A.m && __ldcg(&A.kauto->choice) == (pcg ? 1 : 0);
+}
+
+// End of a level solved by method `pcg`: block 0's thread 0 (which wrote the
+// level's status) records the method in the level's stats and, for AUTO,
+// the level's device time, then picks the next level's method: the other
+// method if it was faster at its latest sample, has none yet, or its sample
+// is older than the probe interval 8 r^2 levels (8..64), r = how many times
+// slower it was.  A failed level counts as infinitely slow.
+__device__ __forceinline__ void level_done(const LevelArgs& A, bool pcg, unsigned long long t0) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  if (A.stat) A.stat->method = pcg ? 1 : 0;
+  KrylovAuto* k = A.kauto;
+  if (!k) return;
+  const int me = pcg ? 1 : 0, ot = 1 - me;
+  double dt = (double)(global_ns() - t0);
+  if (A.stat && A.stat->status != TSFDE_OK) dt = INFINITY;
+  k->t[me] = dt;
+  k->at[me] = A.m;
+  k->used[me] += 1;
+  int next = me;
+  if (k->at[ot] == 0) {
+    next = ot;
+  } else {
+    const double r = k->t[ot] / dt;
+    if (!(r >= 1.0)) {
+      next = ot;
+    } else {
+      const double interval = fmin(fmax(8.0 * r * r, 8.0), 64.0);
+      if ((double)(A.m + 1 - k->at[ot]) >= interval) next = ot;
+    }
+  }
+  k->choice = next;
+  k->for_level = A.m + 1;
+}
+
 // FP64 level solve: preconditioner build and the Krylov solve, all in FP64.
 template <int KP, bool PCG>
-__global__ void __launch_bounds__(kThreads, 2) k_level64(LevelArgs A) {
+__device__ void level64_run(const LevelArgs& A) {
   const DevPlan& P = A.P;
   if (!kp_fits(P, KP)) { write_stat(A.stat, TSFDE_EINVAL, 0, 0, 0.0); return; }
   SmemAll S = smem_setup(P);
@@ -60,10 +107,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_level64(LevelArgs A) {
   write_stat(A.stat, r.status, r.iters, 0, r.relres * scale);
 }
 
+template <int KP, bool PCG>
+__global__ void __launch_bounds__(kThreads, 2) k_level64(LevelArgs A) {
+  if (!auto_mine(A, PCG)) return;
+  const unsigned long long t0 = global_ns();
+  level64_run<KP, PCG>(A);
+  level_done(A, PCG, t0);
+}
+
 // Mixed level solve on the grid engine: the refinement loop of mixed_level
 // (grid.cuh) with the FP32 inner solve spread over the whole cooperative grid.
 template <int KP, bool PCG>
-__global__ void __launch_bounds__(kThreads, 2) k_level_mixed(LevelArgs A) {
+__device__ void level_mixed_run(const LevelArgs& A) {
   const DevPlan& P = A.P;
   if (!kp_fits(P, KP)) { write_stat(A.stat, TSFDE_EINVAL, 0, 0, 0.0); return; }
   SmemAll S = smem_setup(P);
@@ -86,6 +141,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_level_mixed(LevelArgs A) {
   mixed_level<PCG>(A, S, conv, inner, A.k32.x);
 }
 
+template <int KP, bool PCG>
+__global__ void __launch_bounds__(kThreads, 2) k_level_mixed(LevelArgs A) {
+  if (!auto_mine(A, PCG)) return;
+  const unsigned long long t0 = global_ns();
+  level_mixed_run<KP, PCG>(A);
+  level_done(A, PCG, t0);
+}
+
 // Mixed level solve with the inner solve in double-single arithmetic
 // (dsf.cuh): the same refinement loop, every inner vector, product and
 // scalar update carried as FP32 pairs.  kappa^m (and 1/kappa^m for PCG) and
@@ -101,7 +164,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_level_mixed(LevelArgs A) {
 constexpr double kFirstSweep = 100.0;
 
 template <int KP, bool PCG>
-__global__ void __launch_bounds__(kThreads, 2) k_level_mixed_ds(LevelArgs A) {
+__device__ void level_mixed_ds_run(const LevelArgs& A) {
   const DevPlan& P = A.P;
   if (!kp_fits(P, KP)) { write_stat(A.stat, TSFDE_EINVAL, 0, 0, 0.0); return; }
   SmemAll S = smem_setup(P);
@@ -128,6 +191,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_level_mixed_ds(LevelArgs A) {
     return ir.status != TSFDE_ETIMEOUT;
   };
   mixed_level<PCG>(A, S, conv, inner, A.kds.x);
+}
+
+template <int KP, bool PCG>
+__global__ void __launch_bounds__(kThreads, 2) k_level_mixed_ds(LevelArgs A) {
+  if (!auto_mine(A, PCG)) return;
+  const unsigned long long t0 = global_ns();
+  level_mixed_ds_run<KP, PCG>(A);
+  level_done(A, PCG, t0);
 }
 
 }  // namespace tsfde

@@ -138,6 +138,25 @@ struct StepStat {
   int outer;
   int E_active;
   double rel_residual;
+  int method;           // Krylov method that solved the level (0 BiCGSTAB, 1 PCG)
+  int pad;
+};
+
+// Per-level choice of the Krylov method (TSFDE_KRYLOV_AUTO).  Every level
+// launches the BiCGSTAB and the PCG kernel; the one whose method is `choice`
+// for level `for_level` solves it, the other returns at once.  Block 0 of
+// the solving kernel then records the level's device time (globaltimer) for
+// its method and picks the method of the next level: the cheaper one by the
+// latest samples, or the other one as a probe once its sample is older than
+// an interval that grows with the ratio it lost by (8 r^2 levels, 8..64).
+// Cleared by the host at every reset (choice BiCGSTAB for level 1).
+struct KrylovAuto {
+  long long for_level;  // level the choice applies to
+  int choice;           // 0 BiCGSTAB, 1 PCG
+  int pad;
+  double t[2];          // device time (ns) of the latest level of each method
+  long long at[2];      // level of that sample (0: none yet)
+  long long used[2];    // levels solved by each method since the reset
 };
 
 // Krylov workspace of one precision.
@@ -172,6 +191,8 @@ struct LevelArgs {
   const double* u_prev;   // warm start from u^{m-1} (NULL: x0 = 0)
   const StepStat* prev;   // mixed: the previous level's stats (NULL: none)
   int retry_mixed;        // mixed: refine even after a level finished in FP64
+  KrylovAuto* kauto;      // TSFDE_KRYLOV_AUTO: method choice state (NULL: fixed method)
+  long long m;            // level index (with kauto)
 };
 
 // One instance of the batched solve (device-resident descriptor).  All

@@ -29,7 +29,8 @@ def cuda(torch, a):
 
 def solver(alpha=1.5, gamma=0.5, n=127, M=8, r=3.0, **kw):
     import paper_2002_11978_gb300 as pkg
-    return pkg.Solver(alpha, gamma, 1.0, 1.0, n, M, r, kw.pop("soe_tol", 1e-12), krylov="pcg", **kw)
+    return pkg.Solver(alpha, gamma, 1.0, 1.0, n, M, r, kw.pop("soe_tol", 1e-12),
+                      krylov=kw.pop("krylov", "pcg"), **kw)
 
 
 @pytest.mark.parametrize("n", [1, 2, 63, 127, 1023, 4095])
@@ -136,10 +137,14 @@ def test_pcg_full_size_levels_vs_bicgstab(torch):
 
 def test_pcg_mid_size_late_levels(torch):
     """n = 2^14 - 1, gamma = 0.7, alpha = 1.8 on a 64-level mesh (ahat from
-    ~250 down to ~11, where A dominates and PCG gains most): PCG and
-    BiCGSTAB in FP64 agree to 1e-10 at every level, and PCG needs fewer
-    products over the march: two per iteration (A and P^{-1}) against
-    BiCGSTAB's four (measured: 896 PCG iterations, 734 BiCGSTAB)."""
+    ~250 down to ~11): PCG and BiCGSTAB in FP64 agree to 1e-10 at every
+    level.  PCG takes MORE iterations than BiCGSTAB over this march
+    (measured: 896 against 734, ~14 against ~11.5 per level): with x0 = 0
+    the first levels are still ahat-dominated, where the circulant
+    preconditioner of the symmetrised system cannot follow 1/kappa.  Each PCG
+    iteration costs one product with A and one with P^{-1}, a BiCGSTAB
+    iteration two of each, so PCG still needs fewer products: that, and not
+    the iteration count, is what the assertion states."""
     import paper_2002_11978_gb300 as pkg
     prob = ti.config_mid(0.7, 1.8, M=64)
     out, its = {}, {}
@@ -154,4 +159,83 @@ def test_pcg_mid_size_late_levels(torch):
         its[kry] = info["iterations"]
     err = np.max(np.abs(out["pcg"] - out["bicgstab"])) / np.max(np.abs(out["bicgstab"]))
     assert err < 1e-10, err
-    assert 2 * its["pcg"] < 4 * its["bicgstab"], its
+    assert its["pcg"] > its["bicgstab"], its          # more iterations ...
+    products = {"pcg": 2 * its["pcg"], "bicgstab": 4 * its["bicgstab"]}
+    assert products["pcg"] < products["bicgstab"], its  # ... but fewer products
+
+
+@pytest.mark.parametrize("precision", ["mixed_ds", "mixed"])
+@pytest.mark.parametrize("krylov", ["pcg", "bicgstab"])
+def test_inner_failure_goes_to_fp64_finish(torch, precision, krylov):
+    """A failed inner solve must never be read as convergence.  With
+    a = 1e40 the inner arithmetic (FP32, or double-single whose high part is
+    FP32) overflows: the inner solve stops with a non-finite value and no
+    usable correction.  The level must then be finished by the FP64 Krylov
+    solve (outer < 0) and return the dense-LU answer, not x = 0 with OK."""
+    n, a, alpha = 63, 1.0e40, 1.6
+    s = solver(alpha=alpha, n=n, precision=precision, krylov=krylov)
+    t = oracle.ifl_symbol(alpha, n)
+    kap = ti.log_minmax(ti.gaussian_field(n, 3), 0.2, 5.0)
+    b = np.random.default_rng(5).standard_normal(n) * 10
+    ref = oracle.lu_solve(a * np.eye(n) + kap[:, None] * oracle.dense_A(t), b)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    info = s.linear_solve(a, cuda(torch, kap), cuda(torch, b), x)
+    err = np.max(np.abs(x.cpu().numpy() - ref)) / np.max(np.abs(ref))
+    assert info["status"] == 0 and info["outer"] < 0, info
+    assert err < 1e-10, (err, info)
+
+
+def test_fresh_context_ignores_stale_device_memory(torch):
+    """Regression for a context whose Krylov workspaces were not cleared: PCG's
+    first p = z + beta p reads p with beta = 0, and 0 * NaN = NaN, so the
+    inner solve stopped before its first iteration and the level returned
+    x = 0 with status OK.  Freed memory is filled with NaN first, so that
+    the new context's workspaces are likely carved from it."""
+    junk = torch.full((1 << 27,), float("nan"), dtype=torch.float64, device="cuda")
+    del junk
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    n, a, alpha = 63, 1.0e3, 1.6
+    s = solver(alpha=alpha, n=n, precision="mixed_ds")
+    t = oracle.ifl_symbol(alpha, n)
+    kap = ti.log_minmax(ti.gaussian_field(n, 3), 0.2, 5.0)
+    b = np.random.default_rng(5).standard_normal(n) * 10
+    ref = oracle.lu_solve(a * np.eye(n) + kap[:, None] * oracle.dense_A(t), b)
+    for _ in range(2):
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        info = s.linear_solve(a, cuda(torch, kap), cuda(torch, b), x)
+        err = np.max(np.abs(x.cpu().numpy() - ref)) / np.max(np.abs(ref))
+        assert err < 1e-10 and info["iterations"] > 0, (err, info)
+
+
+@pytest.mark.parametrize("precision,warm", [("fp64", False), ("fp64", True), ("mixed_ds", False),
+                                            ("mixed_ds", True), ("mixed", True)])
+def test_auto_method_march_matches_oracle(torch, precision, warm):
+    """krylov = "auto" (per-level choice of BiCGSTAB or PCG from measured
+    level times): n = 127, M = 64, every level within 1e-10 of the oracle's
+    march; level 1 is solved by BiCGSTAB and level 2 by PCG (the first probe),
+    and the stats report the method of every level."""
+    import paper_2002_11978_gb300 as pkg
+    prob = ti.config_smallest()
+    tm, tau = oracle.graded_mesh(prob.T, prob.M, prob.r)
+    soe = oracle.soe_build(prob.gamma, tau[1], prob.T, prob.soe_tol)
+    s = pkg.Solver(prob.alpha, prob.gamma, prob.l, prob.T, prob.n, prob.M, prob.r, prob.soe_tol,
+                   precision=precision, soe=soe, krylov_tol=prob.krylov_tol, warm_start=warm,
+                   krylov="auto")
+    s.set_problem_from(prob)
+    U = torch.zeros((prob.M + 1, prob.n), dtype=torch.float64, device="cuda")
+    uf = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    info = s.solve(uf, U)
+    assert info["status"] == 0, info
+    ref = oracle.march("FIDS", prob.alpha, prob.gamma, prob.l, prob.T, prob.r, prob.n, prob.M,
+                       prob.phi, prob.kappa_table(tm), prob.f_table(tm), soe=soe)
+    err = np.max(np.abs(U.cpu().numpy() - ref)) / np.max(np.abs(ref))
+    assert err < 1e-10, (err, info)
+    st = s.level_stats(1, prob.M)
+    methods = [x["krylov"] for x in st]
+    assert methods[0] == 0 and methods[1] == 1, methods
+    assert info["pcg_levels"] == sum(methods) and 0 < info["pcg_levels"] < prob.M, info
+    # a reset starts the choice again from BiCGSTAB
+    s.reset()
+    s.step()
+    assert s.level_stats(1, 1)[0]["krylov"] == 0

@@ -383,3 +383,21 @@ def test_adjoint_matches_central_differences():
         fd_f = (J(kap0, f0 + h * d) - J(kap0, f0 - h * d)) / (2 * h)
         assert gk @ d == pytest.approx(fd_k, rel=1e-6, abs=1e-12)
         assert gf @ d == pytest.approx(fd_f, rel=1e-6, abs=1e-12)
+
+
+def test_threaded_lu_gives_the_same_bits():
+    """The timed CPU baseline may run the LU's row updates on several threads;
+    each row's update is the same operation sequence, so the solution must be
+    bitwise that of one thread."""
+    rng = np.random.default_rng(11)
+    n = 300
+    A = rng.standard_normal((n, n)) + n * np.eye(n)
+    b = rng.standard_normal(n)
+    x1 = oracle.lu_solve(A, b)
+    try:
+        oracle.set_threads(4)
+        x4 = oracle.lu_solve(A, b)
+    finally:
+        oracle.set_threads(1)
+    assert np.array_equal(x1, x4)
+    assert oracle.get_threads() == 1
