@@ -56,6 +56,7 @@ def parse():
                     help="x0 = 0 for every level as in the paper's experiments (default: start "
                          "from u^{m-1}, same stopping rule ||r|| < tol ||b||)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
+    ap.add_argument("--no-mid", action="store_true", help="skip the mid workload (n = 2^14 - 1, six pairs)")
     ap.add_argument("--dids-levels", type=int, default=None,
                     help="levels of the DIDS (direct history) march to time; default M, 0 skips it")
     ap.add_argument("--krylov", choices=["auto", "bicgstab", "pcg"], default="auto",
@@ -356,48 +357,123 @@ def dids_sample(torch, pkg, prob, stream, levels, warm, u_fids_M, krylov):
 
 def adjoint_sample(torch, pkg, ti, stream):
     """The adjoint workload: n = 4095, M = 1024, J = 1/2 ||u^M - u_obs||^2
-    with u_obs from another kappa; forward march (FP64, all levels kept) and
-    the reverse sweep (transposed FP64 solves, reversed SOE recurrence,
-    fused gradient products), each timed with CUDA events.  The gradient is
-    checked against a central difference of J along one random direction."""
+    with u_obs from another kappa.  Times the forward march (FP64) and the
+    reverse sweep (transposed FP64 solves, reversed SOE recurrence, fused
+    gradient products) twice: over the stored trajectory, and with
+    ceil(sqrt(M)) = 32-level checkpoints (u_all = NULL: each segment marched
+    again from its checkpoint).  The gradient is checked against central
+    differences of J along 3 seeded directions in (kappa, f)."""
     prob, kobs = ti.config_adjoint()
     n, M = prob.n, prob.M
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
-    s = pkg.Solver(prob.alpha, prob.gamma, prob.l, prob.T, n, M, prob.r, 1e-12, stream=stream)
+    s = pkg.Solver(prob.alpha, prob.gamma, prob.l, prob.T, n, M, prob.r, 1e-12, stream=stream,
+                   ckpt_stride=-1)
     ones = np.ones(M + 1)
     U = torch.zeros((M + 1, n), dtype=torch.float64, device="cuda")
     uf = torch.zeros(n, dtype=torch.float64, device="cuda")
 
-    def forward(kap):
-        s.set_problem(dev(prob.phi), dev(kap), None, None, F=[dev(prob.F[0])], G=[ones])
-        s.solve(uf, U)
+    def forward(kap, f, keep=True):
+        s.set_problem(dev(prob.phi), dev(kap), None, None, F=[dev(f)], G=[ones])
+        s.solve(uf, U if keep else None)
         torch.cuda.synchronize()
-        return U
+        return uf
 
-    u_obs = forward(kobs)[M].clone()
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    f0 = prob.F[0]
+    u_obs = forward(kobs, f0).clone()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    gk = torch.zeros(n, dtype=torch.float64, device="cuda")
+    gf = torch.zeros(n, dtype=torch.float64, device="cuda")
     with torch.cuda.stream(stream):
         e[0].record(stream)
-        forward(prob.kappa0)
+        forward(prob.kappa0, f0)
         e[1].record(stream)
-        gk = torch.zeros(n, dtype=torch.float64, device="cuda")
-        gf = torch.zeros(n, dtype=torch.float64, device="cuda")
         info = s.adjoint(U, U[M] - u_obs, gk, gf)
         e[2].record(stream)
+        gk2 = torch.zeros_like(gk)
+        gf2 = torch.zeros_like(gf)
+        info2 = s.adjoint(None, U[M] - u_obs, gk2, gf2)
+        e[3].record(stream)
     torch.cuda.synchronize()
     t_fwd = e[0].elapsed_time(e[1]) / 1e3
     t_adj = e[1].elapsed_time(e[2]) / 1e3
-    d = np.random.default_rng(5).standard_normal(n)
-    d /= np.linalg.norm(d)
-    h = 1e-5 * float(np.max(prob.kappa0))
-    J = lambda kap: 0.5 * float(torch.sum((forward(kap)[M] - u_obs) ** 2))
-    fd = (J(prob.kappa0 + h * d) - J(prob.kappa0 - h * d)) / (2 * h)
-    ad = float(gk.cpu().numpy() @ d)
+    t_ck = e[2].elapsed_time(e[3]) / 1e3
+    ck_diff = float(torch.max(torch.abs(gk2 - gk)) / torch.max(torch.abs(gk)))
+    gkh, gfh = gk.cpu().numpy(), gf.cpu().numpy()
+    J = lambda kap, f: 0.5 * float(torch.sum((forward(kap, f, keep=False) - u_obs) ** 2))
+    sk, sf, h = float(np.max(prob.kappa0)), float(np.max(np.abs(f0))), 1e-6
+    rng = np.random.default_rng(20)
+    worst = 0.0
+    for _ in range(3):
+        dk = rng.standard_normal(n)
+        df = rng.standard_normal(n)
+        dk /= np.linalg.norm(dk)
+        df /= np.linalg.norm(df)
+        fd = (J(prob.kappa0 + h * sk * dk, f0 + h * sf * df) - J(prob.kappa0 - h * sk * dk, f0 - h * sf * df)) / (2 * h)
+        ad = sk * (gkh @ dk) + sf * (gfh @ df)
+        worst = max(worst, abs(ad - fd) / abs(fd))
     return {"workload": "fids-adjoint n=4095 M=1024 gamma=0.5 alpha=1.4 kappa=lognormal GRF",
             "forward_s": t_fwd, "adjoint_s": t_adj, "adjoint_levels_per_s": M / t_adj,
-            "adjoint_iterations": info["iterations"], "status": info["status"],
-            "grad_dir_adjoint": ad, "grad_dir_central_difference": fd,
-            "grad_rel_diff": abs(ad - fd) / max(abs(fd), 1e-300)}
+            "adjoint_checkpointed_s": t_ck, "checkpoint_stride": int(math.ceil(math.sqrt(M))),
+            "checkpointed_vs_trajectory_max_rel_diff": ck_diff,
+            "recomputed_levels": info2["recomputed_levels"],
+            "adjoint_iterations": info["iterations"], "status": info["status"] or info2["status"],
+            "fd_directions": 3, "fd_h": h, "grad_vs_central_difference_max_rel": worst}
+
+
+MID_PAIRS = [(0.3, 0.8), (0.3, 1.2), (0.3, 1.8), (0.7, 0.8), (0.7, 1.2), (0.7, 1.8)]
+
+
+def mid_sample(torch, pkg, ti, stream, warm):
+    """The mid workload: n = 2^14 - 1, M = 2048, six (gamma, alpha) pairs,
+    each a whole march timed with CUDA events on the solver's stream (no L2
+    flush: the SOE history, ~2 MB x E, exceeds L2), for the default path
+    (double-single mixed solve, per-level Krylov choice), FP64 with the
+    same choice, and the paper's FP64 BiCGSTAB (x0 = 0)."""
+    arms = {"mixed": dict(precision="mixed_ds", krylov="auto", warm_start=warm),
+            "fp64": dict(precision="fp64", krylov="auto", warm_start=warm),
+            "paper_bicgstab": dict(precision="fp64", krylov="bicgstab", warm_start=False)}
+    rows = []
+    tot = {k: [0.0, 0, 0] for k in arms}
+    for g, a in MID_PAIRS:
+        prob = ti.config_mid(g, a, M=2048)
+        row = {"gamma": g, "alpha": a}
+        uM = {}
+        for name, kw in arms.items():
+            s = pkg.Solver(prob.alpha, prob.gamma, prob.l, prob.T, prob.n, prob.M, prob.r, prob.soe_tol,
+                           krylov_tol=1e-12, stream=stream, **kw)
+            s.set_problem_from(prob)
+            u = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                s.solve(u, sync=False)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            st = s.level_stats(1, prob.M)
+            its = sum(x["iterations"] for x in st)
+            row[name] = {"steps_per_s": prob.M / t, "krylov_its_per_s": its / t,
+                         "iterations_per_step": its / prob.M,
+                         "status": max(x["status"] for x in st)}
+            tot[name][0] += t
+            tot[name][1] += prob.M
+            tot[name][2] += its
+            uM[name] = u
+            s.close()
+        for name in ("mixed", "fp64"):
+            row[name + "_vs_paper_bicgstab_max_rel_diff_at_M"] = float(
+                torch.max(torch.abs(uM[name] - uM["paper_bicgstab"])) / torch.max(torch.abs(uM["paper_bicgstab"])))
+        rows.append(row)
+    out = {"workload": "fids-mid n=16383 M=2048, (gamma, alpha) in {0.3,0.7} x {0.8,1.2,1.8}",
+           "pairs": rows}
+    for name in arms:
+        t, steps, its = tot[name]
+        out[name + "_steps_per_s"] = steps / t
+        out[name + "_krylov_its_per_s"] = its / t
+    out["mixed_speedup_vs_fp64"] = out["mixed_steps_per_s"] / out["fp64_steps_per_s"]
+    out["mixed_speedup_vs_paper_bicgstab"] = out["mixed_steps_per_s"] / out["paper_bicgstab_steps_per_s"]
+    return out
 
 
 def current_u(torch, s):
@@ -527,6 +603,10 @@ def ours(args):
     if rank == 0 and not args.no_adjoint:
         adjoint = adjoint_sample(torch, pkg, ti, stream)
 
+    mid = None
+    if rank == 0 and not args.no_mid:
+        mid = mid_sample(torch, pkg, ti, stream, not args.cold_start)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample(prob, args.cpu_sample_n)
@@ -557,7 +637,7 @@ def ours(args):
                         kname: {"ms": lvl_ms, "bytes": lvl_bytes, "GB/s": lvl_gbs,
                                 "frac": lvl_gbs / peak}},
             "fp64": fp64, "e2e": e2e, "gpu_launches": (3 if kry == "auto" else 2) * K, "roofline": roof,
-            "cpu_baseline": cpu, "clocks": clk, "batched": batched, "adjoint": adjoint, "dids": dids,
+            "cpu_baseline": cpu, "clocks": clk, "batched": batched, "adjoint": adjoint, "dids": dids, "mid": mid,
         }
         print(json.dumps(line), flush=True)
     s_mx.close()

@@ -66,6 +66,10 @@ def lib():
                                      ctypes.c_int, _dp, _dp]
         L.or_lu_solve.restype = ctypes.c_int
         L.or_lu_solve.argtypes = [ctypes.c_int64, _dp, _dp]
+        L.or_level_rhs.restype = ctypes.c_int
+        L.or_level_rhs.argtypes = [ctypes.POINTER(OrProblem), ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp]
+        L.or_level_defect.restype = None
+        L.or_level_defect.argtypes = [ctypes.c_int64, _dp, ctypes.c_double, _dp, _dp, _dp, _dp]
         L.or_set_threads.restype = None
         L.or_set_threads.argtypes = [ctypes.c_int]
         L.or_get_threads.restype = ctypes.c_int
@@ -244,6 +248,40 @@ def march(scheme: str, alpha, gamma, l, T, r, n, M, phi, kappa, f, mu=None,
     if rc != 0:
         raise RuntimeError(f"or_march failed ({rc})")
     return U
+
+
+def level_rhs(scheme: str, alpha, gamma, l, T, r, n, M, m, U, f_m, soe=None, mu=None,
+              kappa_mu=None) -> np.ndarray:
+    """Right-hand side b^m of level m of Eq. (3.16gu) (FIDS, needs soe) or
+    Eq. (4.1) (DIDS) from the levels U (rows 0..m-1, e.g. a GPU march) and
+    the source f^m: the direct history sums with the direct weights."""
+    if mu is None:
+        mu, km = default_mu(alpha)
+        kappa_mu = km if kappa_mu is None else kappa_mu
+    if kappa_mu is None:
+        kappa_mu = 2 if mu == 2.0 else 1
+    Uc = np.ascontiguousarray(U[:m], dtype=np.float64)
+    assert Uc.shape == (m, n)
+    fm = _f64(f_m)
+    keep = [Uc, fm]
+    if soe is not None:
+        keep += [_f64(soe[0]), _f64(soe[1])]
+    p = OrProblem(alpha, gamma, l, T, r, mu, kappa_mu, n, M, _ptr(Uc), None, None,
+                  0 if soe is None else len(keep[2]), None if soe is None else _ptr(keep[2]),
+                  None if soe is None else _ptr(keep[3]), 0)
+    rhs = np.zeros(n)
+    if lib().or_level_rhs(ctypes.byref(p), 0 if scheme == "DIDS" else 1, m, _ptr(Uc), _ptr(fm), _ptr(rhs)) != 0:
+        raise ValueError("bad level or missing SOE table")
+    return rhs
+
+
+def level_defect(t, a, kappa, u, b) -> np.ndarray:
+    """d = b - (a u + kappa .* (A u)) with A the symmetric Toeplitz matrix of
+    first column t, in double-double arithmetic rounded once."""
+    t, kappa, u, b = _f64(t), _f64(kappa), _f64(u), _f64(b)
+    d = np.zeros(len(u))
+    lib().or_level_defect(len(u), _ptr(t), float(a), _ptr(kappa), _ptr(u), _ptr(b), _ptr(d))
+    return d
 
 
 def adjoint(alpha, gamma, l, T, r, n, M, phi, kappa_x, f_x, u_obs, soe, mu=None,

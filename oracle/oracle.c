@@ -258,6 +258,32 @@ static void level_weights(const or_problem* p, int scheme, int64_t m,
   }
 }
 
+/* Right-hand side of level m of Eq. (3.16gu) (FIDS) / Eq. (4.1) (DIDS)
+ * from the levels U (rows 0..m-1 of n) and the weights c_k = c_k^{(m)}:
+ * Gamma(1-g)^{-1}[ sum_{k=1}^{m-1} (c_{k+1}-c_k) u^k + c_1 u^0 ] + f^m. */
+static void level_rhs(const or_problem* p, int64_t m, const double* c, const double* U,
+                      const double* fm, double* rhs) {
+  const int64_t n = p->n;
+  const double Gg = tgamma(1.0 - p->gamma);
+  for (int64_t i = 0; i < n; ++i) rhs[i] = c[1] * U[i];
+  for (int64_t k = 1; k <= m - 1; ++k) {
+    double d = c[k + 1] - c[k];
+    const double* uk = U + k * n;
+    for (int64_t i = 0; i < n; ++i) rhs[i] += d * uk[i];
+  }
+  for (int64_t i = 0; i < n; ++i) rhs[i] = rhs[i] / Gg + fm[i];
+}
+
+int or_level_rhs(const or_problem* p, int scheme, int64_t m, const double* U, const double* fm,
+                 double* rhs) {
+  if (m < 1 || m > p->M || (scheme == 1 && p->soe_E < 1)) return -1;
+  double* c = (double*)malloc(sizeof(double) * (size_t)(m + 1));
+  level_weights(p, scheme, m, c);
+  level_rhs(p, m, c, U, fm, rhs);
+  free(c);
+  return 0;
+}
+
 int or_march(const or_problem* p, int scheme, double* U) {
   const int64_t n = p->n, M = p->M;
   double* t = (double*)malloc(sizeof(double) * (size_t)n);
@@ -271,16 +297,7 @@ int or_march(const or_problem* p, int scheme, double* U) {
   const int64_t last = (p->levels > 0 && p->levels < M) ? p->levels : M;
   for (int64_t m = 1; m <= last && status == 0; ++m) {
     level_weights(p, scheme, m, c);
-    /* right-hand side of Eq. (3.16gu)/(4.1):
-     * Gamma(1-g)^{-1}[ sum_{k=1}^{m-1} (c_{k+1}-c_k) u^k + c_1 u^0 ] + f^m */
-    for (int64_t i = 0; i < n; ++i) rhs[i] = c[1] * U[i];
-    for (int64_t k = 1; k <= m - 1; ++k) {
-      double d = c[k + 1] - c[k];
-      const double* uk = U + k * n;
-      for (int64_t i = 0; i < n; ++i) rhs[i] += d * uk[i];
-    }
-    const double* fm = p->f + m * n;
-    for (int64_t i = 0; i < n; ++i) rhs[i] = rhs[i] / Gg + fm[i];
+    level_rhs(p, m, c, U, p->f + m * n, rhs);
     /* M^{(m)} = c_m/Gamma(1-g) I + K^{(m)} A */
     const double* km = p->kappa + m * n;
     for (int64_t i = 0; i < n; ++i)
@@ -341,4 +358,62 @@ int or_adjoint(const or_problem* p, const double* U, const double* u_obs,
   }
   free(t); free(C); free(Lam); free(Mat); free(rhs); free(Au);
   return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Defect of a level equation, d = b - (a u + kappa .* (A u)), evaluated in
+ * double-double arithmetic and rounded once: every product is split exactly
+ * by an FMA (the error-free product), every sum by Knuth's TwoSum, as in
+ * the compensated dot product Dot2 of Ogita, Rump and Oishi (SIAM J. Sci.
+ * Comput. 26, 2005).  The result carries an error of a few units of
+ * 2^-104 times sum_j |terms|, so it stays meaningful where the defect is
+ * 1e-12 of b while the terms kappa_i t_{|i-j|} u_j are ~1e8 times larger
+ * (a plain FP64 sum would carry errors ~1e-16 of those).  Used to certify
+ * GPU levels through the bound of Lemma 3.3 and Theorem 3.1:
+ * ||u - u_exact||_inf <= ||d||_inf / a (diagonal dominance of a I + K A). */
+static void two_sum(double a, double b, double* s, double* e) {
+  const double x = a + b;
+  const double z = x - a;
+  *e = (a - (x - z)) + (b - z);
+  *s = x;
+}
+static void two_prod(double a, double b, double* p, double* e) {
+  const double x = a * b;
+  *e = fma(a, b, -x);
+  *p = x;
+}
+/* (hi, lo) += x * y */
+static void dd_add_prod(double* hi, double* lo, double x, double y) {
+  double p, ep, s, es;
+  two_prod(x, y, &p, &ep);
+  two_sum(*hi, p, &s, &es);
+  *hi = s;
+  *lo += es + ep;
+}
+
+void or_level_defect(int64_t n, const double* t, double a, const double* kappa, const double* u,
+                     const double* b, double* d) {
+#pragma omp parallel for schedule(dynamic, 16) num_threads(or_threads) if (or_threads > 1)
+  for (int64_t i = 0; i < n; ++i) {
+    /* (A u)_i as a double-double */
+    double h = 0.0, l = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+      const int64_t k = i > j ? i - j : j - i;
+      dd_add_prod(&h, &l, t[k], u[j]);
+    }
+    double ah, al;
+    two_sum(h, l, &ah, &al);  /* normalise */
+    /* kappa_i (ah + al): exact product of the high part, rounded low part */
+    double kh, kl;
+    two_prod(kappa[i], ah, &kh, &kl);
+    kl += kappa[i] * al;
+    /* b_i - a u_i - (kh + kl) */
+    double rh = b[i], rl = 0.0;
+    dd_add_prod(&rh, &rl, -a, u[i]);
+    double s, e;
+    two_sum(rh, -kh, &s, &e);
+    rh = s;
+    rl += e - kl;
+    d[i] = rh + rl;
+  }
 }

@@ -73,6 +73,10 @@ double or_fids_weight(double T, int64_t M, double r, double gamma, int64_t m,
 /* Row-update threads of or_lu_solve (default 1; results do not depend on it). */
 void or_set_threads(int t);
 int or_get_threads(void);
+/* d = b - (a u + kappa .* (A u)), A the symmetric Toeplitz matrix of first
+ * column t, in double-double arithmetic rounded once (threads as or_lu_solve). */
+void or_level_defect(int64_t n, const double* t, double a, const double* kappa, const double* u,
+                     const double* b, double* d);
 int or_lu_solve(int64_t n, double* A, double* b);
 
 /* y = A v for the symmetric Toeplitz matrix with first column t (dense
@@ -104,6 +108,11 @@ typedef struct {
 } or_problem;
 
 int or_march(const or_problem* p, int scheme, double* U);
+/* Right-hand side of level m (scheme 0 DIDS, 1 FIDS) from the levels U
+ * (rows 0..m-1 of n) and the source fm (n), with the mesh, weights and
+ * SOE table of p (p->kappa and p->f are not read).  0 on success. */
+int or_level_rhs(const or_problem* p, int scheme, int64_t m, const double* U, const double* fm,
+                 double* rhs);
 
 /* Adjoint of the FIDS march for J = 1/2 ||u^M - u_obs||^2 with
  * time-independent kappa (row 0 of p->kappa used for every level) and

@@ -401,3 +401,53 @@ def test_threaded_lu_gives_the_same_bits():
         oracle.set_threads(1)
     assert np.array_equal(x1, x4)
     assert oracle.get_threads() == 1
+
+
+def test_level_defect_matches_exact_rational_arithmetic():
+    """The double-double defect d = b - (a u + kappa .* (A u)) against the
+    exact value in rational arithmetic, on a case built to cancel: b is the
+    FP64 evaluation of a u + kappa .* (A u), so the exact defect is at the
+    rounding level of terms ~1e6 times larger, where a plain FP64
+    evaluation returns noise."""
+    from fractions import Fraction
+    rng = np.random.default_rng(4)
+    n = 12
+    t = np.concatenate(([3.0e6], -rng.uniform(1e4, 1e5, n - 1)))
+    u = rng.standard_normal(n)
+    kap = rng.uniform(0.2, 5.0, n)
+    a = 17.25
+    Au = np.array([sum(t[abs(i - j)] * u[j] for j in range(n)) for i in range(n)])
+    b = a * u + kap * Au
+    d = oracle.level_defect(t, a, kap, u, b)
+    F = Fraction
+    for i in range(n):
+        s = sum(F(t[abs(i - j)]) * F(u[j]) for j in range(n))
+        exact = F(b[i]) - (F(a) * F(u[i]) + F(kap[i]) * s)
+        mag = abs(a * u[i]) + kap[i] * sum(abs(t[abs(i - j)] * u[j]) for j in range(n))
+        assert abs(F(d[i]) - exact) <= F(2.0 ** -100 * mag) + abs(exact) * F(2.0 ** -52), i
+    # the threaded evaluation gives the same bits
+    try:
+        oracle.set_threads(3)
+        assert np.array_equal(oracle.level_defect(t, a, kap, u, b), d)
+    finally:
+        oracle.set_threads(1)
+
+
+@pytest.mark.parametrize("scheme", ["FIDS", "DIDS"])
+def test_level_rhs_is_the_march_right_hand_side(scheme):
+    """level_rhs(m) from the march's own levels 0..m-1 is the right-hand side
+    the march solved at level m: its levels satisfy their equations with it
+    to rounding, measured by the double-double defect."""
+    prob = ti.config_smallest(n=31, M=12)
+    tm, tau = oracle.graded_mesh(prob.T, prob.M, prob.r)
+    soe = oracle.soe_build(prob.gamma, tau[1], prob.T, prob.soe_tol) if scheme == "FIDS" else None
+    K, F = prob.kappa_table(tm), prob.f_table(tm)
+    U = oracle.march(scheme, prob.alpha, prob.gamma, prob.l, prob.T, prob.r, prob.n, prob.M, prob.phi,
+                     K, F, soe=soe)
+    t = oracle.ifl_symbol(prob.alpha, prob.n)
+    for m in (1, 2, 7, prob.M):
+        b = oracle.level_rhs(scheme, prob.alpha, prob.gamma, prob.l, prob.T, prob.r, prob.n, prob.M, m,
+                             U, F[m], soe=soe)
+        ahat = oracle.l1_weight(prob.T, prob.M, prob.r, prob.gamma, m, m) / math.gamma(1 - prob.gamma)
+        d = oracle.level_defect(t, ahat, K[m], U[m], b)
+        assert np.max(np.abs(d)) <= 1e-13 * np.max(np.abs(b)), (m, np.max(np.abs(d)))
