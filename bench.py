@@ -69,7 +69,10 @@ def parse():
                     help="arithmetic of the mixed arm's inner PBiCGSTAB: FP32, or double-single "
                          "(FP32 pairs, ~48-bit significand)")
     ap.add_argument("--batched-levels", type=int, default=128,
-                    help="levels of the batched workload timed (of M = 1024; 0 skips it)")
+                    help="levels of the batched workload on which mixed and FP64 are compared (of "
+                         "M = 1024; 0 skips the batched workload)")
+    ap.add_argument("--no-batched-full", action="store_true",
+                    help="skip timing the batched mixed path over all M = 1024 levels")
     return ap.parse_args()
 
 
@@ -253,12 +256,15 @@ def run_arm(torch, pkg, prob, precision, W, K, flush, stream, e2e=False, warm=Fa
     return s, ms, tim, tot
 
 
-def batched_sample(torch, pkg, ti, levels, rank, world, stream, warm=True):
+def batched_sample(torch, pkg, ti, levels, rank, world, stream, warm=True, full=True):
     """The batched workload: 512 independent problems (n log-uniform in
     [2^9-1, 2^14-1], alpha ~ U(0.6, 1.9), gamma ~ U(0.2, 0.9), M = 1024),
-    this rank's share (instance i on rank i mod world), first `levels`
-    levels, mixed and FP64, one persistent cluster launch each.  Its working
-    set (the SOE histories, ~3 GB) is far above L2."""
+    this rank's share (instance i on rank i mod world).  The launch plan
+    (one persistent launch or two size classes, cluster size per launch) is
+    chosen by tsfde_batch_tune on a 4-level probe and reported with every
+    plan it timed.  Timed with CUDA events: the mixed path over all M levels
+    (full=True), and mixed against FP64 over the first `levels` levels.  Its
+    working set (the SOE histories, ~3 GB) is far above L2."""
     M = 1024
     ns, al, ga = ti.batched_instance_params()
     mine = shard(len(ns), rank, world)
@@ -270,8 +276,13 @@ def batched_sample(torch, pkg, ti, levels, rank, world, stream, warm=True):
                          kappa=dev(p.kappa0), f=dev(p.F[0])))
     unknowns = sum(d["n"] for d in inst)
     out = {"workload": "fids-batched 512 instances n=U_log[511,16383] M=1024 (alpha, gamma random)",
-           "instances": len(inst), "levels_timed": levels, "unknowns": unknowns,
+           "instances": len(inst), "levels_compared": levels, "unknowns": unknowns,
            "initial_guess": "u^{m-1}" if warm else "0"}
+    t0 = time.perf_counter()
+    best, tried = pkg.batch_tune(inst, M, probe_levels=4, precision="mixed", warm_start=warm, stream=stream)
+    out["plan"] = best
+    out["plans_tried"] = tried
+    out["tune_s"] = time.perf_counter() - t0
     us = {}
     # FP64 at 1e-12 drifts by up to 3e-10 over these levels (its recursive
     # residual accumulates per-level errors of ~1e-12 against a huge ahat);
@@ -279,25 +290,27 @@ def batched_sample(torch, pkg, ti, levels, rank, world, stream, warm=True):
     # does at 1e-12 (within 2e-13): the arms are compared at equal accuracy.
     tols = {"mixed": 1e-12, "fp64": 1e-13}
     out["krylov_tol"] = tols
-    for prec in ("mixed", "fp64"):
+    runs = [("mixed", levels), ("fp64", levels)] + ([("mixed_full_M", M)] if full else [])
+    for key, lv in runs:
+        prec = "fp64" if key == "fp64" else "mixed"
         bs = pkg.BatchSolver(inst, M, precision=prec, stream=stream, warm_start=warm,
-                             krylov_tol=tols[prec])
+                             krylov_tol=tols[prec], plan=best)
         outs = [torch.zeros(d["n"], dtype=torch.float64, device="cuda") for d in inst]
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
             e0.record(stream)
-            info = bs.solve(outs, levels=levels)
+            info = bs.solve(outs, levels=lv)
             e1.record(stream)
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3
-        clusters, q = bs.shape
-        out[prec] = {"s": t, "instance_levels_per_s": len(inst) * levels / t,
-                     "unknown_levels_per_s": unknowns * levels / t,
-                     "krylov_its": info["iterations"], "outer": info["outer"],
-                     "fp64_levels": info["fp64_levels"], "status": info["status"],
-                     "clusters": clusters, "cluster_size": q}
-        us[prec] = [u.cpu().numpy() for u in outs]
+        out[key] = {"levels": lv, "s": t, "instance_levels_per_s": len(inst) * lv / t,
+                    "unknown_levels_per_s": unknowns * lv / t,
+                    "krylov_its": info["iterations"], "outer": info["outer"],
+                    "fp64_levels": info["fp64_levels"], "status": info["status"],
+                    "max_final_rel_residual": info["max_rel_residual"]}
+        if key != "mixed_full_M":
+            us[key] = [u.cpu().numpy() for u in outs]
         del bs
     out["mixed_vs_fp64_max_rel_err"] = max(
         float(np.max(np.abs(a - b)) / np.max(np.abs(b))) for a, b in zip(us["mixed"], us["fp64"]))
@@ -586,12 +599,13 @@ def ours(args):
     batched = None
     if args.batched_levels > 0:
         batched = batched_sample(torch, pkg, ti, args.batched_levels, rank, world, stream,
-                                 warm=not args.cold_start)
+                                 warm=not args.cold_start, full=not args.no_batched_full)
         if world > 1:
-            tm = max_over_ranks([batched["mixed"]["s"], batched["fp64"]["s"]], "cuda")
-            for k, prec in enumerate(("mixed", "fp64")):
-                batched[prec]["s_max_over_ranks"] = tm[k]
-                batched[prec]["instance_levels_per_s"] = 512 * args.batched_levels / tm[k]
+            keys = [k for k in ("mixed", "fp64", "mixed_full_M") if k in batched]
+            tm = max_over_ranks([batched[k]["s"] for k in keys], "cuda")
+            for k, key in enumerate(keys):
+                batched[key]["s_max_over_ranks"] = tm[k]
+                batched[key]["instance_levels_per_s"] = 512 * batched[key]["levels"] / tm[k]
 
     dids = None
     dl = prob.M if args.dids_levels is None else min(args.dids_levels, prob.M)

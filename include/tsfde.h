@@ -81,8 +81,8 @@ enum { TSFDE_HISTORY_SOE = 0, TSFDE_HISTORY_DIRECT = 1 };
  * any kappa > 0.  One product with A and one with the preconditioner per
  * iteration instead of two of each; the stopping test is the same, on the
  * residual of the original system.  The mixed paths use it for their inner
- * solves and their FP64 finish.  Grid engine only; the adjoint sweep and the
- * batched solve use BiCGSTAB. */
+ * solves and their FP64 finish, and tsfde_adjoint its transposed solves.
+ * Grid engine only; the batched solve uses BiCGSTAB. */
 /* AUTO: each level of tsfde_step / tsfde_solve takes whichever of the two
  * is cheaper there, decided on the device from measured level times: the
  * method of the previous level, unless the other one was faster at its latest
@@ -211,7 +211,7 @@ typedef struct tsfde_timing {
 typedef struct tsfde_adjoint_info {
   int status;           /* first non-OK level status, else TSFDE_OK          */
   int64_t failed_level; /* level of that status, 0 if none                  */
-  int64_t iterations;   /* total BiCGSTAB iterations of the transposed solves */
+  int64_t iterations;   /* total Krylov iterations of the transposed solves */
   int max_iterations;
   double max_rel_residual;
   int64_t recomputed_levels; /* forward levels marched again from the
@@ -293,8 +293,10 @@ int tsfde_get_symbol(const tsfde_ctx* ctx, double* t);
  * (tsfde_set_problem with kappa1 = NULL) and whose source f^m is the
  * caller's fixed f for every level.
  *
- * Reverse in time, m = M..1, in FP64 with the right-preconditioned
- * PBiCGSTAB of the forward path on the transposed operator:
+ * Reverse in time, m = M..1, in FP64 with the context's level solver on the
+ * transposed operator (BiCGSTAB; or PCG on (ahat_m K^{-1} + A) mu = g^m,
+ * lambda^m = K^{-1} mu, whose residual is that of the transposed system;
+ * with TSFDE_KRYLOV_AUTO the method that solved forward level m):
  *   (ahat_m I + A K) lambda^m = g^m,   g^M = dJ/du^M,
  *   g^m = ahat_{m+1} lambda^{m+1}
  *         - sum_j (c_{j,m+1} Y_j^{(m+1)} - c_{j,m+2} Y_j^{(m+2)}),  m < M,
@@ -371,8 +373,47 @@ int tsfde_batch_solve(tsfde_batch* b, int64_t levels, double* const* u_final,
 /* Per-instance totals of the last solve (status, iterations, outer = sweeps,
  * E_active = levels finished in FP64, rel_residual = worst level). */
 int tsfde_batch_instance_stats(const tsfde_batch* b, int i, tsfde_step_info* out);
-/* Thread-block clusters the persistent launch uses and CTAs per cluster. */
+/* Thread-block clusters the persistent launch uses and CTAs per cluster
+ * (of the first launch; tsfde_batch_get_plan has every launch). */
 int tsfde_batch_shape(const tsfde_batch* b, int* clusters, int* cluster_size);
+
+/* Launch plan of a batched solve.  The instances form one persistent launch
+ * (classes = 1) or two launched side by side on two streams (classes = 2:
+ * instances with n >= split_n in the first).  Every launch has one cluster
+ * size (CTAs per cluster, 4, 8 or 16; 0 in a requested plan: the size that
+ * keeps the most CTAs resident) and one shared-memory layout sized for its
+ * largest transform, because CUDA fixes both per launch.  The cluster size
+ * is the tile schedule of the cluster FFTs: CTA q of Q owns N2/Q columns of
+ * the column passes and N1/(2Q) row pairs of the row pass; the FFT stages
+ * are radix 16 in registers (last stage radix 2^(lg N mod 4)). */
+typedef struct tsfde_batch_plan {
+  int classes;             /* persistent launches, 1 or 2                   */
+  int64_t split_n;         /* classes = 2: n >= split_n go to the first     */
+  int cluster_size[2];     /* per launch                                    */
+  int clusters[2];         /* clusters resident per launch (filled by setup) */
+  double probe_ms;         /* tsfde_batch_tune: the probe solve's time      */
+} tsfde_batch_plan;
+
+/* tsfde_batch_setup with an explicit launch plan (NULL: the default plan,
+ * two classes split at n = 8193, each with its most-resident cluster size,
+ * or opts.cluster_size when set). */
+int tsfde_batch_setup_plan(tsfde_batch** out, int B, const tsfde_instance* inst, int64_t M,
+                           const tsfde_opts* opts, const tsfde_batch_plan* plan);
+/* The plan a batch was set up with (cluster sizes and residency filled in). */
+int tsfde_batch_get_plan(const tsfde_batch* b, tsfde_batch_plan* plan);
+/* Autotuner of the launch plan (the paper has none: it solves one problem at
+ * a time).  Candidates: one launch with cluster size 4, 8 or 16; two launches
+ * split at n = 8193 or n = 4097 with cluster sizes (8 or 16, 4 or 8).  Each
+ * candidate that fits the device is set up for these instances and times a
+ * solve of the first probe_levels levels (1..M) with CUDA events on
+ * opts->stream, after one untimed solve; identical plans are timed once.
+ * *best receives the fastest (probe_ms set); tried (capacity *ntried, both
+ * nullable) every timed plan, *ntried their count.  The caller then passes
+ * *best to tsfde_batch_setup_plan.  Allocates and frees its own device
+ * buffers; synchronises. */
+int tsfde_batch_tune(int B, const tsfde_instance* inst, int64_t M, const tsfde_opts* opts,
+                     int64_t probe_levels, tsfde_batch_plan* best, tsfde_batch_plan* tried,
+                     int* ntried);
 void tsfde_batch_destroy(tsfde_batch* b);
 
 /* Engine the context's mixed level solves use: TSFDE_ENGINE_GRID or

@@ -79,6 +79,17 @@ class tsfde_batch_info(ctypes.Structure):
                 ("max_rel_residual", ctypes.c_double)]
 
 
+class tsfde_batch_plan(ctypes.Structure):
+    _fields_ = [("classes", ctypes.c_int), ("split_n", ctypes.c_int64),
+                ("cluster_size", ctypes.c_int * 2), ("clusters", ctypes.c_int * 2),
+                ("probe_ms", ctypes.c_double)]
+
+
+def plan_dict(p):
+    return {"classes": p.classes, "split_n": p.split_n, "cluster_size": list(p.cluster_size),
+            "clusters": list(p.clusters), "probe_ms": p.probe_ms}
+
+
 class tsfde_timing(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int64), ("rhs_ms", ctypes.c_double),
                 ("level_ms", ctypes.c_double)]
@@ -114,6 +125,14 @@ _SIGNATURES = [
     ("tsfde_batch_instance_stats", ctypes.c_int, [_V, ctypes.c_int, ctypes.POINTER(tsfde_step_info)]),
     ("tsfde_batch_shape", ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("tsfde_batch_destroy", None, [_V]),
+    ("tsfde_batch_setup_plan", ctypes.c_int, [ctypes.POINTER(_V), ctypes.c_int,
+                                              ctypes.POINTER(tsfde_instance), ctypes.c_int64,
+                                              ctypes.POINTER(tsfde_opts), ctypes.POINTER(tsfde_batch_plan)]),
+    ("tsfde_batch_get_plan", ctypes.c_int, [_V, ctypes.POINTER(tsfde_batch_plan)]),
+    ("tsfde_batch_tune", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(tsfde_instance), ctypes.c_int64,
+                                        ctypes.POINTER(tsfde_opts), ctypes.c_int64,
+                                        ctypes.POINTER(tsfde_batch_plan), ctypes.POINTER(tsfde_batch_plan),
+                                        ctypes.POINTER(ctypes.c_int)]),
     ("tsfde_get_level_stats", ctypes.c_int, [_V, ctypes.c_int64, ctypes.c_int64,
                                              ctypes.POINTER(tsfde_step_info)]),
     ("tsfde_get_solution", ctypes.c_int, [_V, _V]),
@@ -389,37 +408,24 @@ class BatchSolver:
 
     def __init__(self, instances, M, *, precision="mixed", precond="strang", krylov_tol=1e-12,
                  max_it=2000, inner_tol=1e-2, max_outer=60, inner_max_it=40, mu=None,
-                 kappa_mu=None, stream=None, cluster_size=0, warm_start=False):
+                 kappa_mu=None, stream=None, cluster_size=0, warm_start=False, plan=None):
+        """plan: None (the default launch plan), a tsfde_batch_plan, or a dict
+        as batch_tune / .plan return."""
         lib = load_library()
-        o = default_opts()
-        o.cluster_size = cluster_size
-        o.warm_start = 1 if warm_start else 0
-        o.krylov_tol = krylov_tol
-        o.max_it = max_it
-        o.precision = {"fp64": TSFDE_FP64, "mixed": TSFDE_MIXED}[precision]
-        o.precond = {"strang": TSFDE_STRANG, "none": TSFDE_PRECOND_NONE}[precond]
-        o.inner_tol = inner_tol
-        o.max_outer = max_outer
-        o.inner_max_it = inner_max_it
-        o.mu = 0.0 if mu is None else mu
-        o.kappa_mu = 0 if kappa_mu is None else kappa_mu
-        if stream is not None:
-            o.stream = _stream_handle(stream)
-        B = len(instances)
-        arr = (tsfde_instance * B)()
-        self.ns = []
-        for i, d in enumerate(instances):
-            g = float(d["gamma"])
-            n = int(d["n"])
-            arr[i] = tsfde_instance(float(d["alpha"]), g, float(d.get("l", 1.0)), float(d.get("T", 1.0)),
-                                    float(d.get("r", (2.0 - g) / g)), n, float(d.get("soe_tol", 1e-12)),
-                                    _dev(d["phi"], n, "phi"), _dev(d["kappa"], n, "kappa"),
-                                    _dev(d["f"], n, "f"))
-            self.ns.append(n)
+        o, arr = _batch_args(instances, precision, precond, krylov_tol, max_it, inner_tol, max_outer,
+                             inner_max_it, mu, kappa_mu, stream, cluster_size, warm_start)
+        self.ns = [int(d["n"]) for d in instances]
         self.lib = lib
-        self.B, self.M = B, int(M)
+        self.B, self.M = len(instances), int(M)
         self.ctx = ctypes.c_void_p()
-        _check(lib.tsfde_batch_setup(ctypes.byref(self.ctx), B, arr, self.M, ctypes.byref(o)))
+        pp = None if plan is None else ctypes.byref(_as_plan(plan))
+        _check(lib.tsfde_batch_setup_plan(ctypes.byref(self.ctx), self.B, arr, self.M, ctypes.byref(o), pp))
+
+    @property
+    def plan(self):
+        p = tsfde_batch_plan()
+        _check(self.lib.tsfde_batch_get_plan(self.ctx, ctypes.byref(p)))
+        return plan_dict(p)
 
     def __del__(self):
         if getattr(self, "ctx", None):
@@ -449,6 +455,59 @@ class BatchSolver:
         info = tsfde_step_info()
         _check(self.lib.tsfde_batch_instance_stats(self.ctx, i, ctypes.byref(info)))
         return _info_dict(info)
+
+
+def _batch_args(instances, precision="mixed", precond="strang", krylov_tol=1e-12, max_it=2000,
+                inner_tol=1e-2, max_outer=60, inner_max_it=40, mu=None, kappa_mu=None, stream=None,
+                cluster_size=0, warm_start=False):
+    o = default_opts()
+    o.cluster_size = cluster_size
+    o.warm_start = 1 if warm_start else 0
+    o.krylov_tol = krylov_tol
+    o.max_it = max_it
+    o.precision = {"fp64": TSFDE_FP64, "mixed": TSFDE_MIXED}[precision]
+    o.precond = {"strang": TSFDE_STRANG, "none": TSFDE_PRECOND_NONE}[precond]
+    o.inner_tol = inner_tol
+    o.max_outer = max_outer
+    o.inner_max_it = inner_max_it
+    o.mu = 0.0 if mu is None else mu
+    o.kappa_mu = 0 if kappa_mu is None else kappa_mu
+    if stream is not None:
+        o.stream = _stream_handle(stream)
+    B = len(instances)
+    arr = (tsfde_instance * B)()
+    for i, d in enumerate(instances):
+        g = float(d["gamma"])
+        n = int(d["n"])
+        arr[i] = tsfde_instance(float(d["alpha"]), g, float(d.get("l", 1.0)), float(d.get("T", 1.0)),
+                                float(d.get("r", (2.0 - g) / g)), n, float(d.get("soe_tol", 1e-12)),
+                                _dev(d["phi"], n, "phi"), _dev(d["kappa"], n, "kappa"),
+                                _dev(d["f"], n, "f"))
+    return o, arr
+
+
+def _as_plan(p):
+    if isinstance(p, tsfde_batch_plan):
+        return p
+    q = tsfde_batch_plan()
+    q.classes = int(p["classes"])
+    q.split_n = int(p.get("split_n", 0))
+    for k in range(2):
+        q.cluster_size[k] = int(p["cluster_size"][k])
+    return q
+
+
+def batch_tune(instances, M, probe_levels=4, **kw):
+    """Autotune the batched launch plan (tsfde_batch_tune): returns
+    (best plan, list of every timed plan) as dicts; kw as BatchSolver."""
+    lib = load_library()
+    o, arr = _batch_args(instances, **kw)
+    best = tsfde_batch_plan()
+    tried = (tsfde_batch_plan * 16)()
+    nt = ctypes.c_int(16)
+    _check(lib.tsfde_batch_tune(len(instances), arr, int(M), ctypes.byref(o), int(probe_levels),
+                                ctypes.byref(best), tried, ctypes.byref(nt)))
+    return plan_dict(best), [plan_dict(tried[k]) for k in range(nt.value)]
 
 
 def toeplitz_apply_static(alpha, n, v, y, l=1.0, mu=None, kappa_mu=None, stream=None):

@@ -947,7 +947,7 @@ int tsfde_get_engine(const tsfde_ctx* c) { return c ? c->engine : -1; }
 // the reversed SOE recurrence, or dJ/du^M at m = M), the transposed level
 // solve into lambda^m and the gradient terms with u^m (dev n).
 static int adjoint_level(tsfde_ctx* c, int64_t m, const double* um, const double* dJ, double* grad_kappa,
-                         double* grad_f) {
+                         double* grad_f, int krylov) {
   const int64_t n = c->n, M = c->M;
   cudaStream_t s = c->stream;
   cudaError_t e;
@@ -984,6 +984,8 @@ static int adjoint_level(tsfde_ctx* c, int64_t m, const double* um, const double
   A.k32 = c->k32;
   A.r64 = c->r64;
   A.stat = c->adjStats + m;
+  A.krylov = krylov;
+  A.hinv64 = c->hinv64;
   AdjGradArgs Gd{um, grad_kappa, grad_f};
   if ((e = launch_level_adj(A, Gd, s)) != cudaSuccess) return cuda_fail(c, e, "adjoint level kernel");
   return TSFDE_OK;
@@ -1023,10 +1025,22 @@ int tsfde_adjoint(tsfde_ctx* c, const double* u_all, const double* dJ, double* g
   // kappa of every level is kappa0
   if ((e = launch_convert(c->kap0, c->kappa64, c->kappa32, (int)n, s)) != cudaSuccess)
     return cuda_fail(c, e, "convert kernel");
+  // Krylov method of each reverse level: the context's; with AUTO, the one
+  // that solved the same forward level (the transposed system has the same
+  // balance of ahat K^{-1} against A)
+  std::vector<int> kry(M + 1, c->opts.krylov == TSFDE_KRYLOV_PCG ? TSFDE_KRYLOV_PCG : TSFDE_KRYLOV_BICGSTAB);
+  if (c->opts.krylov == TSFDE_KRYLOV_AUTO && c->m == M) {
+    std::vector<StepStat> fw(M + 1);
+    if ((e = cudaMemcpyAsync(fw.data(), c->stats, sizeof(StepStat) * (M + 1), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_fail(c, e, "adjoint sync");
+    for (int64_t m = 1; m <= M; ++m) kry[m] = fw[m].method == 1 ? TSFDE_KRYLOV_PCG : TSFDE_KRYLOV_BICGSTAB;
+  }
   int st0 = TSFDE_OK;
   if (u_all) {
     for (int64_t m = M; m >= 1 && st0 == TSFDE_OK; --m)
-      st0 = adjoint_level(c, m, u_all + (size_t)m * n, dJ, grad_kappa, grad_f);
+      st0 = adjoint_level(c, m, u_all + (size_t)m * n, dJ, grad_kappa, grad_f, kry[m]);
   } else {
     // Checkpointed sweep: segments (k0, k1] of ck_stride levels, last first;
     // each is marched again from its checkpoint k0 into ck_seg, then swept
@@ -1046,7 +1060,7 @@ int tsfde_adjoint(tsfde_ctx* c, const double* u_all, const double* dJ, double* g
       }
       // the recomputed forward levels wrote kappa^m = kappa0 again: unchanged
       for (int64_t m = k1; m > k0 && st0 == TSFDE_OK; --m)
-        st0 = adjoint_level(c, m, c->ck_seg + (size_t)(m - k0 - 1) * n, dJ, grad_kappa, grad_f);
+        st0 = adjoint_level(c, m, c->ck_seg + (size_t)(m - k0 - 1) * n, dJ, grad_kappa, grad_f, kry[m]);
     }
     c->ck_recomputing = false;
     c->m = M;

@@ -188,6 +188,7 @@ struct tsfde_batch {
   int B = 0;
   int64_t M = 0;
   tsfde_opts opts{};
+  tsfde_batch_plan plan{};
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   std::vector<BClass> cls;
@@ -258,10 +259,15 @@ int pick_q(int64_t nmin, int64_t nmax, int want) {
 
 extern "C" {
 
-int tsfde_batch_setup(tsfde_batch** out, int B, const tsfde_instance* inst, int64_t M,
-                      const tsfde_opts* opts) {
+int tsfde_batch_setup_plan(tsfde_batch** out, int B, const tsfde_instance* inst, int64_t M,
+                           const tsfde_opts* opts, const tsfde_batch_plan* plan) {
   if (!out) return TSFDE_EINVAL;
   *out = nullptr;
+  if (plan && (plan->classes < 1 || plan->classes > 2)) return TSFDE_EINVAL;
+  for (int k = 0; plan && k < plan->classes; ++k)
+    if (plan->cluster_size[k] != 0 && plan->cluster_size[k] != 4 && plan->cluster_size[k] != 8 &&
+        plan->cluster_size[k] != 16)
+      return TSFDE_EINVAL;
   if (B < 1 || !inst || M < 1) return TSFDE_EINVAL;
   tsfde_opts o;
   if (opts) o = *opts; else tsfde_default_opts(&o);
@@ -293,22 +299,34 @@ int tsfde_batch_setup(tsfde_batch** out, int B, const tsfde_instance* inst, int6
   b->M = M;
   b->opts = o;
   b->stream = static_cast<cudaStream_t>(o.stream);
-  // size classes: transforms of length L >= 16384 (one CTA per SM with their
-  // shared-memory layout) and the rest (several CTAs per SM)
-  std::vector<int> Ls(B);
-  for (int i = 0; i < B; ++i) {
-    int L = 8;
-    while (L < 2 * inst[i].n - 1) L *= 2;
-    Ls[i] = L;
+  // Size classes.  Default plan: transforms of length L >= 16384 (n >= 8193:
+  // one CTA per SM with their shared-memory layout) and the rest (several
+  // CTAs per SM), each with the cluster size that keeps the most CTAs
+  // resident.  A plan (tsfde_batch_tune) may instead put every instance in
+  // one persistent launch, move the split, and fix each class's cluster size.
+  tsfde_batch_plan pl{};
+  if (plan) {
+    pl = *plan;
+  } else {
+    pl.classes = 2;
+    pl.split_n = 8193;
+    pl.cluster_size[0] = pl.cluster_size[1] = o.cluster_size;
   }
   std::vector<int> order(B);
   for (int i = 0; i < B; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return inst[a].n > inst[c].n; });
+  std::vector<int> want_q;
   {
     BClass big, small;
-    for (int i : order) (Ls[i] >= 16384 ? big : small).members.push_back(i);
-    if (!big.members.empty()) b->cls.push_back(big);
-    if (!small.members.empty()) b->cls.push_back(small);
+    for (int i : order) (pl.classes == 1 || inst[i].n >= pl.split_n ? big : small).members.push_back(i);
+    if (!big.members.empty()) {
+      b->cls.push_back(big);
+      want_q.push_back(pl.cluster_size[0]);
+    }
+    if (!small.members.empty()) {
+      b->cls.push_back(small);
+      want_q.push_back(pl.cluster_size[pl.classes == 2 ? 1 : 0]);
+    }
   }
   std::vector<int> cls_of(B, 0);
   for (size_t k = 0; k < b->cls.size(); ++k) {
@@ -319,7 +337,7 @@ int tsfde_batch_setup(tsfde_batch** out, int B, const tsfde_instance* inst, int6
       lo = std::min(lo, inst[i].n);
       hi = std::max(hi, inst[i].n);
     }
-    C.Q = pick_q(lo, hi, o.cluster_size);
+    C.Q = pick_q(lo, hi, want_q[k]);
     if (C.Q == 0) {
       const int st = bfail(b, TSFDE_ENOTSUP, "no cluster size fits these instances on this device");
       tsfde_batch_destroy(b);
@@ -504,8 +522,109 @@ int tsfde_batch_setup(tsfde_batch** out, int B, const tsfde_instance* inst, int6
     }
   }
   b->stats.assign(B, StepStat{});
+  b->plan = pl;
+  b->plan.classes = (int)b->cls.size();
+  for (int k = 0; k < 2; ++k) {
+    b->plan.cluster_size[k] = k < (int)b->cls.size() ? b->cls[k].Q : 0;
+    b->plan.clusters[k] = k < (int)b->cls.size() ? b->cls[k].clusters : 0;
+  }
+  if (b->cls.size() == 1) b->plan.split_n = 0;
   *out = b;
   return TSFDE_OK;
+}
+
+int tsfde_batch_setup(tsfde_batch** out, int B, const tsfde_instance* inst, int64_t M,
+                      const tsfde_opts* opts) {
+  return tsfde_batch_setup_plan(out, B, inst, M, opts, nullptr);
+}
+
+int tsfde_batch_get_plan(const tsfde_batch* b, tsfde_batch_plan* plan) {
+  if (!b || !plan) return TSFDE_EINVAL;
+  *plan = b->plan;
+  return TSFDE_OK;
+}
+
+// Launch-plan search: every candidate is set up for the real batch and
+// times a solve of its first probe_levels levels (CUDA events on the
+// options' stream, after one untimed solve); the fastest is returned.
+int tsfde_batch_tune(int B, const tsfde_instance* inst, int64_t M, const tsfde_opts* opts,
+                     int64_t probe_levels, tsfde_batch_plan* best, tsfde_batch_plan* tried, int* ntried) {
+  if (!best || B < 1 || !inst || M < 1) return TSFDE_EINVAL;
+  if (probe_levels < 1 || probe_levels > M) return TSFDE_EINVAL;
+  const int cap = (ntried && tried) ? *ntried : 0;
+  if (ntried) *ntried = 0;
+  std::vector<tsfde_batch_plan> cand;
+  auto add = [&](int classes, int64_t split, int q0, int q1) {
+    tsfde_batch_plan p{};
+    p.classes = classes;
+    p.split_n = split;
+    p.cluster_size[0] = q0;
+    p.cluster_size[1] = q1;
+    cand.push_back(p);
+  };
+  for (int q : {4, 8, 16}) add(1, 0, q, 0);
+  for (int64_t split : {(int64_t)8193, (int64_t)4097})
+    for (int qb : {8, 16})
+      for (int qs : {4, 8}) add(2, split, qb, qs);
+  int64_t ntot = 0;
+  for (int i = 0; i < B; ++i) ntot += std::max<int64_t>(inst[i].n, 1);
+  void* out_buf = nullptr;
+  if (cudaMalloc(&out_buf, sizeof(double) * (size_t)ntot) != cudaSuccess) return TSFDE_ENOMEM;
+  std::vector<double*> outs(B);
+  {
+    double* q = static_cast<double*>(out_buf);
+    for (int i = 0; i < B; ++i) {
+      outs[i] = q;
+      q += std::max<int64_t>(inst[i].n, 1);
+    }
+  }
+  cudaStream_t s = opts ? static_cast<cudaStream_t>(opts->stream) : nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int st = TSFDE_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = TSFDE_ECUDA;
+  double best_ms = 0.0;
+  bool found = false;
+  std::vector<tsfde_batch_plan> done;
+  for (size_t c = 0; c < cand.size() && st == TSFDE_OK; ++c) {
+    tsfde_batch* b = nullptr;
+    const int rc = tsfde_batch_setup_plan(&b, B, inst, M, opts, &cand[c]);
+    if (rc == TSFDE_ENOTSUP || rc == TSFDE_ENOMEM) continue;  // this plan does not fit
+    if (rc != TSFDE_OK) { st = rc; break; }
+    // plans that end up identical to one already timed are skipped
+    bool dup = false;
+    for (const tsfde_batch_plan& d : done)
+      if (d.classes == b->plan.classes && d.split_n == b->plan.split_n &&
+          d.cluster_size[0] == b->plan.cluster_size[0] && d.cluster_size[1] == b->plan.cluster_size[1])
+        dup = true;
+    float ms = 0.f;
+    int r1 = TSFDE_OK;
+    if (!dup) {
+      r1 = tsfde_batch_solve(b, probe_levels, outs.data(), nullptr);
+      if (r1 == TSFDE_OK && cudaEventRecord(e0, s) == cudaSuccess) {
+        r1 = tsfde_batch_solve(b, probe_levels, outs.data(), nullptr);
+        if (r1 == TSFDE_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                               cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+          r1 = TSFDE_ECUDA;
+      }
+    }
+    tsfde_batch_plan got = b->plan;
+    tsfde_batch_destroy(b);
+    if (dup) continue;
+    if (r1 != TSFDE_OK) { st = r1; break; }
+    got.probe_ms = ms;
+    done.push_back(got);
+    if (ntried && *ntried < cap) tried[(*ntried)++] = got;
+    if (!found || ms < best_ms) {
+      best_ms = ms;
+      *best = got;
+      found = true;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(out_buf);
+  if (st == TSFDE_OK && !found) st = TSFDE_ENOTSUP;
+  return st;
 }
 
 int tsfde_batch_solve(tsfde_batch* b, int64_t levels, double* const* u_final,

@@ -644,7 +644,12 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
 // p = z + beta p with its forward column FFTs | row pass (A) | q = S p,
 // (p, q) | x += alpha p, r -= alpha q, ||K r||, forward column FFTs of r |
 // row pass (P^{-1}) | z = P^{-1} r, (r, z).
-template <typename R, class BInit, int KP = kPre>
+// TR selects the transposed level system (ahat I + A K) lambda = g of the
+// adjoint sweep: with mu = K lambda it reads (ahat K^{-1} + A) mu = g, the
+// same S with the right-hand side g itself, and its residual g - S mu is
+// that of the transposed system, so r starts at g and the test is on ||r||.
+// The caller recovers lambda = K^{-1} mu.
+template <typename R, class BInit, int KP = kPre, bool TR = false>
 __device__ SolveRes pcg(const DevPlan& P, const Smem<R>& sm, const KVecs<R>& V,
                         const R* __restrict__ kap, const R* __restrict__ hinv, double ahat,
                         bool prec, double tol, int max_it, BInit& binit) {
@@ -660,7 +665,7 @@ __device__ SolveRes pcg(const DevPlan& P, const Smem<R>& sm, const KVecs<R>& V,
     R acc = 0;
     auto pro = [&](int i) -> R {
       const R bi = binit(i);
-      const R ri = bi * hinv[i];
+      const R ri = TR ? bi : bi * hinv[i];
       V.x[i] = R(0);
       V.p[i] = R(0);
       V.r[i] = ri;
@@ -753,7 +758,7 @@ __device__ SolveRes pcg(const DevPlan& P, const Smem<R>& sm, const KVecs<R>& V,
         V.x[i] = V.x[i] + aR * V.p[i];
         const R ri = V.r[i] - aR * V.v[i];
         V.r[i] = ri;
-        const R kr = kap[i] * ri;
+        const R kr = TR ? ri : kap[i] * ri;
         acc += kr * kr;
         return ri;
       };

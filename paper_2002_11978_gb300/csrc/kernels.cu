@@ -306,7 +306,7 @@ static cudaError_t set_attrs(size_t smem) {
                       level64_kernel(2, 1), level64_kernel(4, 1), level32_kernel(2, 1),
                       level32_kernel(4, 1), levelds_kernel(2, 1), levelds_kernel(4, 1),
                       (const void*)k_apply64, (const void*)k_apply32, (const void*)k_apply_ds,
-                      level_adj_kernel()};
+                      level_adj_kernel(0), level_adj_kernel(1)};
   for (const void* k : ks) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -323,7 +323,7 @@ int coop_blocks_per_sm(size_t smem) {
                       level64_kernel(2, 1), level64_kernel(4, 1), level32_kernel(2, 1),
                       level32_kernel(4, 1), levelds_kernel(2, 1), levelds_kernel(4, 1),
                       (const void*)k_apply64, (const void*)k_apply32, (const void*)k_apply_ds,
-                      level_adj_kernel()};
+                      level_adj_kernel(0), level_adj_kernel(1)};
   for (const void* k : ks) {
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, smem) != cudaSuccess) return 0;
@@ -391,7 +391,8 @@ cudaError_t launch_level_adj(const LevelArgs& a, const AdjGradArgs& g, cudaStrea
   cudaError_t e = cudaMemsetAsync(a.P.bar, 0, sizeof(GridBarrier), s);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&a, (void*)&g};
-  return cudaLaunchCooperativeKernel(level_adj_kernel(), dim3(a.P.G), dim3(kThreads), args, smem, s);
+  const int pcg = a.krylov == TSFDE_KRYLOV_PCG ? 1 : 0;
+  return cudaLaunchCooperativeKernel(level_adj_kernel(pcg), dim3(a.P.G), dim3(kThreads), args, smem, s);
 }
 
 cudaError_t launch_apply(const ApplyArgs& a, int precision, cudaStream_t s) {

@@ -318,7 +318,7 @@ cudaError_t launch_level(const LevelArgs& a, int precision, cudaStream_t s);
 const void* level64_kernel(int kp, int pcg);
 const void* level32_kernel(int kp, int pcg);
 const void* levelds_kernel(int kp, int pcg);
-const void* level_adj_kernel();
+const void* level_adj_kernel(int pcg);
 // cluster engine (cluster.cu): mixed level solve with the FP32 inner solves
 // on one thread-block cluster; a.P.G must equal a.P.cl.G.
 cudaError_t launch_level_cluster(const LevelArgs& a, cudaStream_t s);

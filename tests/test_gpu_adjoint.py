@@ -42,17 +42,21 @@ def _forward(torch, s, prob, kap, f):
     return U
 
 
-@pytest.mark.parametrize("n,M", [(255, 32), (63, 16), (1, 4), (7, 1)])
-def test_adjoint_matches_dense_oracle(torch, n, M):
+@pytest.mark.parametrize("n,M,krylov", [(255, 32, "bicgstab"), (63, 16, "bicgstab"), (1, 4, "bicgstab"),
+                                        (7, 1, "bicgstab"), (255, 32, "pcg"), (63, 16, "pcg"),
+                                        (1, 4, "pcg"), (255, 32, "auto")])
+def test_adjoint_matches_dense_oracle(torch, n, M, krylov):
     """Same SOE table on both sides; the oracle solves every transposed level
     system by dense LU with the direct FIDS weights.  Forward and transposed
     solves run to a relative residual of 1e-14: the gradient is within about
     cond(level matrix) x tol of the dense one (cond ~1e3-1e4 at n = 255),
-    so 1e-14 is what brings it under 1e-10."""
+    so 1e-14 is what brings it under 1e-10.  The transposed solves run
+    BiCGSTAB, or PCG on (ahat K^{-1} + A) mu = g with lambda = K^{-1} mu, or
+    (auto) the method the forward march chose at each level."""
     prob, kobs = ti.config_adjoint(n=n, M=M)
     tm, tau = oracle.graded_mesh(prob.T, M, prob.r)
     soe = oracle.soe_build(prob.gamma, tau[1], prob.T, 1e-12)
-    _, _, _, s = _setup(torch, n, M, soe=soe, krylov_tol=1e-14)
+    _, _, _, s = _setup(torch, n, M, soe=soe, krylov_tol=1e-14, krylov=krylov)
     f0 = prob.F[0]
     u_obs = oracle.march("FIDS", prob.alpha, prob.gamma, prob.l, prob.T, prob.r, n, M, prob.phi,
                          np.tile(kobs, (M + 1, 1)), np.tile(f0, (M + 1, 1)), soe=soe)[M]

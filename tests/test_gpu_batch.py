@@ -156,3 +156,67 @@ def test_batch_warm_start_matches_cold(torch, precision):
     assert iw["status"] == 0, iw
     for a, b in zip(Uw, Uc):
         assert np.max(np.abs(a - b)) / np.max(np.abs(b)) < 1e-10
+
+
+def _mixed_specs():
+    # sizes across both default size classes: two of the large one
+    # (transforms of L = 16384 and 32768) and several small ones
+    return [(0, 16383, 1.1, 0.3), (1, 9000, 1.5, 0.5), (2, 4000, 1.7, 0.8), (3, 2047, 0.7, 0.4),
+            (4, 1500, 1.9, 0.6), (5, 700, 1.2, 0.2), (6, 511, 0.9, 0.9), (7, 3000, 1.4, 0.7)]
+
+
+def test_batch_tuner_returns_the_fastest_plan_and_it_solves(torch):
+    """tsfde_batch_tune times every launch plan that fits (one launch with
+    cluster size 4, 8 or 16; two launches split at n = 8193 or 4097) on a
+    probe solve and returns the fastest; a batch set up with that plan gives
+    the default plan's u^M (mixed, warm start) to 1e-10."""
+    import paper_2002_11978_gb300 as pkg
+    M = 16
+    inst, probs = _instances(torch, _mixed_specs(), M)
+    best, tried = pkg.batch_tune(inst, M, probe_levels=2, precision="mixed", warm_start=True)
+    assert len(tried) >= 2, tried
+    assert best["probe_ms"] == min(t["probe_ms"] for t in tried), (best, tried)
+    assert {t["classes"] for t in tried} == {1, 2}, tried
+    _, U0, info0 = _batch(torch, inst, M, precision="mixed", warm_start=True)
+    bs, U1, info1 = _batch(torch, inst, M, precision="mixed", warm_start=True, plan=best)
+    got = bs.plan
+    assert got["classes"] == best["classes"] and got["cluster_size"] == best["cluster_size"], (got, best)
+    assert info0["status"] == 0 and info1["status"] == 0
+    for a, b in zip(U0, U1):
+        assert np.max(np.abs(a - b)) / np.max(np.abs(a)) < 1e-10
+
+
+def test_batch_large_class_certified(torch):
+    """Instances of the large size class (n >= 8193: transforms of L = 16384
+    and 32768), mixed, warm start, on the batched workload's M = 1024 mesh.
+    u^m for m = 1..8 comes from batched solves through level m (the launch
+    is deterministic, so these are the levels of one march); at levels 2 and
+    8 the residual certificate of the single-problem tests (oracle.certify:
+    double-double defect with the direct FIDS history, Lemma 3.3) bounds the
+    error by 1e-10 of max|u^m|.  The SOE table is the library's for the same
+    parameters, read from a single-problem context."""
+    import math
+
+    import paper_2002_11978_gb300 as pkg
+    from oracle import certify
+    M = 1024
+    specs = [(0, 16383, 1.1, 0.3), (1, 9000, 1.5, 0.5), (2, 700, 1.7, 0.8)]
+    inst, probs = _instances(torch, specs, M)
+    bs = pkg.BatchSolver(inst, M, precision="mixed", warm_start=True)
+    traj = [[p.phi.copy()] for p in probs]
+    for m in range(1, 9):
+        outs = [torch.zeros(d["n"], dtype=torch.float64, device="cuda") for d in inst]
+        info = bs.solve(outs, levels=m)
+        assert info["status"] == 0, info
+        for k, u in enumerate(outs):
+            traj[k].append(u.cpu().numpy())
+    for k in (0, 1):
+        p = probs[k]
+        U = np.array(traj[k])
+        soe = pkg.Solver(p.alpha, p.gamma, p.l, p.T, p.n, M, p.r, 1e-12).soe()
+        t = oracle.ifl_symbol(p.alpha, p.n)
+        for m in (2, 8):
+            b = oracle.level_rhs("FIDS", p.alpha, p.gamma, p.l, p.T, p.r, p.n, M, m, U, p.F[0], soe=soe)
+            ahat = oracle.l1_weight(p.T, M, p.r, p.gamma, m, m) / math.gamma(1 - p.gamma)
+            bound, l33 = certify.certify_level(t, ahat, p.kappa0, U[m], b)
+            assert bound <= 1e-10 * np.max(np.abs(U[m])), (p.n, m, bound, l33)

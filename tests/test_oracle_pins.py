@@ -451,3 +451,35 @@ def test_level_rhs_is_the_march_right_hand_side(scheme):
         ahat = oracle.l1_weight(prob.T, prob.M, prob.r, prob.gamma, m, m) / math.gamma(1 - prob.gamma)
         d = oracle.level_defect(t, ahat, K[m], U[m], b)
         assert np.max(np.abs(d)) <= 1e-13 * np.max(np.abs(b)), (m, np.max(np.abs(d)))
+
+
+def test_certificate_bounds_the_true_error_tightly():
+    """oracle.certify: for a level solved by dense LU and then perturbed by a
+    known amount, the certified bound must lie above the true error
+    (computed against the LU solution, itself accurate to ~1e-14 here) and
+    within a factor 2 of it; the Lemma 3.3 bound alone is looser."""
+    from oracle import certify
+    n, a, alpha = 300, 18.0, 1.6
+    t = oracle.ifl_symbol(alpha, n)
+    kap = ti.log_minmax(ti.gaussian_field(n, 3), 0.2, 5.0)
+    b = np.random.default_rng(2).standard_normal(n) * 10
+    u_exact = oracle.lu_solve(a * np.eye(n) + kap[:, None] * oracle.dense_A(t), b)
+    for scale in (1e-7, 1e-10):
+        du = scale * np.random.default_rng(3).standard_normal(n) * np.max(np.abs(u_exact))
+        u = u_exact + du
+        bound, lemma = certify.certify_level(t, a, kap, u, b)
+        true = np.max(np.abs(u - u_exact))
+        # the LU reference carries its own rounding, ~1e-16 of max|u|
+        assert true - 1e-14 * np.max(np.abs(u_exact)) <= bound <= 2.0 * true, (scale, true, bound)
+        assert lemma >= bound
+
+
+def test_certificate_of_the_exact_solution_is_at_rounding_level():
+    from oracle import certify
+    n, a, alpha = 200, 1.0e3, 1.2
+    t = oracle.ifl_symbol(alpha, n)
+    kap = 1.0 + 0.5 * np.sin(np.pi * ti.interior_nodes(n))
+    b = np.random.default_rng(8).standard_normal(n)
+    u = oracle.lu_solve(a * np.eye(n) + kap[:, None] * oracle.dense_A(t), b)
+    bound, _ = certify.certify_level(t, a, kap, u, b)
+    assert bound <= 1e-13 * np.max(np.abs(u)), bound
