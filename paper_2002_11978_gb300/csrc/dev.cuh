@@ -55,11 +55,21 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
 }
 
 // --------------------------------------------------- shared-memory FFT
+// The shared twiddle table W_T^i is stored with one spare entry after every
+// eight (entry i at tpad(i)): the radix-4 stages read it with strides
+// T/(4 Ns), multiples of 8 entries (128 bytes for 16-byte entries) in the
+// middle stages, which would put up to 16 lanes of a warp on the same banks.
+__host__ __device__ __forceinline__ int tpad(int i) { return i + (i >> 3); }
+// Entries of the padded table for a table of T, rounded up to even so that
+// the following tables stay 16-byte aligned.
+__host__ __device__ __forceinline__ int tpad_len(int T) { return (T + (T >> 3) + 1) & ~1; }
+
 // Stockham autosort FFT (radix 4, one radix-2 stage when log2 N is odd) of
 // B independent length-N sequences held in shared memory with layout
 // [k][b] (element k of sequence b at k*B + b).  `a` holds the input, `b`
 // is scratch of the same size; the function returns whichever buffer holds
-// the result.  tw[k] = e^{-2 pi i k / T} for k < T, T >= N a power of two.
+// the result.  tw[tpad(k)] = e^{-2 pi i k / T} for k < T, T >= N a power of
+// two.
 // INV selects e^{+...}; neither direction normalises.
 template <typename R, bool INV>
 __device__ __forceinline__ cplx<R>* fft_batch(cplx<R>* a, cplx<R>* b, int N, int lgB,
@@ -85,7 +95,7 @@ __device__ __forceinline__ cplx<R>* fft_batch(cplx<R>* a, cplx<R>* b, int N, int
         Z v2 = in[((j + 2 * Q) << lgB) + bb];
         Z v3 = in[((j + 3 * Q) << lgB) + bb];
         if (Ns > 1) {
-          Z w1 = tw[k * st], w2 = tw[2 * k * st], w3 = tw[3 * k * st];
+          Z w1 = tw[tpad(k * st)], w2 = tw[tpad(2 * k * st)], w3 = tw[tpad(3 * k * st)];
           if (INV) { w1 = cconj(w1); w2 = cconj(w2); w3 = cconj(w3); }
           v1 = cmul(v1, w1); v2 = cmul(v2, w2); v3 = cmul(v3, w3);
         }
@@ -110,7 +120,7 @@ __device__ __forceinline__ cplx<R>* fft_batch(cplx<R>* a, cplx<R>* b, int N, int
         Z v0 = in[(j << lgB) + bb];
         Z v1 = in[((j + H) << lgB) + bb];
         if (Ns > 1) {
-          Z w = tw[k * st];
+          Z w = tw[tpad(k * st)];
           if (INV) w = cconj(w);
           v1 = cmul(v1, w);
         }

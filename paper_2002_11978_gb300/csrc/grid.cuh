@@ -87,23 +87,26 @@ struct SmemAll {
   Smem<dsf> s;  // tw is NULL unless the plan has double-single tables
 };
 
-// Shared memory: [tw64 T][tw32 T][twds T][bufA W][bufB W][red 64]
+// Shared memory: [tw64 Tp][tw32 Tp][twds Tp][bufA W][bufB W][red 64], the
+// twiddle tables padded (Tp = tpad_len(T), entry k at tpad(k); see dev.cuh)
 __device__ __forceinline__ SmemAll smem_setup(const DevPlan& P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   char* base = reinterpret_cast<char*>(smem_raw);
+  const size_t Tp = (size_t)tpad_len(P.T);
   double2* tw64 = reinterpret_cast<double2*>(base);
-  float2* tw32 = reinterpret_cast<float2*>(base + (size_t)P.T * sizeof(double2));
-  dsf2* twds = reinterpret_cast<dsf2*>(base + (size_t)P.T * (sizeof(double2) + sizeof(float2)));
-  char* wbase = base + (size_t)P.T * (2 * sizeof(double2) + sizeof(float2));
+  float2* tw32 = reinterpret_cast<float2*>(base + Tp * sizeof(double2));
+  dsf2* twds = reinterpret_cast<dsf2*>(base + Tp * (sizeof(double2) + sizeof(float2)));
+  char* wbase = base + Tp * (2 * sizeof(double2) + sizeof(float2));
   double2* bA = reinterpret_cast<double2*>(wbase);
   double2* bB = bA + P.W;
   double* red = reinterpret_cast<double*>(bB + P.W);
   const int stride = P.L / P.T;
   const bool ds = P.twLds != nullptr;
   for (int k = threadIdx.x; k < P.T; k += blockDim.x) {
-    tw64[k] = P.twL64[k * stride];
-    tw32[k] = P.twL32[k * stride];
-    if (ds) twds[k] = P.twLds[k * stride];
+    const int kp = tpad(k);
+    tw64[kp] = P.twL64[k * stride];
+    tw32[kp] = P.twL32[k * stride];
+    if (ds) twds[kp] = P.twLds[k * stride];
   }
   __syncthreads();
   SmemAll s;
@@ -171,8 +174,10 @@ constexpr int kPre = 4;
 // column FFTs over j1 (j = N2 j1 + j2), twiddle W_Nc^{j2 k1}, store
 // S1[k1*N2 + j2].  Without FULL only rows j1 < N1/2 can be non-zero
 // (nin <= L/2).
+// out: where the column transforms go (NULL: S1).
 template <typename R, bool FULL, int KP = kPre, class Pro>
-__device__ void passA_real(const DevPlan& P, const Smem<R>& sm, int nin, Pro& pro) {
+__device__ void passA_real(const DevPlan& P, const Smem<R>& sm, int nin, Pro& pro,
+                           cplx<R>* out = nullptr) {
   typedef cplx<R> Z;
   const Geo& g = P.gr;
   const int lc = lgct<R>(g), ct = 1 << lc;
@@ -181,7 +186,7 @@ __device__ void passA_real(const DevPlan& P, const Smem<R>& sm, int nin, Pro& pr
   const int total = N1 << lc;
   const int rows = FULL ? N1 : (N1 >> 1);
   const int tstride = P.L / g.Nfft;
-  Z* S1 = reinterpret_cast<Z*>(P.S1);
+  Z* S1 = out ? out : reinterpret_cast<Z*>(P.S1);
   const Z* tw = twL<R>(P);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int c0 = tile << lc;
@@ -272,10 +277,24 @@ enum { MID_APPLY = 0, MID_SPEC = 1, MID_CONV = 2 };
 //  MID_SPEC: forward only; stores sa = Re X_k / Nc, sb = Re conj X_k' / Nc
 //    (the spectrum of an even real sequence is real).
 //  MID_CONV: complex product Z'_k = Z_k * conv_k (geometry gc).
-template <typename R, int MID, int KP = kPre>
+// Row input of a pass B: the combination a + cb b + cc c of up to three
+// column transforms (b, c NULL when absent), optionally kept in `keep`.
+// The column transforms are linear, so a combination of transforms is the
+// transform of the combination: the Krylov loops use this to form the
+// transform of a new search direction without a column pass of its own.
+template <typename R> struct RowIn {
+  const cplx<R>* a;
+  const cplx<R>* b;
+  R cb;
+  const cplx<R>* c;
+  R cc;
+  cplx<R>* keep;
+};
+
+template <typename R, int MID, int KP = kPre, bool COMB = false>
 __device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__ sa,
                       const R* __restrict__ sb, R* sa_out, R* sb_out,
-                      const cplx<R>* __restrict__ conv) {
+                      const cplx<R>* __restrict__ conv, const RowIn<R>* in = nullptr) {
   typedef cplx<R> Z;
   const Geo& g = (MID == MID_CONV) ? P.gc : P.gr;
   const int N1 = g.N1, N2 = g.N2;
@@ -315,7 +334,22 @@ __device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int b = e & (B - 1), k2 = e >> lgB;
       const int row = b ? kb : ka;
-      sm.bA[e] = ldcg(S1 + row * N2 + k2);
+      if constexpr (COMB) {
+        const int at = row * N2 + k2;
+        Z v = ldcg(in->a + at);
+        if (in->b) {
+          const Z w = ldcg(in->b + at);
+          v = mkc<R>(v.x + in->cb * w.x, v.y + in->cb * w.y);
+        }
+        if (in->c) {
+          const Z w = ldcg(in->c + at);
+          v = mkc<R>(v.x + in->cc * w.x, v.y + in->cc * w.y);
+        }
+        if (in->keep) in->keep[at] = v;
+        sm.bA[e] = v;
+      } else {
+        sm.bA[e] = ldcg(S1 + row * N2 + k2);
+      }
     }
     __syncthreads();
     Z* res = fft_batch<R, false>(sm.bA, sm.bB, N2, lgB, sm.tw, P.T);
@@ -371,7 +405,7 @@ __device__ void passB(const DevPlan& P, const Smem<R>& sm, const R* __restrict__
 // y_{2j+1} = Im z_j for j1 < N1/2.  epi(i, y_i) consumes each output and
 // returns the next product's input x_i (used only with DO_A).
 template <typename R, bool DO_A, int KP = kPre, class Epi>
-__device__ void passCA_real(const DevPlan& P, const Smem<R>& sm, Epi& epi) {
+__device__ void passCA_real(const DevPlan& P, const Smem<R>& sm, Epi& epi, cplx<R>* out = nullptr) {
   typedef cplx<R> Z;
   const Geo& g = P.gr;
   const int lc = lgct<R>(g), ct = 1 << lc;
@@ -380,7 +414,7 @@ __device__ void passCA_real(const DevPlan& P, const Smem<R>& sm, Epi& epi) {
   const int total = N1 << lc;
   const int tstride = P.L / g.Nfft;
   const Z* S2 = reinterpret_cast<const Z*>(P.S2);
-  Z* S1 = reinterpret_cast<Z*>(P.S1);
+  Z* S1 = out ? out : reinterpret_cast<Z*>(P.S1);
   const Z* tw = twL<R>(P);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int c0 = tile << lc;
@@ -461,7 +495,7 @@ __device__ void passC_cplx(const DevPlan& P, const Smem<R>& sm, Epi& epi) {
 // on length-L FFTs; P^{-1} v is then the symmetric Toeplitz product with
 // first column g, i.e. the same zero-padded product as A with the spectrum
 // of the even embedding of g (built here as (sigma, rho) tables).
-template <typename R>
+template <typename R, int KP = kPre>
 __device__ bool build_precond(const DevPlan& P, const Smem<R>& sm, double ahat, double kbar) {
   typedef cplx<R> Z;
   const double* lam = P.lam;
@@ -485,9 +519,9 @@ __device__ bool build_precond(const DevPlan& P, const Smem<R>& sm, double ahat, 
     const int k = L - i;
     return (k < n) ? gv[k] : R(0);
   };
-  passA_real<R, true>(P, sm, L, proE);
+  passA_real<R, true, KP>(P, sm, L, proE);
   if (!gsync(P, sm.red)) return false;
-  passB<R, MID_SPEC>(P, sm, nullptr, nullptr, saG<R>(P), sbG<R>(P), nullptr);
+  passB<R, MID_SPEC, KP>(P, sm, nullptr, nullptr, saG<R>(P), sbG<R>(P), nullptr);
   return gsync(P, sm.red);
 }
 
@@ -640,10 +674,16 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
 // and one with P^{-1} per iteration (BiCGSTAB needs two of each).  The
 // residual r of S relates to the original one by b - (ahat I + K A) x =
 // K r, and the stopping test is on that: ||K r|| < tol ||b||, the same
-// criterion as bicgstab's.  hinv = 1/kappa.  Per iteration six grid phases:
-// p = z + beta p with its forward column FFTs | row pass (A) | q = S p,
+// criterion as bicgstab's.  hinv = 1/kappa.
+// Per iteration five grid phases.  The column transforms are linear, so the
+// transform of p = z + beta p_old is F(z) + beta F(p_old): F(z) comes out of
+// the pass that produces z (its inverse column FFTs fused with the forward
+// ones), F(p_old) is kept in the spare half of S1, and the row pass of the
+// product with A loads their combination; the spatial p is formed in that
+// product's epilogue.  Phases: row pass (A) on F(z) + beta F(p) | q = S p,
 // (p, q) | x += alpha p, r -= alpha q, ||K r||, forward column FFTs of r |
-// row pass (P^{-1}) | z = P^{-1} r, (r, z).
+// row pass (P^{-1}) | z = P^{-1} r, (r, z), forward column FFTs of z.
+// Without a preconditioner z = r and the last two phases drop out.
 // TR selects the transposed level system (ahat I + A K) lambda = g of the
 // adjoint sweep: with mu = K lambda it reads (ahat K^{-1} + A) mu = g, the
 // same S with the right-hand side g itself, and its residual g - S mu is
@@ -654,15 +694,13 @@ __device__ SolveRes pcg(const DevPlan& P, const Smem<R>& sm, const KVecs<R>& V,
                         const R* __restrict__ kap, const R* __restrict__ hinv, double ahat,
                         bool prec, double tol, int max_it, BInit& binit) {
   const int n = P.n;
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int gstr = gridDim.x * blockDim.x;
   const R a = (R)ahat;
   SolveRes out{TSFDE_OK, 0, 0.0};
-  // x = 0, p = 0, r = K^{-1} b (and its forward column FFTs), ||b||.  p is
-  // read by the first p = z + beta p (beta = 0), so it must hold no stale
+  // x = 0, p = 0, r = K^{-1} b and its forward column FFTs, ||b|| (and,
+  // without a preconditioner, rho = (r, r)).  p must hold no stale
   // non-finite value: 0 * NaN is NaN.
   {
-    R acc = 0;
+    R acc = 0, arr = 0;
     auto pro = [&](int i) -> R {
       const R bi = binit(i);
       const R ri = TR ? bi : bi * hinv[i];
@@ -670,44 +708,35 @@ __device__ SolveRes pcg(const DevPlan& P, const Smem<R>& sm, const KVecs<R>& V,
       V.p[i] = R(0);
       V.r[i] = ri;
       acc += bi * bi;
+      arr += ri * ri;
       return ri;
     };
-    if (prec) {
-      passA_real<R, false, KP>(P, sm, n, pro);
-    } else {
-      for (int i = gtid; i < n; i += gstr) pro(i);
-    }
+    passA_real<R, false, KP>(P, sm, n, pro);
     put_partial(P, SL_BB, block_sum((double)acc, sm.red));
+    put_partial(P, SL_RR0, block_sum((double)arr, sm.red));
   }
-  double bb;
-  if (!gsync_sum(P, sm.red, SL_BB, bb)) { out.status = TSFDE_ETIMEOUT; return out; }
+  double bb, rho;
+  if (!gsync_sum2(P, sm.red, SL_BB, SL_RR0, 0u, bb, rho)) { out.status = TSFDE_ETIMEOUT; return out; }
   if (!isfinite(bb)) { out.status = TSFDE_ENONFINITE; return out; }
   if (bb == 0.0) return out;
   const double nb = sqrt(bb);
-  // z = P^{-1} r (the forward column FFTs of r are in S1), rho = (r, z)
+  const R* z = prec ? V.s : V.r;
+  // z = P^{-1} r from the forward column FFTs of r in S1, rho = (r, z); the
+  // same tile pass computes the forward column FFTs of z into S1
   auto precond = [&](double& rho_out) -> bool {
+    passB<R, MID_APPLY, KP>(P, sm, saG<R>(P), sbG<R>(P), nullptr, nullptr, nullptr);
+    if (!gsync(P, sm.red)) return false;
     R acc = 0;
-    if (prec) {
-      passB<R, MID_APPLY, KP>(P, sm, saG<R>(P), sbG<R>(P), nullptr, nullptr, nullptr);
-      if (!gsync(P, sm.red)) return false;
-      auto epi = [&](int i, R y) -> R {
-        V.s[i] = y;
-        acc += V.r[i] * y;
-        return R(0);
-      };
-      passCA_real<R, false, KP>(P, sm, epi);
-    } else {
-      for (int i = gtid; i < n; i += gstr) {
-        const R ri = V.r[i];
-        V.s[i] = ri;
-        acc += ri * ri;
-      }
-    }
+    auto epi = [&](int i, R y) -> R {
+      V.s[i] = y;
+      acc += V.r[i] * y;
+      return y;
+    };
+    passCA_real<R, true, KP>(P, sm, epi);
     put_partial(P, SL_RR0, block_sum((double)acc, sm.red));
     return gsync_sum(P, sm.red, SL_RR0, rho_out);
   };
-  double rho;
-  if (!precond(rho)) { out.status = TSFDE_ETIMEOUT; return out; }
+  if (prec && !precond(rho)) { out.status = TSFDE_ETIMEOUT; return out; }
   double rr = bb, beta = 0.0;
   int it = 0;
   for (;;) {
@@ -718,25 +747,22 @@ __device__ SolveRes pcg(const DevPlan& P, const Smem<R>& sm, const KVecs<R>& V,
     if (relres < tol) return out;
     if (it >= max_it) { out.status = TSFDE_ENOCONV; return out; }
     if (!(rho > 0.0)) { out.status = TSFDE_EBREAKDOWN; return out; }
+    const bool first = it == 0;
     out.iters = ++it;
-    // p = z + beta p, forward column FFTs of p
+    // row pass of A on F(p) = F(z) + beta F(p_old)
     {
-      const R bR = (R)beta;
-      auto pro = [&](int i) -> R {
-        const R pi = V.s[i] + bR * V.p[i];
-        V.p[i] = pi;
-        return pi;
-      };
-      passA_real<R, false, KP>(P, sm, n, pro);
+      cplx<R>* Fp = reinterpret_cast<cplx<R>*>(P.S1) + P.Nc;  // F(p), kept between iterations
+      const RowIn<R> in{reinterpret_cast<const cplx<R>*>(P.S1), first ? nullptr : Fp, (R)beta, nullptr, R(0), Fp};
+      passB<R, MID_APPLY, KP, true>(P, sm, saT<R>(P), sbT<R>(P), nullptr, nullptr, nullptr, &in);
     }
     if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
-    passB<R, MID_APPLY, KP>(P, sm, saT<R>(P), sbT<R>(P), nullptr, nullptr, nullptr);
-    if (!gsync(P, sm.red)) { out.status = TSFDE_ETIMEOUT; return out; }
-    // q = S p = ahat K^{-1} p + A p, (p, q)
+    // p = z + beta p, q = S p = ahat K^{-1} p + A p, (p, q)
     {
+      const R bR = (R)beta;
       R acc = 0;
       auto epi = [&](int i, R y) -> R {
-        const R pi = V.p[i];
+        const R pi = first ? z[i] : z[i] + bR * V.p[i];
+        V.p[i] = pi;
         const R qi = a * hinv[i] * pi + y;
         V.v[i] = qi;
         acc += pi * qi;
@@ -750,34 +776,34 @@ __device__ SolveRes pcg(const DevPlan& P, const Smem<R>& sm, const KVecs<R>& V,
     if (!isfinite(pq)) { out.status = TSFDE_ENONFINITE; return out; }
     if (!(pq > 0.0)) { out.status = TSFDE_EBREAKDOWN; return out; }
     const double alpha = rho / pq;
-    // x += alpha p, r -= alpha q, ||K r||^2, forward column FFTs of r
+    // x += alpha p, r -= alpha q, ||K r||^2 (and (r, r) without a
+    // preconditioner), forward column FFTs of r
     {
       const R aR = (R)alpha;
-      R acc = 0;
+      R acc = 0, arr = 0;
       auto pro = [&](int i) -> R {
         V.x[i] = V.x[i] + aR * V.p[i];
         const R ri = V.r[i] - aR * V.v[i];
         V.r[i] = ri;
         const R kr = TR ? ri : kap[i] * ri;
         acc += kr * kr;
+        arr += ri * ri;
         return ri;
       };
-      if (prec) {
-        passA_real<R, false, KP>(P, sm, n, pro);
-      } else {
-        for (int i = gtid; i < n; i += gstr) pro(i);
-      }
+      passA_real<R, false, KP>(P, sm, n, pro);
       put_partial(P, SL_RR, block_sum((double)acc, sm.red));
+      put_partial(P, SL_RR0, block_sum((double)arr, sm.red));
     }
-    if (!gsync_sum(P, sm.red, SL_RR, rr)) { out.status = TSFDE_ETIMEOUT; return out; }
+    double rho_np;
+    if (!gsync_sum2(P, sm.red, SL_RR, SL_RR0, 0u, rr, rho_np)) { out.status = TSFDE_ETIMEOUT; return out; }
     if (sqrt(rr) / nb < tol) {
       out.relres = sqrt(rr) / nb;
       out.iters = it;
       if (!isfinite(out.relres)) out.status = TSFDE_ENONFINITE;
       return out;
     }
-    double rho_new;
-    if (!precond(rho_new)) { out.status = TSFDE_ETIMEOUT; return out; }
+    double rho_new = rho_np;
+    if (prec && !precond(rho_new)) { out.status = TSFDE_ETIMEOUT; return out; }
     beta = rho_new / rho;
     rho = rho_new;
   }
@@ -818,16 +844,17 @@ static __device__ void write_stat(StepStat* st, int status, int iters, int outer
 
 // Warm start of a level solve: u = u_prev and r64 = b - (ahat I + K A) u_prev
 // (one FP64 product); returns b.b and r.r (grid-wide, in every CTA).
-static __device__ bool warm_residual(const LevelArgs& A, SmemAll& S, double& bb, double& rr) {
+template <int KP = kPre>
+__device__ bool warm_residual(const LevelArgs& A, SmemAll& S, double& bb, double& rr) {
   const DevPlan& P = A.P;
   auto pro = [&](int i) -> double {
     const double x = A.u_prev[i];
     A.u[i] = x;
     return x;
   };
-  passA_real<double, false>(P, S.d, P.n, pro);
+  passA_real<double, false, KP>(P, S.d, P.n, pro);
   if (!gsync(P, S.d.red)) return false;
-  passB<double, MID_APPLY>(P, S.d, P.saT64, P.sbT64, nullptr, nullptr, nullptr);
+  passB<double, MID_APPLY, KP>(P, S.d, P.saT64, P.sbT64, nullptr, nullptr, nullptr);
   if (!gsync(P, S.d.red)) return false;
   double bacc = 0.0, racc = 0.0;
   auto epi = [&](int i, double y) -> double {
@@ -838,7 +865,7 @@ static __device__ bool warm_residual(const LevelArgs& A, SmemAll& S, double& bb,
     racc += ri * ri;
     return 0.0;
   };
-  passCA_real<double, false>(P, S.d, epi);
+  passCA_real<double, false, KP>(P, S.d, epi);
   put_partial(P, SL_BB, block_sum(bacc, S.d.red));
   put_partial(P, SL_RES, block_sum(racc, S.d.red));
   return gsync_sum2(P, S.d.red, SL_BB, SL_RES, 0u, bb, rr);
@@ -865,7 +892,7 @@ static __device__ bool warm_residual(const LevelArgs& A, SmemAll& S, double& bb,
 // FP64 PBiCGSTAB on the remaining residual, so a level never returns an
 // unconverged answer.  PCG selects the Krylov method of that FP64 finish
 // (the inner solves choose their own).
-template <bool PCG = false, typename RI, class Conv, class Inner>
+template <bool PCG = false, int KP = kPre, typename RI, class Conv, class Inner>
 __device__ void mixed_level(const LevelArgs& A, SmemAll& S, Conv& conv, Inner& inner, const RI* e) {
   const DevPlan& P = A.P;
   const int n = P.n;
@@ -876,7 +903,7 @@ __device__ void mixed_level(const LevelArgs& A, SmemAll& S, Conv& conv, Inner& i
   // The preconditioner is built in FP64 and rounded to FP32; building it in
   // FP32 would bury its smallest eigenvalues (1/(ahat + kbar lambda_max),
   // ~1e-8 of the largest at n = 2^17-1) under rounding.
-  if (A.precond && !build_precond<double>(P, S.d, A.ahat, kbar)) {
+  if (A.precond && !build_precond<double, KP>(P, S.d, A.ahat, kbar)) {
     write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0);
     return;
   }
@@ -884,7 +911,7 @@ __device__ void mixed_level(const LevelArgs& A, SmemAll& S, Conv& conv, Inner& i
   {
     for (int k = gtid; k < P.Nc; k += gstr) conv(k);
     if (A.u_prev) {
-      if (!warm_residual(A, S, bb, rr0)) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
+      if (!warm_residual<KP>(A, S, bb, rr0)) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
     } else {
       double acc = 0.0;
       for (int i = gtid; i < n; i += gstr) {
@@ -928,9 +955,9 @@ __device__ void mixed_level(const LevelArgs& A, SmemAll& S, Conv& conv, Inner& i
     // w = M (nr e) in FP64
     const double ah = A.ahat;
     auto pro = [&](int i) -> double { return nr * (double)e[i]; };
-    passA_real<double, false>(P, S.d, n, pro);
+    passA_real<double, false, KP>(P, S.d, n, pro);
     if (!gsync(P, S.d.red)) { status = TSFDE_ETIMEOUT; break; }
-    passB<double, MID_APPLY>(P, S.d, P.saT64, P.sbT64, nullptr, nullptr, nullptr);
+    passB<double, MID_APPLY, KP>(P, S.d, P.saT64, P.sbT64, nullptr, nullptr, nullptr);
     if (!gsync(P, S.d.red)) { status = TSFDE_ETIMEOUT; break; }
     {
       double rw = 0.0, ww = 0.0;
@@ -941,7 +968,7 @@ __device__ void mixed_level(const LevelArgs& A, SmemAll& S, Conv& conv, Inner& i
         ww += wi * wi;
         return 0.0;
       };
-      passCA_real<double, false>(P, S.d, epi);
+      passCA_real<double, false, KP>(P, S.d, epi);
       put_partial(P, SL_RV, block_sum(rw, S.d.red));
       put_partial(P, SL_TT, block_sum(ww, S.d.red));
     }
@@ -995,8 +1022,8 @@ __device__ void mixed_level(const LevelArgs& A, SmemAll& S, Conv& conv, Inner& i
     KVecs<double> V = A.k64;
     auto binit = [&](int i) -> double { return A.r64[i]; };
     const double tol_d = fmax(A.tol * nb / nr, 1e-14);
-    SolveRes fr = level_krylov<PCG, kPre>(P, S.d, V, A.kappa64, A.hinv64, A.ahat, A.precond != 0,
-                                          tol_d, A.max_it, binit);
+    SolveRes fr = level_krylov<PCG, KP>(P, S.d, V, A.kappa64, A.hinv64, A.ahat, A.precond != 0,
+                                        tol_d, A.max_it, binit);
     if (fr.status == TSFDE_OK) {
       for (int i = gtid; i < n; i += gstr) A.u[i] += V.x[i];
       relres = fr.relres * nr / nb;

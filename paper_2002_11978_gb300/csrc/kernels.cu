@@ -18,7 +18,7 @@ namespace tsfde {
 
 // Shared memory: [tw64 T][tw32 T][twds T][bufA W][bufB W][red 64]
 size_t plan_smem_bytes(const DevPlan& P) {
-  return (size_t)P.T * (2 * sizeof(double2) + sizeof(float2)) +
+  return (size_t)tpad_len(P.T) * (2 * sizeof(double2) + sizeof(float2)) +
          2 * (size_t)P.W * sizeof(double2) + 64 * sizeof(double);
 }
 

@@ -77,7 +77,7 @@ __device__ void level64_run(const LevelArgs& A) {
   }
   const double kbar = mean_kappa(P, A.kappa64, S.d.red);
   if (kbar < 0.0) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
-  if (A.precond && !build_precond<double>(P, S.d, A.ahat, kbar)) {
+  if (A.precond && !build_precond<double, KP>(P, S.d, A.ahat, kbar)) {
     write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0);
     return;
   }
@@ -92,7 +92,7 @@ __device__ void level64_run(const LevelArgs& A) {
   }
   // warm start: solve M d = b - M u_prev to ||r|| < tol ||b||, u = u_prev + d
   double bb, rr;
-  if (!warm_residual(A, S, bb, rr)) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
+  if (!warm_residual<KP>(A, S, bb, rr)) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
   if (!isfinite(bb) || !isfinite(rr)) { write_stat(A.stat, TSFDE_ENONFINITE, 0, 0, 0.0); return; }
   if (bb == 0.0 || rr == 0.0) { write_stat(A.stat, TSFDE_OK, 0, 0, 0.0); return; }
   const double scale = sqrt(rr / bb);
@@ -138,7 +138,7 @@ __device__ void level_mixed_run(const LevelArgs& A) {
                                A.inner_tol, A.inner_max_it, binit);
     return ir.status != TSFDE_ETIMEOUT;
   };
-  mixed_level<PCG>(A, S, conv, inner, A.k32.x);
+  mixed_level<PCG, KP>(A, S, conv, inner, A.k32.x);
 }
 
 template <int KP, bool PCG>
@@ -190,7 +190,7 @@ __device__ void level_mixed_ds_run(const LevelArgs& A) {
                                A.max_it, binit);
     return ir.status != TSFDE_ETIMEOUT;
   };
-  mixed_level<PCG>(A, S, conv, inner, A.kds.x);
+  mixed_level<PCG, KP>(A, S, conv, inner, A.kds.x);
 }
 
 template <int KP, bool PCG>

@@ -195,7 +195,7 @@ def test_batch_large_class_certified(torch):
     double-double defect with the direct FIDS history, Lemma 3.3) bounds the
     error by 1e-10 of max|u^m|.  The SOE table and the Toeplitz entries are
     the library's for the same parameters, read from a single-problem
-    context (entries within 3e-16 of the oracle's)."""
+    context (entries within two ulps of the oracle's)."""
     import math
 
     import paper_2002_11978_gb300 as pkg
@@ -217,7 +217,7 @@ def test_batch_large_class_certified(torch):
         ref = pkg.Solver(p.alpha, p.gamma, p.l, p.T, p.n, M, p.r, 1e-12)
         soe, t = ref.soe(), ref.symbol()  # the library's tables (see test_gpu_certificate.py)
         t_or = oracle.ifl_symbol(p.alpha, p.n)
-        assert np.max(np.abs(t - t_or) / np.abs(t_or)) <= 3e-16
+        assert np.max(np.abs(t - t_or) / np.abs(t_or)) <= 5e-16  # two ulps
         for m in (2, 8):
             b = oracle.level_rhs("FIDS", p.alpha, p.gamma, p.l, p.T, p.r, p.n, M, m, U, p.F[0], soe=soe)
             ahat = oracle.l1_weight(p.T, M, p.r, p.gamma, m, m) / math.gamma(1 - p.gamma)
