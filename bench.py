@@ -262,9 +262,11 @@ def batched_sample(torch, pkg, ti, levels, rank, world, stream, warm=True, full=
     this rank's share (instance i on rank i mod world).  The launch plan
     (one persistent launch or two size classes, cluster size per launch) is
     chosen by tsfde_batch_tune on a 4-level probe and reported with every
-    plan it timed.  Timed with CUDA events: the mixed path over all M levels
-    (full=True), and mixed against FP64 over the first `levels` levels.  Its
-    working set (the SOE histories, ~3 GB) is far above L2."""
+    plan it timed.  Timed with CUDA events: BiCGSTAB and PCG in the mixed
+    and the FP64 arithmetic over the first `levels` levels (the faster method
+    of each is the arm's figure), and the faster mixed method over all M
+    levels (full=True).  Its working set (the SOE histories, ~3 GB) is far
+    above L2."""
     M = 1024
     ns, al, ga = ti.batched_instance_params()
     mine = shard(len(ns), rank, world)
@@ -290,11 +292,11 @@ def batched_sample(torch, pkg, ti, levels, rank, world, stream, warm=True, full=
     # does at 1e-12 (within 2e-13): the arms are compared at equal accuracy.
     tols = {"mixed": 1e-12, "fp64": 1e-13}
     out["krylov_tol"] = tols
-    runs = [("mixed", levels), ("fp64", levels)] + ([("mixed_full_M", M)] if full else [])
-    for key, lv in runs:
-        prec = "fp64" if key == "fp64" else "mixed"
+    # both Krylov methods on the first levels, in both arithmetics; the faster
+    # mixed method then runs the whole march
+    def run_one(key, prec, kry, lv):
         bs = pkg.BatchSolver(inst, M, precision=prec, stream=stream, warm_start=warm,
-                             krylov_tol=tols[prec], plan=best)
+                             krylov_tol=tols[prec], plan=best, krylov=kry)
         outs = [torch.zeros(d["n"], dtype=torch.float64, device="cuda") for d in inst]
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -304,16 +306,27 @@ def batched_sample(torch, pkg, ti, levels, rank, world, stream, warm=True, full=
             e1.record(stream)
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3
-        out[key] = {"levels": lv, "s": t, "instance_levels_per_s": len(inst) * lv / t,
+        out[key] = {"levels": lv, "krylov": kry, "s": t, "instance_levels_per_s": len(inst) * lv / t,
                     "unknown_levels_per_s": unknowns * lv / t,
                     "krylov_its": info["iterations"], "outer": info["outer"],
                     "fp64_levels": info["fp64_levels"], "status": info["status"],
                     "max_final_rel_residual": info["max_rel_residual"]}
-        if key != "mixed_full_M":
+        if lv == levels:
             us[key] = [u.cpu().numpy() for u in outs]
         del bs
+
+    for prec in ("mixed", "fp64"):
+        for kry in ("bicgstab", "pcg"):
+            run_one(f"{prec}_{kry}", prec, kry, levels)
+    best_m = min(("bicgstab", "pcg"), key=lambda k: out[f"mixed_{k}"]["s"])
+    best_f = min(("bicgstab", "pcg"), key=lambda k: out[f"fp64_{k}"]["s"])
+    out["mixed"] = dict(out[f"mixed_{best_m}"])
+    out["fp64"] = dict(out[f"fp64_{best_f}"])
+    if full:
+        run_one("mixed_full_M", "mixed", best_m, M)
     out["mixed_vs_fp64_max_rel_err"] = max(
-        float(np.max(np.abs(a - b)) / np.max(np.abs(b))) for a, b in zip(us["mixed"], us["fp64"]))
+        float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+        for a, b in zip(us[f"mixed_{best_m}"], us[f"fp64_{best_f}"]))
     out["mixed_speedup"] = out["fp64"]["s"] / out["mixed"]["s"]
     return out
 

@@ -82,7 +82,8 @@ enum { TSFDE_HISTORY_SOE = 0, TSFDE_HISTORY_DIRECT = 1 };
  * iteration instead of two of each; the stopping test is the same, on the
  * residual of the original system.  The mixed paths use it for their inner
  * solves and their FP64 finish, and tsfde_adjoint its transposed solves.
- * Grid engine only; the batched solve uses BiCGSTAB. */
+ * The batched solve runs it on its clusters (ce_pcg); the single-problem
+ * cluster engine runs BiCGSTAB only. */
 /* AUTO: each level of tsfde_step / tsfde_solve takes whichever of the two
  * is cheaper there, decided on the device from measured level times: the
  * method of the previous level, unless the other one was faster at its latest
@@ -161,7 +162,7 @@ typedef struct tsfde_opts {
                            accepts SOE only                                 */
   int krylov;           /* TSFDE_KRYLOV_BICGSTAB (default), TSFDE_KRYLOV_PCG
                            or TSFDE_KRYLOV_AUTO; the batched solve accepts
-                           BICGSTAB only                                    */
+                           BICGSTAB or PCG (one method for the batch)      */
   int ckpt_stride;      /* adjoint checkpoints: every ckpt_stride-th level of
                            the forward march (level 0 at each reset) keeps
                            u^{k-1}, u^k and the SOE history, so that
@@ -334,9 +335,10 @@ int tsfde_adjoint(tsfde_ctx* ctx, const double* u_all, const double* dJ_duM,
  * its transforms in distributed shared memory, writes u^M and claims the
  * next.  Instances are taken largest first.  kappa and f are time
  * independent per instance.  Options (tsfde_opts): mu / kappa_mu (common),
- * precision (MIXED: FP32 PBiCGSTAB sweeps refined in FP64 with the FP64
- * fallback of the single-problem path; FP64: PBiCGSTAB in FP64),
- * krylov_tol, max_it, inner_tol, max_outer, inner_max_it, precond, stream.
+ * precision (MIXED: FP32 Krylov sweeps refined in FP64 with the FP64
+ * fallback of the single-problem path; FP64: the Krylov solve in FP64),
+ * krylov (BICGSTAB, or PCG on the symmetrised system), krylov_tol, max_it,
+ * inner_tol, max_outer, inner_max_it, precond, stream.
  * Each instance needs n >= 31 (its transforms are split over the cluster). */
 typedef struct tsfde_instance {
   double alpha, gamma, l, T, r;  /* as tsfde_setup                           */
@@ -460,7 +462,7 @@ int tsfde_linear_solve(tsfde_ctx* ctx, double a, const double* kappa,
  * on (-l, l), splitting mu (<= 0: 1 + alpha/2) and kappa_mu (<= 0: derived
  * from mu).  v, y: dev n, owned by the caller.  No context is needed and
  * no memory is allocated: the twiddles, symbol, spectrum and work buffers
- * live in one fixed array of about 1.5 MB inside the library, which every
+ * live in one fixed array of about 1.6 MB inside the library, which every
  * GPU that loads the library keeps until the process exits.
  *  - n must be <= 16383; larger n returns TSFDE_ENOTSUP (with a message on
  *    stderr) without touching the device.

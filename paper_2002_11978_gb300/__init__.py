@@ -408,12 +408,13 @@ class BatchSolver:
 
     def __init__(self, instances, M, *, precision="mixed", precond="strang", krylov_tol=1e-12,
                  max_it=2000, inner_tol=1e-2, max_outer=60, inner_max_it=40, mu=None,
-                 kappa_mu=None, stream=None, cluster_size=0, warm_start=False, plan=None):
+                 kappa_mu=None, stream=None, cluster_size=0, warm_start=False, plan=None,
+                 krylov="bicgstab"):
         """plan: None (the default launch plan), a tsfde_batch_plan, or a dict
         as batch_tune / .plan return."""
         lib = load_library()
         o, arr = _batch_args(instances, precision, precond, krylov_tol, max_it, inner_tol, max_outer,
-                             inner_max_it, mu, kappa_mu, stream, cluster_size, warm_start)
+                             inner_max_it, mu, kappa_mu, stream, cluster_size, warm_start, krylov)
         self.ns = [int(d["n"]) for d in instances]
         self.lib = lib
         self.B, self.M = len(instances), int(M)
@@ -459,8 +460,9 @@ class BatchSolver:
 
 def _batch_args(instances, precision="mixed", precond="strang", krylov_tol=1e-12, max_it=2000,
                 inner_tol=1e-2, max_outer=60, inner_max_it=40, mu=None, kappa_mu=None, stream=None,
-                cluster_size=0, warm_start=False):
+                cluster_size=0, warm_start=False, krylov="bicgstab"):
     o = default_opts()
+    o.krylov = {"bicgstab": TSFDE_KRYLOV_BICGSTAB, "pcg": TSFDE_KRYLOV_PCG}[krylov]
     o.cluster_size = cluster_size
     o.warm_start = 1 if warm_start else 0
     o.krylov_tol = krylov_tol

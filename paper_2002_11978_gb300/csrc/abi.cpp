@@ -437,7 +437,7 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
   ok &= dalloc(c, &dsaG64, Nc) && dalloc(c, &dsbG64, Nc) && dalloc(c, &dsaG32, Nc) && dalloc(c, &dsbG32, Nc);
   ok &= dalloc(c, &dg64, n) && dalloc(c, &dg32, n);
   ok &= dalloc(c, &dS1, L) && dalloc(c, &dS2, L);
-  ok &= dalloc(c, &dpart, (size_t)kSlots * std::max(P.G, P.cl.G)) && dalloc(c, &dbar, 1);
+  ok &= dalloc(c, &dpart, (size_t)2 * kSlots * std::max(P.G, P.cl.G)) && dalloc(c, &dbar, 1);
   float2* dspT = nullptr;
   float2* dspG = nullptr;
   if (use_cluster) ok &= dalloc(c, &dspT, Nc) && dalloc(c, &dspG, Nc);

@@ -10,9 +10,10 @@
 //   the Strang preconditioner of Sec. 4.1 built in FP64 (Bluestein length-n
 //     inverse DFT of 1/(ahat + kbar lambda) on length-L complex transforms,
 //     then the spectrum of its even embedding),
-//   the level solve: FP32 PBiCGSTAB sweeps refined by FP64 residual products
-//     and finished in FP64 when the refinement stalls (the rules of
-//     mixed_level in grid.cuh), or plain FP64 PBiCGSTAB.
+//   the level solve: FP32 Krylov sweeps (PBiCGSTAB, or PCG on the
+//     symmetrised system) refined by FP64 residual products and finished in
+//     FP64 when the refinement stalls (the rules of mixed_level in grid.cuh),
+//     or the plain FP64 Krylov solve.
 // Instances never wait on one another, so there is no grid-wide barrier: the
 // only waits are cluster barriers, whose partners are co-scheduled by the
 // hardware and take the same branches (every decision uses cluster-reduced
@@ -335,6 +336,15 @@ __device__ __noinline__ void bt_copy_out(const BatchCtx* bx, int m) {
   }
 }
 
+// The level's Krylov solve on the cluster: BiCGSTAB or PCG on the
+// symmetrised system.
+template <typename R>
+__device__ __forceinline__ SolveRes bt_krylov(const CeCtx<R>* cx, const BatchArgs& A, bool prec, double tol,
+                                              int max_it, const double* r64, double sc) {
+  if (A.krylov == TSFDE_KRYLOV_PCG) return ce_pcg<R>(cx, prec, tol, max_it, r64, sc);
+  return ce_bicgstab<R>(cx, prec, tol, max_it, r64, sc);
+}
+
 struct LevelOut {
   int status, iters, outer;
   bool fp64;
@@ -375,7 +385,7 @@ __device__ LevelOut bt_level(BatchCtx* bx, const BatchArgs& A, int m, bool prev_
   __syncthreads();
   if (A.precision == TSFDE_FP64) {
     const double scale = sqrt(rr0 / bb);
-    const SolveRes r = ce_bicgstab<double>(&bx->c64, prec, A.tol / scale, A.max_it, I.r64, 1.0);
+    const SolveRes r = bt_krylov<double>(&bx->c64, A, prec, A.tol / scale, A.max_it, I.r64, 1.0);
     cl.sync();
     if (warm && r.status == TSFDE_OK) bt_add_fp64(bx, m);
     o.status = r.status;
@@ -391,7 +401,7 @@ __device__ LevelOut bt_level(BatchCtx* bx, const BatchArgs& A, int m, bool prev_
   const double ah = I.ahat[m];
   while (!fallback) {
     if (o.outer >= A.max_outer) { fallback = true; break; }
-    const SolveRes ir = ce_bicgstab<float>(&bx->c32, prec, A.inner_tol, A.inner_max_it, I.r64, 1.0 / nr);
+    const SolveRes ir = bt_krylov<float>(&bx->c32, A, prec, A.inner_tol, A.inner_max_it, I.r64, 1.0 / nr);
     o.iters += ir.iters;
     ++o.outer;
     cl.sync();
@@ -430,7 +440,7 @@ __device__ LevelOut bt_level(BatchCtx* bx, const BatchArgs& A, int m, bool prev_
   }
   if (fallback && o.status == TSFDE_OK) {
     const double tol_d = fmax(A.tol * nb / nr, 1e-14);
-    const SolveRes fr = ce_bicgstab<double>(&bx->c64, prec, tol_d, A.max_it, I.r64, 1.0);
+    const SolveRes fr = bt_krylov<double>(&bx->c64, A, prec, tol_d, A.max_it, I.r64, 1.0);
     cl.sync();
     if (fr.status == TSFDE_OK) {
       bt_add_fp64(bx, m);
@@ -463,10 +473,10 @@ __global__ void __launch_bounds__(kBT, 2) k_batch(BatchArgs A) {
       const BInst& I = bx->I;
       CeCtx<float>& c32 = bx->c32;
       c32.g = I.gr; c32.lay = A.lay; c32.spT = I.spT32; c32.spG = I.spG32;
-      c32.V = I.v32; c32.kap = I.kap32; c32.a = 0.f;
+      c32.V = I.v32; c32.kap = I.kap32; c32.hinv = I.hinv32; c32.a = 0.f;
       CeCtx<double>& c64 = bx->c64;
       c64.g = I.gr; c64.lay = A.lay; c64.spT = I.spT64; c64.spG = I.spG64;
-      c64.V = I.v64; c64.kap = I.kap64; c64.a = 0.0;
+      c64.V = I.v64; c64.kap = I.kap64; c64.hinv = I.hinv64; c64.a = 0.0;
     }
     __syncthreads();
     {

@@ -273,8 +273,8 @@ int tsfde_batch_setup_plan(tsfde_batch** out, int B, const tsfde_instance* inst,
   if (opts) o = *opts; else tsfde_default_opts(&o);
   if (o.precision != TSFDE_FP64 && o.precision != TSFDE_MIXED) return TSFDE_EINVAL;
   if (o.history == TSFDE_HISTORY_DIRECT) return TSFDE_ENOTSUP;  // FIDS only
-  if (o.krylov == TSFDE_KRYLOV_PCG) return TSFDE_ENOTSUP;        // BiCGSTAB only
-  if (o.krylov != TSFDE_KRYLOV_BICGSTAB) return TSFDE_EINVAL;
+  if (o.krylov == TSFDE_KRYLOV_AUTO) return TSFDE_ENOTSUP;       // one method per batch
+  if (o.krylov != TSFDE_KRYLOV_BICGSTAB && o.krylov != TSFDE_KRYLOV_PCG) return TSFDE_EINVAL;
   if (o.history != TSFDE_HISTORY_SOE) return TSFDE_EINVAL;
   if (o.precond != TSFDE_STRANG && o.precond != TSFDE_PRECOND_NONE) return TSFDE_EINVAL;
   if (!(o.krylov_tol > 0.0) || o.max_it < 1) return TSFDE_EINVAL;
@@ -433,14 +433,15 @@ int tsfde_batch_setup_plan(tsfde_batch** out, int B, const tsfde_instance* inst,
     I.n = n; I.E = h.E; I.ld = ld;
     I.gr = h.gr; I.gc = h.gc;
     I.tstride = Lmax / h.L;
-    double *phi, *k64, *f, *Hh, *u0, *u1, *u2, *r64, *w, *ah, *eps, *cw, *lam;
-    float* k32;
+    double *phi, *k64, *f, *Hh, *u0, *u1, *u2, *r64, *w, *ah, *eps, *cw, *lam, *h64;
+    float *k32, *h32;
     int* ea;
     double2 *ch, *bh, *t64, *g64;
     float2 *t32, *g32;
     ok = ok && balloc(b, &phi, ld) && balloc(b, &k64, ld) && balloc(b, &f, ld) &&
          balloc(b, &Hh, (size_t)E * ld) && balloc(b, &u0, ld) && balloc(b, &u1, ld) &&
          balloc(b, &u2, ld) && balloc(b, &r64, ld) && balloc(b, &w, ld) && balloc(b, &k32, ld) &&
+         balloc(b, &h64, ld) && balloc(b, &h32, ld) &&
          balloc(b, &ah, M + 1) && balloc(b, &eps, h.eps.size()) && balloc(b, &cw, h.cw.size()) &&
          balloc(b, &ea, M + 1) && balloc(b, &lam, n) && balloc(b, &ch, n) && balloc(b, &bh, h.L) &&
          balloc(b, &t64, h.Nc) && balloc(b, &t32, h.Nc) && balloc(b, &g64, h.Nc) && balloc(b, &g32, h.Nc);
@@ -448,7 +449,7 @@ int tsfde_batch_setup_plan(tsfde_batch** out, int B, const tsfde_instance* inst,
     float* v32[9];
     for (int q = 0; q < 9 && ok; ++q) ok = balloc(b, &v64[q], ld) && balloc(b, &v32[q], ld);
     if (!ok) break;
-    I.phi = phi; I.kap64 = k64; I.kap32 = k32; I.f = f; I.H = Hh;
+    I.phi = phi; I.kap64 = k64; I.kap32 = k32; I.hinv64 = h64; I.hinv32 = h32; I.f = f; I.H = Hh;
     I.u[0] = u0; I.u[1] = u1; I.u[2] = u2; I.r64 = r64; I.w = w;
     I.v64 = KVecs<double>{v64[0], v64[1], v64[2], v64[3], v64[4], v64[5], v64[6], v64[7], v64[8]};
     I.v32 = KVecs<float>{v32[0], v32[1], v32[2], v32[3], v32[4], v32[5], v32[6], v32[7], v32[8]};
@@ -470,15 +471,20 @@ int tsfde_batch_setup_plan(tsfde_batch** out, int B, const tsfde_instance* inst,
     if (e == cudaSuccess) {
       std::vector<double> kh(n);
       e = cudaMemcpy(kh.data(), k64, nb, cudaMemcpyDeviceToHost);
-      std::vector<float> k32h(n);
+      std::vector<float> k32h(n), h32h(n);
+      std::vector<double> h64h(n);
       double sum = 0.0;
       for (int j = 0; j < n; ++j) {
         if (!(kh[j] > 0.0) || !std::isfinite(kh[j])) ok = false;
         sum += kh[j];
         k32h[j] = (float)kh[j];
+        h64h[j] = 1.0 / kh[j];
+        h32h[j] = (float)h64h[j];
       }
       kmean[i] = sum / n;
       if (e == cudaSuccess) e = up(k32, k32h);
+      if (e == cudaSuccess) e = up(h64, h64h);
+      if (e == cudaSuccess) e = up(h32, h32h);
     }
     if (e == cudaSuccess) e = up(ah, h.ahat);
     if (e == cudaSuccess) e = up(eps, h.eps);
@@ -643,6 +649,7 @@ int tsfde_batch_solve(tsfde_batch* b, int64_t levels, double* const* u_final,
   A0.max_outer = b->opts.max_outer;
   A0.inner_max_it = b->opts.inner_max_it;
   A0.warm = b->opts.warm_start;
+  A0.krylov = b->opts.krylov;
   A0.tw64 = b->tw64;
   A0.tw32 = b->tw32;
   // the classes' streams start after the caller's stream reaches this point

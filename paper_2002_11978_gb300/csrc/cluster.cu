@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kCT, 1) k_level_cluster(LevelArgs A) {
         g.T1 = cg_.T1; g.LT = cg_.LT; g.lgLT = cg_.lgLT; g.q = 0;
         cx->lay = lay;
         cx->spT = P.spT_cl; cx->spG = P.spG_cl;
-        cx->V = A.k32; cx->kap = A.kappa32; cx->a = (float)A.ahat;
+        cx->V = A.k32; cx->kap = A.kappa32; cx->hinv = nullptr; cx->a = (float)A.ahat;
       }
       __syncthreads();
       const SolveRes r = ce_bicgstab<float>(cx, A.precond != 0, A.inner_tol, A.inner_max_it, A.r64, sc);
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kCT, 1) k_level_cluster(LevelArgs A) {
     put_partial(P, SL_CST, stv);
     double o_its, o_st;
     const bool ok = gsync_sum2(P, S.d.red, SL_CIT, SL_CST, 0u, o_its, o_st);
-    S = smem_setup(P);  // the cluster passes overwrote the grid tables
+    S = smem_setup(P, false);  // the cluster passes overwrote the grid tables
     ir.iters = (int)o_its;
     ir.status = (int)o_st;
     return ok;

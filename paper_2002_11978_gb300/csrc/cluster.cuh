@@ -317,6 +317,7 @@ template <typename R> struct CeCtx {
   const cplx<R>* spG;  // preconditioner spectrum, row-pass order
   KVecs<R> V;
   const R* kap;
+  const R* hinv;       // 1/kappa (PCG on the symmetrised system; NULL otherwise)
   R a;                 // ahat
 };
 
@@ -327,8 +328,8 @@ template <typename R> __device__ __forceinline__ CeGeo ce_enter(const CeCtx<R>* 
 }
 
 // epilogue / prologue modes of the column passes
-enum { PRO_P = 0, PRO_S = 1 };                          // forward of p or s
-enum { EPI_PH = 0, EPI_SH = 1, EPI_V = 2, EPI_T = 3 };  // inverse into ...
+enum { PRO_P = 0, PRO_S = 1, PRO_R = 2, PRO_PZ = 3 };  // forward of p, s, r, or z + c0 p
+enum { EPI_PH = 0, EPI_SH = 1, EPI_V = 2, EPI_T = 3, EPI_Z = 4, EPI_Q = 5 };  // inverse into ...
 
 // Inverse column pass of a product inside the solve; the last FFT stage
 // writes y (zero at entries >= n) into ce_io, then per mode:
@@ -336,6 +337,8 @@ enum { EPI_PH = 0, EPI_SH = 1, EPI_V = 2, EPI_T = 3 };  // inverse into ...
 //     vector straight from ce_io (the next product's input);
 //   EPI_V: v = a ph + kappa y, acc.x = (rh, v);  EPI_T: t = a sh + kappa y,
 //     acc.x = (t, s), acc.y = (t, t).   xin is ph or p (sh or s).
+//   PCG (ce_pcg): EPI_Z: z = y (into V.s), acc.x = (r, z);  EPI_Q:
+//     q = a hinv p + y (into V.v), acc.x = (p, q), xin = p.
 // TR (transposed operator a I + A K): kappa scales the forwarded input
 // instead of the product's output.
 template <typename R>
@@ -363,9 +366,10 @@ __device__ __noinline__ cplx<R> ce_colinv_op(const CeCtx<R>* cxp, int mode, cons
     __syncthreads();
     ce_colfwd_buf(g, s, N1 >> 1);
   } else {
-    R* const dst = (mode == EPI_V) ? cxp->V.v : cxp->V.t;
-    const R* const dotv = (mode == EPI_V) ? cxp->V.rh : cxp->V.s;
-    const R* const kap = cxp->kap;
+    const bool pz = (mode == EPI_Z || mode == EPI_Q);
+    R* const dst = (mode == EPI_V || mode == EPI_Q) ? cxp->V.v : (mode == EPI_Z ? cxp->V.s : cxp->V.t);
+    const R* const dotv = (mode == EPI_V) ? cxp->V.rh : (mode == EPI_Z ? cxp->V.r : (mode == EPI_Q ? xin : cxp->V.s));
+    const R* const kap = (mode == EPI_Q) ? cxp->hinv : cxp->kap;
     const R a = cxp->a;
     for (int p0 = threadIdx.x; p0 < npair; p0 += kVB * blockDim.x) {
       Z xv[kVB], kv[kVB], dv[kVB];
@@ -375,8 +379,10 @@ __device__ __noinline__ cplx<R> ce_colinv_op(const CeCtx<R>* cxp, int mode, cons
         const int i0 = pair_i0(g, pp);
         xv[u] = kv[u] = dv[u] = mkc<R>(R(0), R(0));
         if (pp < npair && i0 < n) {
-          xv[u] = ld2(xin, i0);
-          kv[u] = ld2(kap, i0);
+          if (mode != EPI_Z) {
+            xv[u] = ld2(xin, i0);
+            kv[u] = ld2(kap, i0);
+          }
           dv[u] = ld2(dotv, i0);
         }
       }
@@ -386,7 +392,10 @@ __device__ __noinline__ cplx<R> ce_colinv_op(const CeCtx<R>* cxp, int mode, cons
         if (pp < npair) {
           const int i0 = pair_i0(g, pp);
           const Z y = Bn[pp];
-          Z w = mkc<R>(a * xv[u].x + kv[u].x * y.x, a * xv[u].y + kv[u].y * y.y);
+          Z w;
+          if (mode == EPI_Z) w = y;
+          else if (mode == EPI_Q) w = mkc<R>(a * kv[u].x * xv[u].x + y.x, a * kv[u].y * xv[u].y + y.y);
+          else w = mkc<R>(a * xv[u].x + kv[u].x * y.x, a * xv[u].y + kv[u].y * y.y);
           if (i0 + 1 >= n) w.y = R(0);
           if (i0 >= n) w.x = R(0);
           st2(dst, i0, n, w);
@@ -395,22 +404,25 @@ __device__ __noinline__ cplx<R> ce_colinv_op(const CeCtx<R>* cxp, int mode, cons
         }
       }
     }
+    (void)pz;
   }
   return mkc<R>(acc0, acc1);
 }
 
-// Forward column pass of p = r + beta (p - omega v) (PRO_P) or of
-// s = r - alpha v (PRO_S), storing the new vector; the entries are formed in
-// ce_io first (loads issued together), then transformed.
+// Forward column pass of p = r + beta (p - omega v) (PRO_P), of
+// s = r - alpha v (PRO_S), of r itself (PRO_R), or (PCG) of p = z + c0 p with
+// z = zsrc (PRO_PZ), storing the new vector (not for PRO_R); the entries are
+// formed in ce_io first (loads issued together), then transformed.
 template <typename R>
-__device__ __noinline__ void ce_colfwd_vec(const CeCtx<R>* cxp, int mode, R c0, R c1) {
+__device__ __noinline__ void ce_colfwd_vec(const CeCtx<R>* cxp, int mode, R c0, R c1,
+                                           const R* zsrc = nullptr) {
   typedef cplx<R> Z;
   const CeGeo g = ce_enter(cxp);
   const CeSm<R> s = ce_sm<R>(cxp->lay);
   const int N1 = g.N1, n = g.n, lgcQ = g.lgcQ;
-  const R* const r_ = cxp->V.r;
+  const R* const r_ = (mode == PRO_PZ) ? zsrc : cxp->V.r;
   const R* const v_ = cxp->V.v;
-  R* const dst = (mode == PRO_P) ? cxp->V.p : cxp->V.s;
+  R* const dst = (mode == PRO_P || mode == PRO_PZ) ? cxp->V.p : cxp->V.s;
   Z* const X = ce_io(g, s);
   const int npair = (N1 >> 1) << lgcQ;
   for (int p0 = threadIdx.x; p0 < npair; p0 += kVB * blockDim.x) {
@@ -422,8 +434,8 @@ __device__ __noinline__ void ce_colfwd_vec(const CeCtx<R>* cxp, int mode, R c0, 
       rv[u] = vv[u] = pv[u] = mkc<R>(R(0), R(0));
       if (pp < npair && i0 < n) {
         rv[u] = ld2(r_, i0);
-        vv[u] = ld2(v_, i0);
-        if (mode == PRO_P) pv[u] = ld2((const R*)dst, i0);
+        if (mode == PRO_P || mode == PRO_S) vv[u] = ld2(v_, i0);
+        if (mode == PRO_P || mode == PRO_PZ) pv[u] = ld2((const R*)dst, i0);
       }
     }
 #pragma unroll
@@ -435,13 +447,18 @@ __device__ __noinline__ void ce_colfwd_vec(const CeCtx<R>* cxp, int mode, R c0, 
         if (mode == PRO_P) {
           x.x = rv[u].x + c0 * (pv[u].x - c1 * vv[u].x);
           x.y = rv[u].y + c0 * (pv[u].y - c1 * vv[u].y);
-        } else {
+        } else if (mode == PRO_S) {
           x.x = rv[u].x - c0 * vv[u].x;
           x.y = rv[u].y - c0 * vv[u].y;
+        } else if (mode == PRO_PZ) {
+          x.x = rv[u].x + c0 * pv[u].x;
+          x.y = rv[u].y + c0 * pv[u].y;
+        } else {
+          x = rv[u];
         }
         if (i0 + 1 >= n) x.y = R(0);
         if (i0 >= n) x.x = R(0);
-        st2(dst, i0, n, x);
+        if (mode != PRO_R) st2(dst, i0, n, x);
         X[pp] = x;
       }
     }
@@ -595,6 +612,128 @@ __device__ __noinline__ SolveRes ce_bicgstab(const CeCtx<R>* cxp, bool prec, dou
     cl.sync();
     rho_new = ce_total(s.part, Q, CS_RR0);
     rr = ce_total(s.part, Q, CS_RR);
+  }
+}
+
+// Preconditioned CG on the symmetrised level system (ahat K^{-1} + A) x =
+// K^{-1} b, b_i = (R)(sc r64_i), x0 = 0, with the Strang circulant of
+// Eq. (4.3) up to a constant factor (the same spectrum tables), on the
+// cluster in precision R: the recurrences and the stopping rule of pcg in
+// grid.cuh (||K r|| < tol ||b||, the residual of the original system).
+// Needs cxp->hinv = 1/kappa.  Per iteration: forward pass of p = z + beta p,
+// row pass (A), q = S p with (p, q), the update of x and r with ||K r||, and
+// (with the preconditioner) the forward pass of r, row pass (P^{-1}) and
+// z = P^{-1} r with (r, z).
+template <typename R>
+__device__ __noinline__ SolveRes ce_pcg(const CeCtx<R>* cxp, bool prec, double tol, int max_it,
+                                        const double* __restrict__ r64, double sc) {
+  typedef cplx<R> Z;
+  cg::cluster_group cl = cg::this_cluster();
+  const CeGeo g = ce_enter(cxp);
+  const CeSm<R> s = ce_sm<R>(cxp->lay);
+  const int Q = g.Q, n = g.n;
+  const int npair = (g.N1 >> 1) << g.lgcQ;
+  SolveRes out{TSFDE_OK, 0, 0.0};
+  const KVecs<R> V = cxp->V;
+  // x = 0, p = 0, r = K^{-1} b, ||b||^2 and (r, r)
+  {
+    R acc = R(0), arr = R(0);
+    for (int pp = threadIdx.x; pp < npair; pp += blockDim.x) {
+      const int i0 = pair_i0(g, pp);
+      Z b2 = mkc<R>(R(0), R(0));
+      if (i0 + 1 < n) {
+        const double2 r2 = reinterpret_cast<const double2*>(r64)[i0 >> 1];
+        b2 = mkc<R>((R)(r2.x * sc), (R)(r2.y * sc));
+      } else if (i0 < n) {
+        b2.x = (R)(r64[i0] * sc);
+      }
+      const Z h = (i0 < n) ? ld2(cxp->hinv, i0) : mkc<R>(R(0), R(0));
+      Z rk = mkc<R>(b2.x * h.x, b2.y * h.y);
+      if (i0 + 1 >= n) rk.y = R(0);
+      const Z z = mkc<R>(R(0), R(0));
+      st2(V.x, i0, n, z); st2(V.p, i0, n, z); st2(V.r, i0, n, rk);
+      acc += b2.x * b2.x + b2.y * b2.y;
+      arr += rk.x * rk.x + rk.y * rk.y;
+    }
+    ce_put(s.part, Q, CS_BB, block_sum((double)acc, s.red));
+    ce_put(s.part, Q, CS_RR0, block_sum((double)arr, s.red));
+  }
+  cl.sync();
+  const double bb = ce_total(s.part, Q, CS_BB);
+  double rho = ce_total(s.part, Q, CS_RR0);
+  if (!isfinite(bb)) { out.status = TSFDE_ENONFINITE; return out; }
+  if (bb == 0.0) return out;
+  const double nb = sqrt(bb);
+  // z = P^{-1} r (into V.s), (r, z)
+  auto precond = [&](double& rho_out) {
+    ce_colfwd_vec<R>(cxp, PRO_R, R(0), R(0));
+    cl.sync();
+    ce_rows_apply<R>(cxp, true);
+    cl.sync();
+    const Z acc = ce_colinv_op<R>(cxp, EPI_Z, nullptr);
+    ce_put(s.part, Q, CS_RV, block_sum((double)acc.x, s.red));
+    cl.sync();
+    rho_out = ce_total(s.part, Q, CS_RV);
+  };
+  if (prec) precond(rho);
+  const R* const zv = prec ? V.s : V.r;
+  double rr = bb, beta = 0.0;
+  int it = 0;
+  for (;;) {
+    const double relres = sqrt(rr) / nb;
+    out.relres = relres;
+    out.iters = it;
+    if (!isfinite(relres) || !isfinite(rho)) { out.status = TSFDE_ENONFINITE; return out; }
+    if (relres < tol) return out;
+    if (it >= max_it) { out.status = TSFDE_ENOCONV; return out; }
+    if (!(rho > 0.0)) { out.status = TSFDE_EBREAKDOWN; return out; }
+    out.iters = ++it;
+    // p = z + beta p and its forward pass; q = S p, (p, q)
+    ce_colfwd_vec<R>(cxp, PRO_PZ, (R)beta, R(0), zv);
+    cl.sync();
+    ce_rows_apply<R>(cxp, false);
+    cl.sync();
+    {
+      const Z acc = ce_colinv_op<R>(cxp, EPI_Q, V.p);
+      ce_put(s.part, Q, CS_TS, block_sum((double)acc.x, s.red));
+    }
+    cl.sync();
+    const double pq = ce_total(s.part, Q, CS_TS);
+    if (!isfinite(pq)) { out.status = TSFDE_ENONFINITE; return out; }
+    if (!(pq > 0.0)) { out.status = TSFDE_EBREAKDOWN; return out; }
+    const double alpha = rho / pq;
+    // x += alpha p, r -= alpha q, ||K r||^2 and (r, r)
+    {
+      const R aR = (R)alpha;
+      R akr = R(0), arr = R(0);
+      for (int pp = threadIdx.x; pp < npair; pp += blockDim.x) {
+        const int i0 = pair_i0(g, pp);
+        if (i0 >= n) continue;
+        const Z xv = ld2(V.x, i0), pv = ld2(V.p, i0), rv = ld2(V.r, i0), qv = ld2(V.v, i0);
+        const Z kv = ld2(cxp->kap, i0);
+        const Z x = mkc<R>(xv.x + aR * pv.x, xv.y + aR * pv.y);
+        Z r = mkc<R>(rv.x - aR * qv.x, rv.y - aR * qv.y);
+        if (i0 + 1 >= n) r.y = R(0);
+        st2(V.x, i0, n, x);
+        st2(V.r, i0, n, r);
+        const R k0 = kv.x * r.x, k1 = kv.y * r.y;
+        akr += k0 * k0 + k1 * k1;
+        arr += r.x * r.x + r.y * r.y;
+      }
+      ce_put(s.part, Q, CS_RR, block_sum((double)akr, s.red));
+      ce_put(s.part, Q, CS_RR0, block_sum((double)arr, s.red));
+    }
+    cl.sync();
+    rr = ce_total(s.part, Q, CS_RR);
+    double rho_new = ce_total(s.part, Q, CS_RR0);
+    if (sqrt(rr) / nb < tol) {
+      out.relres = sqrt(rr) / nb;
+      if (!isfinite(out.relres)) out.status = TSFDE_ENONFINITE;
+      return out;
+    }
+    if (prec) precond(rho_new);
+    beta = rho_new / rho;
+    rho = rho_new;
   }
 }
 

@@ -89,8 +89,11 @@ struct SmemAll {
 
 // Shared memory: [tw64 Tp][tw32 Tp][twds Tp][bufA W][bufB W][red 64], the
 // twiddle tables padded (Tp = tpad_len(T), entry k at tpad(k); see dev.cuh)
-__device__ __forceinline__ SmemAll smem_setup(const DevPlan& P) {
+// init_epoch: also clear the CTA's grid-barrier epoch (at the start of a
+// kernel; not when the tables are reloaded in mid-kernel).
+__device__ __forceinline__ SmemAll smem_setup(const DevPlan& P, bool init_epoch = true) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (init_epoch && threadIdx.x == 0) s_grid_epoch = 0u;
   char* base = reinterpret_cast<char*>(smem_raw);
   const size_t Tp = (size_t)tpad_len(P.T);
   double2* tw64 = reinterpret_cast<double2*>(base);
@@ -119,7 +122,7 @@ __device__ __forceinline__ SmemAll smem_setup(const DevPlan& P) {
 }
 
 __device__ __forceinline__ void put_partial(const DevPlan& P, int slot, double v) {
-  if (threadIdx.x == 0) P.part[slot * P.G + blockIdx.x] = v;
+  if (threadIdx.x == 0) grid_partials_next(P.part, P.G)[slot * P.G + blockIdx.x] = v;
 }
 // Grid barrier; the _sum variants also return the grid-wide reduction of
 // the partial slots written before the barrier (bit-identical in all CTAs).

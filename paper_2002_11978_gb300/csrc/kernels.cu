@@ -429,7 +429,7 @@ constexpr int kStaticMaxG = 1024;    // largest cooperative grid
 // tw64 | tw32 | sym | sig | rho | S1 | S2
 constexpr size_t kSA_bar = 0;
 constexpr size_t kSA_part = 256;
-constexpr size_t kSA_status = kSA_part + sizeof(double) * kSlots * kStaticMaxG;
+constexpr size_t kSA_status = kSA_part + sizeof(double) * 2 * kSlots * kStaticMaxG;
 constexpr size_t kSA_tw64 = kSA_status + 256;
 constexpr size_t kSA_tw32 = kSA_tw64 + sizeof(double2) * kStaticMaxL;
 constexpr size_t kSA_sym = kSA_tw32 + sizeof(float2) * kStaticMaxL;
@@ -456,6 +456,7 @@ __device__ double static_gap_pow(double k, double nu) {
 }
 
 __global__ void __launch_bounds__(kThreads, 2) k_apply_static(StaticApplyArgs A) {
+  grid_epoch_init();
   const DevPlan& P = A.P;
   const int n = P.n, L = P.L;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -493,7 +494,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_apply_static(StaticApplyArgs A)
                       2.0 * nu / (A.alpha * pow(Nd, A.alpha)));
   }
   if (!gsync(P, red0)) { if (blockIdx.x == 0 && threadIdx.x == 0) *A.status = TSFDE_ETIMEOUT; return; }
-  SmemAll S = smem_setup(P);
+  SmemAll S = smem_setup(P, false);  // the barrier epoch runs on from grid_epoch_init
   // spectrum of the even embedding of the symbol -> (sigma, rho) tables
   const double* sym = A.sym;
   auto proE = [&](int i) -> double {

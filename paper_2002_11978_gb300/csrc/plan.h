@@ -21,16 +21,11 @@ struct __align__(8) dsf {
 struct __align__(16) dsf2 { dsf x, y; };
 
 // Bounded grid barrier state (cleared by the host before each cooperative
-// launch); see grid_sync_red in dev.cuh.  The arrival counter and the
-// release word sit on separate 128-byte lines so that polling does not
-// contend with arrivals.
+// launch); see grid_sync_red in dev.cuh.
 struct GridBarrier {
   unsigned int count;     // arrivals, monotonic within one launch
   int err;                // set once any CTA gave up waiting
   unsigned int pad0[30];
-  unsigned int gen;       // number of completed barriers
-  unsigned int pad1[31];
-  double result[16];      // scalars reduced by the last CTA to arrive
 };
 
 // One factorisation Nfft = N1 * N2 of a power-of-two transform, driven by
@@ -98,7 +93,7 @@ struct DevPlan {
   int G;       // CTAs of the cooperative grid
   long long timeout;  // barrier wait budget (SM cycles)
   GridBarrier* bar;
-  double* part;       // [kSlots][G] per-CTA partial sums
+  double* part;       // [2][kSlots][G] per-CTA partial sums, by barrier parity
   const double2* twL64;  // W_L^k, k < L
   const float2* twL32;
   // Toeplitz symbol spectrum S (DFT_L of the even embedding), in the (k1,k2)
@@ -206,6 +201,8 @@ struct BInst {
   const double* phi;
   const double* kap64;
   const float* kap32;
+  const double* hinv64;  // 1/kappa (PCG)
+  const float* hinv32;
   const double* f;
   double* H;             // E x ld scaled SOE history
   double* u[3];          // rotating levels
@@ -239,6 +236,7 @@ struct BatchArgs {
   double tol, inner_tol;
   int max_it, max_outer, inner_max_it;
   int warm;              // start each level from u^{m-1}
+  int krylov;            // TSFDE_KRYLOV_BICGSTAB or TSFDE_KRYLOV_PCG
   const double2* tw64;   // W_Lmax^k
   const float2* tw32;
   CeLay lay;             // shared-memory layout (sized for the largest instance)

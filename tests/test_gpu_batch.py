@@ -56,15 +56,17 @@ def _single(torch, p, precision="fp64"):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batch_matches_oracle(torch, precision):
+@pytest.mark.parametrize("krylov", ["bicgstab", "pcg"])
+def test_batch_matches_oracle(torch, precision, krylov):
     """Five instances of different n, alpha, gamma (cluster sizes from 4 to
     8 CTAs' worth of rows), M = 12: each u^M against the oracle's dense FIDS
-    march with its plain SOE table (both tables within 1e-12)."""
+    march with its plain SOE table (both tables within 1e-12), with the
+    paper's BiCGSTAB or PCG on the symmetrised system (ce_pcg)."""
     M = 12
     specs = [(0, 63, 1.5, 0.5), (1, 127, 0.8, 0.3), (2, 200, 1.9, 0.8), (3, 511, 1.2, 0.6),
              (4, 96, 0.6, 0.2)]
     inst, probs = _instances(torch, specs, M)
-    bs, U, info = _batch(torch, inst, M, precision=precision)
+    bs, U, info = _batch(torch, inst, M, precision=precision, krylov=krylov)
     assert info["status"] == 0 and info["iterations"] > 0, info
     for p, u in zip(probs, U):
         tm, tau = oracle.graded_mesh(p.T, M, p.r)
@@ -223,3 +225,19 @@ def test_batch_large_class_certified(torch):
             ahat = oracle.l1_weight(p.T, M, p.r, p.gamma, m, m) / math.gamma(1 - p.gamma)
             bound, l33 = certify.certify_level(t, ahat, p.kappa0, U[m], b)
             assert bound <= 1e-10 * np.max(np.abs(U[m])), (p.n, m, bound, l33)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_pcg_matches_batch_bicgstab_at_workload_sizes(torch, precision):
+    """The batched workload's size range (transforms of L = 1024 to 32768),
+    M = 64 levels, warm start: PCG on the symmetrised system and BiCGSTAB
+    reach the same u^M (both stop at the same residual test; FP64 at 1e-13,
+    as the benchmark compares the arms)."""
+    M = 64
+    inst, probs = _instances(torch, _mixed_specs(), M)
+    tol = 1e-13 if precision == "fp64" else 1e-12
+    _, Ub, ib = _batch(torch, inst, M, precision=precision, krylov="bicgstab", warm_start=True, krylov_tol=tol)
+    _, Up, ip = _batch(torch, inst, M, precision=precision, krylov="pcg", warm_start=True, krylov_tol=tol)
+    assert ib["status"] == 0 and ip["status"] == 0, (ib, ip)
+    for a, b in zip(Ub, Up):
+        assert np.max(np.abs(a - b)) / np.max(np.abs(a)) < 1e-10
