@@ -161,8 +161,8 @@ typedef struct tsfde_opts {
                            TSFDE_HISTORY_DIRECT (DIDS); the batched solve
                            accepts SOE only                                 */
   int krylov;           /* TSFDE_KRYLOV_BICGSTAB (default), TSFDE_KRYLOV_PCG
-                           or TSFDE_KRYLOV_AUTO; the batched solve accepts
-                           BICGSTAB or PCG (one method for the batch)      */
+                           or TSFDE_KRYLOV_AUTO; in the batched solve AUTO
+                           chooses per level within each instance's march */
   int ckpt_stride;      /* adjoint checkpoints: every ckpt_stride-th level of
                            the forward march (level 0 at each reset) keeps
                            u^{k-1}, u^k and the SOE history, so that
@@ -337,8 +337,10 @@ int tsfde_adjoint(tsfde_ctx* ctx, const double* u_all, const double* dJ_duM,
  * independent per instance.  Options (tsfde_opts): mu / kappa_mu (common),
  * precision (MIXED: FP32 Krylov sweeps refined in FP64 with the FP64
  * fallback of the single-problem path; FP64: the Krylov solve in FP64),
- * krylov (BICGSTAB, or PCG on the symmetrised system), krylov_tol, max_it,
- * inner_tol, max_outer, inner_max_it, precond, stream.
+ * krylov (BICGSTAB, PCG on the symmetrised system, or AUTO: the per-level
+ * choice of TSFDE_KRYLOV_AUTO made within each instance's march from the
+ * cluster's own level times), krylov_tol, max_it, inner_tol, max_outer,
+ * inner_max_it, precond, stream.
  * Each instance needs n >= 31 (its transforms are split over the cluster). */
 typedef struct tsfde_instance {
   double alpha, gamma, l, T, r;  /* as tsfde_setup                           */

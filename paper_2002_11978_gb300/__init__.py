@@ -462,7 +462,7 @@ def _batch_args(instances, precision="mixed", precond="strang", krylov_tol=1e-12
                 inner_tol=1e-2, max_outer=60, inner_max_it=40, mu=None, kappa_mu=None, stream=None,
                 cluster_size=0, warm_start=False, krylov="bicgstab"):
     o = default_opts()
-    o.krylov = {"bicgstab": TSFDE_KRYLOV_BICGSTAB, "pcg": TSFDE_KRYLOV_PCG}[krylov]
+    o.krylov = {"bicgstab": TSFDE_KRYLOV_BICGSTAB, "pcg": TSFDE_KRYLOV_PCG, "auto": TSFDE_KRYLOV_AUTO}[krylov]
     o.cluster_size = cluster_size
     o.warm_start = 1 if warm_start else 0
     o.krylov_tol = krylov_tol

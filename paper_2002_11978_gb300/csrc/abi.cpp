@@ -171,7 +171,13 @@ int ilog2(int64_t x) {
   return k;
 }
 
-Geo make_geo(int Nfft) {
+// Column tiles are sized so that their count matches the N1/2 + 1 row pairs
+// (one work item per CTA in every pass): one column per tile when
+// N1 = 2 N2, two when N1 = N2.  The real-input geometry keeps one column
+// (its passes run at prefetch depth 2, which covers N1 elements per item up
+// to n = 2^17 - 1); the complex geometry of the preconditioner build (depth
+// 4) takes two when N1 = N2.
+Geo make_geo(int Nfft, bool pair_columns) {
   Geo g{};
   const int lg = ilog2(Nfft);
   g.Nfft = Nfft;
@@ -179,8 +185,9 @@ Geo make_geo(int Nfft) {
   g.N1 = 1 << g.lgN1;
   g.lgN2 = lg - g.lgN1;
   g.N2 = 1 << g.lgN2;
-  g.lgct64 = 0;  // one column per tile: N2 tiles balance the N1/2+1 row pairs
-  g.lgct32 = 0;
+  const int lc = (pair_columns && g.N1 == g.N2 && g.N2 >= 2) ? 1 : 0;
+  g.lgct64 = lc;
+  g.lgct32 = lc;
   return g;
 }
 
@@ -336,8 +343,8 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
   P.n = (int)n;
   P.L = (int)L;
   P.Nc = (int)(L / 2);
-  P.gr = make_geo(P.Nc);
-  P.gc = make_geo(P.L);
+  P.gr = make_geo(P.Nc, false);
+  P.gc = make_geo(P.L, false);
   P.T = std::max(std::max(P.gr.N1, P.gr.N2), std::max(P.gc.N1, P.gc.N2));
   P.W = std::max(std::max(P.gr.N1 << P.gr.lgct64, 2 * P.gr.N2),
                  std::max(P.gc.N1 << P.gc.lgct64, 2 * P.gc.N2));
@@ -449,8 +456,10 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
   ok &= dalloc(c, &c->b, n) && dalloc(c, &c->kappa64, n) && dalloc(c, &c->kappa32, ld);
   ok &= dalloc(c, &c->phi, n) && dalloc(c, &c->kap0, n) && dalloc(c, &c->kap1d, n);
   ok &= dalloc(c, &c->F, 4 * n) && dalloc(c, &c->r64, n);
+  // Krylov vectors of every arithmetic: length ld (even, zero padded), so
+  // that entries can be moved in aligned pairs
   double** v64[] = {&c->k64.r, &c->k64.rh, &c->k64.p, &c->k64.v, &c->k64.s, &c->k64.t, &c->k64.ph, &c->k64.sh};
-  for (double** p : v64) ok &= dalloc(c, p, n);
+  for (double** p : v64) ok &= dalloc(c, p, ld);
   float** v32[] = {&c->k32.x, &c->k32.r, &c->k32.rh, &c->k32.p, &c->k32.v, &c->k32.s, &c->k32.t, &c->k32.ph, &c->k32.sh};
   for (float** p : v32) ok &= dalloc(c, p, ld);
   ok &= dalloc(c, &c->stats, M + 1) && dalloc(c, &c->status, 1);

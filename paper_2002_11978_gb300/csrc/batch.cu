@@ -42,7 +42,27 @@ struct BatchCtx {
   CeCtx<double> c64;
   BInst I;
   int inst;
+  int method;  // Krylov method of the current level (TSFDE_KRYLOV_BICGSTAB / _PCG)
 };
+
+// Per-instance choice of the Krylov method (TSFDE_KRYLOV_AUTO), the rule of
+// KrylovAuto (plan.h) applied to one instance's march: the latest level time
+// of each method, and a probe of the other method when it was faster at its
+// latest sample, has none, or its sample is older than 8 r^2 levels (8..64).
+struct BatchAuto {
+  double t[2];
+  int at[2];
+};
+__device__ __forceinline__ int bt_auto_next(BatchAuto& k, int me, int m, double dt) {
+  const int ot = 1 - me;
+  k.t[me] = dt;
+  k.at[me] = m;
+  if (k.at[ot] == 0) return ot;
+  const double r = k.t[ot] / dt;
+  if (!(r >= 1.0)) return ot;
+  const double interval = fmin(fmax(8.0 * r * r, 8.0), 64.0);
+  return ((double)(m + 1 - k.at[ot]) >= interval) ? ot : me;
+}
 
 size_t batch_smem_bytes(const CeLay& lay) { return ce_ctx_offset(lay) + sizeof(BatchCtx); }
 
@@ -339,9 +359,9 @@ __device__ __noinline__ void bt_copy_out(const BatchCtx* bx, int m) {
 // The level's Krylov solve on the cluster: BiCGSTAB or PCG on the
 // symmetrised system.
 template <typename R>
-__device__ __forceinline__ SolveRes bt_krylov(const CeCtx<R>* cx, const BatchArgs& A, bool prec, double tol,
+__device__ __forceinline__ SolveRes bt_krylov(const CeCtx<R>* cx, int method, bool prec, double tol,
                                               int max_it, const double* r64, double sc) {
-  if (A.krylov == TSFDE_KRYLOV_PCG) return ce_pcg<R>(cx, prec, tol, max_it, r64, sc);
+  if (method == TSFDE_KRYLOV_PCG) return ce_pcg<R>(cx, prec, tol, max_it, r64, sc);
   return ce_bicgstab<R>(cx, prec, tol, max_it, r64, sc);
 }
 
@@ -385,7 +405,7 @@ __device__ LevelOut bt_level(BatchCtx* bx, const BatchArgs& A, int m, bool prev_
   __syncthreads();
   if (A.precision == TSFDE_FP64) {
     const double scale = sqrt(rr0 / bb);
-    const SolveRes r = bt_krylov<double>(&bx->c64, A, prec, A.tol / scale, A.max_it, I.r64, 1.0);
+    const SolveRes r = bt_krylov<double>(&bx->c64, bx->method, prec, A.tol / scale, A.max_it, I.r64, 1.0);
     cl.sync();
     if (warm && r.status == TSFDE_OK) bt_add_fp64(bx, m);
     o.status = r.status;
@@ -401,7 +421,7 @@ __device__ LevelOut bt_level(BatchCtx* bx, const BatchArgs& A, int m, bool prev_
   const double ah = I.ahat[m];
   while (!fallback) {
     if (o.outer >= A.max_outer) { fallback = true; break; }
-    const SolveRes ir = bt_krylov<float>(&bx->c32, A, prec, A.inner_tol, A.inner_max_it, I.r64, 1.0 / nr);
+    const SolveRes ir = bt_krylov<float>(&bx->c32, bx->method, prec, A.inner_tol, A.inner_max_it, I.r64, 1.0 / nr);
     o.iters += ir.iters;
     ++o.outer;
     cl.sync();
@@ -440,7 +460,7 @@ __device__ LevelOut bt_level(BatchCtx* bx, const BatchArgs& A, int m, bool prev_
   }
   if (fallback && o.status == TSFDE_OK) {
     const double tol_d = fmax(A.tol * nb / nr, 1e-14);
-    const SolveRes fr = bt_krylov<double>(&bx->c64, A, prec, tol_d, A.max_it, I.r64, 1.0);
+    const SolveRes fr = bt_krylov<double>(&bx->c64, bx->method, prec, tol_d, A.max_it, I.r64, 1.0);
     cl.sync();
     if (fr.status == TSFDE_OK) {
       bt_add_fp64(bx, m);
@@ -489,8 +509,27 @@ __global__ void __launch_bounds__(kBT, 2) k_batch(BatchArgs A) {
     int nfp64 = 0, status = TSFDE_OK;
     double worst = 0.0;
     bool prev_fp64 = false;
+    // Krylov method: fixed, or chosen per level from CTA 0's level times
+    BatchAuto ka{{0.0, 0.0}, {0, 0}};
+    if (threadIdx.x == 0) bx->method = (A.krylov == TSFDE_KRYLOV_PCG) ? TSFDE_KRYLOV_PCG : TSFDE_KRYLOV_BICGSTAB;
+    __syncthreads();
     for (int m = 1; m <= A.M; ++m) {
+      unsigned long long t0 = 0;
+      if (A.krylov == TSFDE_KRYLOV_AUTO && cl.block_rank() == 0 && threadIdx.x == 0)
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
       const LevelOut o = bt_level(bx, A, m, prev_fp64);
+      if (A.krylov == TSFDE_KRYLOV_AUTO) {
+        // CTA 0 picks the next level's method and hands it to every CTA
+        if (cl.block_rank() == 0 && threadIdx.x == 0) {
+          unsigned long long t1;
+          asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+          const int me = bx->method == TSFDE_KRYLOV_PCG ? 1 : 0;
+          const double dt = o.status == TSFDE_OK ? (double)(t1 - t0) : INFINITY;
+          const int next = bt_auto_next(ka, me, m, dt) ? TSFDE_KRYLOV_PCG : TSFDE_KRYLOV_BICGSTAB;
+          for (int r = 0; r < Q; ++r) cl.map_shared_rank(&bx->method, r)[0] = next;
+        }
+        cl.sync();
+      }
       prev_fp64 = o.fp64;
       its += o.iters;
       outer += o.outer;

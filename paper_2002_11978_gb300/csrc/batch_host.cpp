@@ -273,8 +273,8 @@ int tsfde_batch_setup_plan(tsfde_batch** out, int B, const tsfde_instance* inst,
   if (opts) o = *opts; else tsfde_default_opts(&o);
   if (o.precision != TSFDE_FP64 && o.precision != TSFDE_MIXED) return TSFDE_EINVAL;
   if (o.history == TSFDE_HISTORY_DIRECT) return TSFDE_ENOTSUP;  // FIDS only
-  if (o.krylov == TSFDE_KRYLOV_AUTO) return TSFDE_ENOTSUP;       // one method per batch
-  if (o.krylov != TSFDE_KRYLOV_BICGSTAB && o.krylov != TSFDE_KRYLOV_PCG) return TSFDE_EINVAL;
+  if (o.krylov != TSFDE_KRYLOV_BICGSTAB && o.krylov != TSFDE_KRYLOV_PCG && o.krylov != TSFDE_KRYLOV_AUTO)
+    return TSFDE_EINVAL;
   if (o.history != TSFDE_HISTORY_SOE) return TSFDE_EINVAL;
   if (o.precond != TSFDE_STRANG && o.precond != TSFDE_PRECOND_NONE) return TSFDE_EINVAL;
   if (!(o.krylov_tol > 0.0) || o.max_it < 1) return TSFDE_EINVAL;

@@ -177,6 +177,18 @@ constexpr int kPre = 4;
 // column FFTs over j1 (j = N2 j1 + j2), twiddle W_Nc^{j2 k1}, store
 // S1[k1*N2 + j2].  Without FULL only rows j1 < N1/2 can be non-zero
 // (nin <= L/2).
+// A prologue of passA_real may take the entries in pairs: invocable as
+// pro(PairTag{}, i0) for even i0 < nin, returning entries i0 and i0 + 1 (the
+// latter is dropped when i0 + 1 >= nin), so that its loads and stores can be
+// 16-byte pair accesses issued together.  Otherwise pro(i) gives entry i.
+struct PairTag {};
+template <typename R> __device__ __forceinline__ cplx<R> ld_pair(const R* v, int i0) {
+  return reinterpret_cast<const cplx<R>*>(v)[i0 >> 1];
+}
+template <typename R> __device__ __forceinline__ void st_pair(R* v, int i0, cplx<R> z) {
+  reinterpret_cast<cplx<R>*>(v)[i0 >> 1] = z;
+}
+
 // out: where the column transforms go (NULL: S1).
 template <typename R, bool FULL, int KP = kPre, class Pro>
 __device__ void passA_real(const DevPlan& P, const Smem<R>& sm, int nin, Pro& pro,
@@ -207,9 +219,16 @@ __device__ void passA_real(const DevPlan& P, const Smem<R>& sm, int nin, Pro& pr
       Z v = mkc<R>(R(0), R(0));
       if (j1 < rows) {
         const int i0 = 2 * (N2 * j1 + c0 + c);
-        const R x0 = (i0 < nin) ? pro(i0) : R(0);
-        const R x1 = (i0 + 1 < nin) ? pro(i0 + 1) : R(0);
-        v = mkc<R>(x0, x1);
+        if constexpr (std::is_invocable_v<Pro&, PairTag, int>) {
+          if (i0 < nin) {
+            v = pro(PairTag{}, i0);
+            if (i0 + 1 >= nin) v.y = R(0);
+          }
+        } else {
+          const R x0 = (i0 < nin) ? pro(i0) : R(0);
+          const R x1 = (i0 + 1 < nin) ? pro(i0 + 1) : R(0);
+          v = mkc<R>(x0, x1);
+        }
       }
       sm.bA[e] = v;
     }
@@ -570,13 +589,18 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
     const double beta = (rho_new / rho) * (alpha / omega);
     rho = rho_new;
     out.iters = ++it;
-    // p = r + beta (p - omega v)
+    // p = r + beta (p - omega v), in pairs (the Krylov vectors are padded)
     {
       const R bR = (R)beta, oR = (R)omega;
-      auto pro = [&](int i) -> R {
-        const R pi = V.r[i] + bR * (V.p[i] - oR * V.v[i]);
-        V.p[i] = pi;
-        return (TR && !prec) ? kap[i] * pi : pi;
+      auto pro = [&](PairTag, int i0) -> cplx<R> {
+        const cplx<R> r2 = ld_pair(V.r, i0), p2 = ld_pair(V.p, i0), v2 = ld_pair(V.v, i0);
+        const cplx<R> q = mkc<R>(r2.x + bR * (p2.x - oR * v2.x), r2.y + bR * (p2.y - oR * v2.y));
+        st_pair(V.p, i0, q);
+        if (TR && !prec) {
+          const cplx<R> k2 = mkc<R>(kap[i0], i0 + 1 < n ? kap[i0 + 1] : R(0));
+          return mkc<R>(k2.x * q.x, k2.y * q.y);
+        }
+        return q;
       };
       passA_real<R, false, KP>(P, sm, n, pro);
     }
@@ -607,13 +631,18 @@ __device__ SolveRes bicgstab(const DevPlan& P, const Smem<R>& sm, const KVecs<R>
     if (!isfinite(rv)) { out.status = TSFDE_ENONFINITE; return out; }
     if (rv == 0.0) { out.status = TSFDE_EBREAKDOWN; return out; }
     alpha = rho / rv;
-    // s = r - alpha v
+    // s = r - alpha v, in pairs
     {
       const R aR = (R)alpha;
-      auto pro = [&](int i) -> R {
-        const R si = V.r[i] - aR * V.v[i];
-        V.s[i] = si;
-        return (TR && !prec) ? kap[i] * si : si;
+      auto pro = [&](PairTag, int i0) -> cplx<R> {
+        const cplx<R> r2 = ld_pair(V.r, i0), v2 = ld_pair(V.v, i0);
+        const cplx<R> q = mkc<R>(r2.x - aR * v2.x, r2.y - aR * v2.y);
+        st_pair(V.s, i0, q);
+        if (TR && !prec) {
+          const cplx<R> k2 = mkc<R>(kap[i0], i0 + 1 < n ? kap[i0 + 1] : R(0));
+          return mkc<R>(k2.x * q.x, k2.y * q.y);
+        }
+        return q;
       };
       passA_real<R, false, KP>(P, sm, n, pro);
     }

@@ -142,16 +142,17 @@ def test_setup_validates_krylov(lib):
 
 
 def test_batch_krylov_option(lib):
-    """The batched solve takes one method for the whole batch: AUTO is not
-    supported; PCG is accepted (this instance is then rejected for its NULL
-    data pointers, before any device work)."""
+    """The batched solve accepts BiCGSTAB, PCG and AUTO, and rejects other
+    values; an instance with NULL data pointers is rejected before any
+    device work."""
     import paper_2002_11978_gb300 as pkg
     o = pkg.default_opts()
     inst = (pkg.tsfde_instance * 1)()
     inst[0] = pkg.tsfde_instance(1.5, 0.5, 1.0, 1.0, 3.0, 63, 1e-12, None, None, None)
     b = ctypes.c_void_p()
-    o.krylov = pkg.TSFDE_KRYLOV_AUTO
-    assert lib.tsfde_batch_setup(ctypes.byref(b), 1, inst, 8, ctypes.byref(o)) == pkg.TSFDE_ENOTSUP
-    o.krylov = pkg.TSFDE_KRYLOV_PCG
+    o.krylov = 7
     assert lib.tsfde_batch_setup(ctypes.byref(b), 1, inst, 8, ctypes.byref(o)) == pkg.TSFDE_EINVAL
+    for k in (pkg.TSFDE_KRYLOV_PCG, pkg.TSFDE_KRYLOV_AUTO):
+        o.krylov = k
+        assert lib.tsfde_batch_setup(ctypes.byref(b), 1, inst, 8, ctypes.byref(o)) == pkg.TSFDE_EINVAL
     assert not b

@@ -56,7 +56,7 @@ def _single(torch, p, precision="fp64"):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("krylov", ["bicgstab", "pcg"])
+@pytest.mark.parametrize("krylov", ["bicgstab", "pcg", "auto"])
 def test_batch_matches_oracle(torch, precision, krylov):
     """Five instances of different n, alpha, gamma (cluster sizes from 4 to
     8 CTAs' worth of rows), M = 12: each u^M against the oracle's dense FIDS
@@ -230,14 +230,15 @@ def test_batch_large_class_certified(torch):
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_batch_pcg_matches_batch_bicgstab_at_workload_sizes(torch, precision):
     """The batched workload's size range (transforms of L = 1024 to 32768),
-    M = 64 levels, warm start: PCG on the symmetrised system and BiCGSTAB
-    reach the same u^M (both stop at the same residual test; FP64 at 1e-13,
+    M = 64 levels, warm start: PCG on the symmetrised system, the per-level
+    choice (auto) and BiCGSTAB reach the same u^M (both stop at the same residual test; FP64 at 1e-13,
     as the benchmark compares the arms)."""
     M = 64
     inst, probs = _instances(torch, _mixed_specs(), M)
     tol = 1e-13 if precision == "fp64" else 1e-12
     _, Ub, ib = _batch(torch, inst, M, precision=precision, krylov="bicgstab", warm_start=True, krylov_tol=tol)
-    _, Up, ip = _batch(torch, inst, M, precision=precision, krylov="pcg", warm_start=True, krylov_tol=tol)
-    assert ib["status"] == 0 and ip["status"] == 0, (ib, ip)
-    for a, b in zip(Ub, Up):
-        assert np.max(np.abs(a - b)) / np.max(np.abs(a)) < 1e-10
+    for kry in ("pcg", "auto"):
+        _, Up, ip = _batch(torch, inst, M, precision=precision, krylov=kry, warm_start=True, krylov_tol=tol)
+        assert ib["status"] == 0 and ip["status"] == 0, (kry, ib, ip)
+        for a, b in zip(Ub, Up):
+            assert np.max(np.abs(a - b)) / np.max(np.abs(a)) < 1e-10, kry
