@@ -344,7 +344,7 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
   P.L = (int)L;
   P.Nc = (int)(L / 2);
   P.gr = make_geo(P.Nc, false);
-  P.gc = make_geo(P.L, false);
+  P.gc = make_geo(P.L, true);
   P.T = std::max(std::max(P.gr.N1, P.gr.N2), std::max(P.gc.N1, P.gc.N2));
   P.W = std::max(std::max(P.gr.N1 << P.gr.lgct64, 2 * P.gr.N2),
                  std::max(P.gc.N1 << P.gc.lgct64, 2 * P.gc.N2));
