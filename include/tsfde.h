@@ -32,6 +32,7 @@
 #ifndef TSFDE_H
 #define TSFDE_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -87,9 +88,10 @@ enum { TSFDE_HISTORY_SOE = 0, TSFDE_HISTORY_DIRECT = 1 };
 /* AUTO: each level of tsfde_step / tsfde_solve takes whichever of the two
  * is cheaper there, decided on the device from measured level times: the
  * method of the previous level, unless the other one was faster at its latest
- * sample, or that sample is older than 8 r^2 levels (8..64; r = how many
- * times slower it was), in which case the other one is tried.  The first
- * level uses BiCGSTAB, the second PCG.  PCG is weak where a K^{-1}
+ * sample, or a trial of the other one is due: 8 r^2 levels (8..64; r = how
+ * many times slower it was) after its latest sample, doubled for each
+ * trial of it lost in a row (at most 16 times).  The first level uses
+ * BiCGSTAB, the second PCG.  PCG is weak where a K^{-1}
  * dominates (large a_m, the first levels of a graded mesh: its circulant
  * preconditioner cannot follow the variation of 1/kappa) and strong where A
  * dominates; BiCGSTAB the other way round.  Per-level stats report the
@@ -478,6 +480,18 @@ int tsfde_linear_solve(tsfde_ctx* ctx, double a, const double* kappa,
  *    for its own completion and returns the kernel's status. */
 int tsfde_toeplitz_apply_static(double alpha, double mu, int kappa_mu, double l,
                                 int64_t n, const double* v, double* y, void* stream);
+
+/* ---- measurement helper ------------------------------------------------
+ * Not part of the method.  Streams 16-byte loads that bypass L1 over the
+ * device buffer buf (bytes long, 16-byte aligned, a multiple of 16) `reps`
+ * times with every resident thread of the GPU, enqueued on `stream`
+ * (cudaStream_t, NULL = default) without waiting.  The caller sizes buf to
+ * fit in L2, warms it with one call and times a second one (CUDA events on
+ * the same stream): bytes * reps / time is the L2 read bandwidth against
+ * which the level kernels, whose vectors stay in L2, are reported.  No
+ * allocation; nothing is written.  TSFDE_EINVAL for a NULL, unaligned or
+ * short buffer or reps < 1; TSFDE_ECUDA if the launch fails. */
+int tsfde_probe_l2_read(const void* buf, size_t bytes, int reps, void* stream);
 
 #ifdef __cplusplus
 }

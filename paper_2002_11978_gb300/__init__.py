@@ -144,6 +144,7 @@ _SIGNATURES = [
                                           ctypes.POINTER(tsfde_step_info)]),
     ("tsfde_toeplitz_apply_static", ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                    ctypes.c_double, ctypes.c_int64, _V, _V, _V]),
+    ("tsfde_probe_l2_read", ctypes.c_int, [_V, ctypes.c_size_t, ctypes.c_int, _V]),
 ]
 
 _lib = None
@@ -520,6 +521,18 @@ def toeplitz_apply_static(alpha, n, v, y, l=1.0, mu=None, kappa_mu=None, stream=
                                            0 if kappa_mu is None else kappa_mu, l, int(n),
                                            _dev(v, n, "v"), _dev(y, n, "y"),
                                            _stream_handle(stream)))
+
+
+def probe_l2_read(buf, reps, stream=None):
+    """Enqueue tsfde_probe_l2_read over the CUDA tensor buf (its whole
+    storage, 16-byte aligned) `reps` times on `stream`; time it with events
+    on that stream."""
+    lib = load_library()
+    nbytes = buf.numel() * buf.element_size()
+    if not buf.is_cuda or not buf.is_contiguous():
+        raise ValueError("buf must be a contiguous CUDA tensor")
+    _check(lib.tsfde_probe_l2_read(ctypes.c_void_p(buf.data_ptr()), nbytes, int(reps),
+                                   _stream_handle(stream)))
 
 
 def _prec(p):

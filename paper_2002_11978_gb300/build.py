@@ -16,7 +16,7 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libtsfde.so")
 BUILD = os.path.join(ROOT, "_build")
 
-SOURCES = ["kernels.cu", "level64.cu", "level64_pcg.cu", "level32.cu", "level32_pcg.cu", "levelds.cu", "levelds_pcg.cu", "cluster.cu", "batch.cu", "abi.cpp", "batch_host.cpp", "host_math.cpp"]
+SOURCES = ["kernels.cu", "level64.cu", "level64_pcg.cu", "level32.cu", "level32_pcg.cu", "levelds.cu", "levelds_pcg.cu", "cluster.cu", "batch.cu", "abi.cpp", "batch_host.cpp", "host_math.cpp", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 

@@ -651,6 +651,7 @@ int tsfde_reset(tsfde_ctx* c) {
     KrylovAuto k0{};
     k0.for_level = 1;
     k0.choice = 0;
+    auto_rule_init(k0.rule);
     c->kauto_init = k0;
     if ((e = cudaMemcpyAsync(c->kauto, &c->kauto_init, sizeof(KrylovAuto), cudaMemcpyHostToDevice, c->stream)) !=
         cudaSuccess)

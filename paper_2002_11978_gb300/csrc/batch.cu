@@ -45,25 +45,6 @@ struct BatchCtx {
   int method;  // Krylov method of the current level (TSFDE_KRYLOV_BICGSTAB / _PCG)
 };
 
-// Per-instance choice of the Krylov method (TSFDE_KRYLOV_AUTO), the rule of
-// KrylovAuto (plan.h) applied to one instance's march: the latest level time
-// of each method, and a probe of the other method when it was faster at its
-// latest sample, has none, or its sample is older than 8 r^2 levels (8..64).
-struct BatchAuto {
-  double t[2];
-  int at[2];
-};
-__device__ __forceinline__ int bt_auto_next(BatchAuto& k, int me, int m, double dt) {
-  const int ot = 1 - me;
-  k.t[me] = dt;
-  k.at[me] = m;
-  if (k.at[ot] == 0) return ot;
-  const double r = k.t[ot] / dt;
-  if (!(r >= 1.0)) return ot;
-  const double interval = fmin(fmax(8.0 * r * r, 8.0), 64.0);
-  return ((double)(m + 1 - k.at[ot]) >= interval) ? ot : me;
-}
-
 size_t batch_smem_bytes(const CeLay& lay) { return ce_ctx_offset(lay) + sizeof(BatchCtx); }
 
 __device__ __forceinline__ CeGeo geo_q(const CeGeo& g0) {
@@ -509,8 +490,10 @@ __global__ void __launch_bounds__(kBT, 2) k_batch(BatchArgs A) {
     int nfp64 = 0, status = TSFDE_OK;
     double worst = 0.0;
     bool prev_fp64 = false;
-    // Krylov method: fixed, or chosen per level from CTA 0's level times
-    BatchAuto ka{{0.0, 0.0}, {0, 0}};
+    // Krylov method: fixed, or chosen per level by auto_rule_next (plan.h)
+    // from CTA 0's level times
+    AutoRule ka;
+    auto_rule_init(ka);
     if (threadIdx.x == 0) bx->method = (A.krylov == TSFDE_KRYLOV_PCG) ? TSFDE_KRYLOV_PCG : TSFDE_KRYLOV_BICGSTAB;
     __syncthreads();
     for (int m = 1; m <= A.M; ++m) {
@@ -525,7 +508,7 @@ __global__ void __launch_bounds__(kBT, 2) k_batch(BatchArgs A) {
           asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
           const int me = bx->method == TSFDE_KRYLOV_PCG ? 1 : 0;
           const double dt = o.status == TSFDE_OK ? (double)(t1 - t0) : INFINITY;
-          const int next = bt_auto_next(ka, me, m, dt) ? TSFDE_KRYLOV_PCG : TSFDE_KRYLOV_BICGSTAB;
+          const int next = auto_rule_next(ka, me, m, dt) ? TSFDE_KRYLOV_PCG : TSFDE_KRYLOV_BICGSTAB;
           for (int r = 0; r < Q; ++r) cl.map_shared_rank(&bx->method, r)[0] = next;
         }
         cl.sync();

@@ -33,34 +33,18 @@ __device__ __forceinline__ bool auto_mine(const LevelArgs& A, bool pcg) {
 
 // End of a level solved by method `pcg`: block 0's thread 0 (which wrote the
 // level's status) records the method in the level's stats and, for AUTO,
-// the level's device time, then picks the next level's method: the other
-// method if it was faster at its latest sample, has none yet, or its sample
-// is older than the probe interval 8 r^2 levels (8..64), r = how many times
-// slower it was.  A failed level counts as infinitely slow.
+// hands the level's device time to the choice rule (auto_rule_next,
+// plan.h) for the next level's method.
 __device__ __forceinline__ void level_done(const LevelArgs& A, bool pcg, unsigned long long t0) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   if (A.stat) A.stat->method = pcg ? 1 : 0;
   KrylovAuto* k = A.kauto;
   if (!k) return;
-  const int me = pcg ? 1 : 0, ot = 1 - me;
+  const int me = pcg ? 1 : 0;
   double dt = (double)(global_ns() - t0);
   if (A.stat && A.stat->status != TSFDE_OK) dt = INFINITY;
-  k->t[me] = dt;
-  k->at[me] = A.m;
   k->used[me] += 1;
-  int next = me;
-  if (k->at[ot] == 0) {
-    next = ot;
-  } else {
-    const double r = k->t[ot] / dt;
-    if (!(r >= 1.0)) {
-      next = ot;
-    } else {
-      const double interval = fmin(fmax(8.0 * r * r, 8.0), 64.0);
-      if ((double)(A.m + 1 - k->at[ot]) >= interval) next = ot;
-    }
-  }
-  k->choice = next;
+  k->choice = auto_rule_next(k->rule, me, A.m, dt);
   k->for_level = A.m + 1;
 }
 

@@ -137,20 +137,74 @@ struct StepStat {
   int pad;
 };
 
+// Per-level Krylov choice (TSFDE_KRYLOV_AUTO), shared by the grid engine
+// (one state per context) and the batched engine (one per instance).  After
+// each level, the method that solved it records its device time, and the
+// next level runs
+//  - the other method if that has no sample yet, if its latest sample was
+//    faster, or if this level failed (a failed level counts as infinitely
+//    slow);
+//  - else the same method, until a trial of the other is due: 8 r^2 levels
+//    (8..64) after the other's latest sample, r = how many times slower it
+//    was, times 2^k for k (at most 4) trials of it lost in a row.
+// A lost trial sends the march back at once; a trial that wins clears its
+// method's loss count and the march stays with it.
+struct AutoRule {
+  double t[2];      // device time (ns) of the latest level of each method
+  long long at[2];  // level of that sample (0: none yet)
+  int loss[2];      // trials of each method lost in a row
+  int trial;        // method run as a trial at the current level, -1 none
+  int pad;
+};
+
+__host__ __device__ inline void auto_rule_init(AutoRule& k) {
+  k.t[0] = k.t[1] = 0.0;
+  k.at[0] = k.at[1] = 0;
+  k.loss[0] = k.loss[1] = 0;
+  k.trial = -1;
+  k.pad = 0;
+}
+
+// Records level m solved by method `me` (0 BiCGSTAB, 1 PCG) in dt ns
+// (anything not below 1e300 for a failed level); returns the method of
+// level m + 1.
+__host__ __device__ inline int auto_rule_next(AutoRule& k, int me, long long m, double dt) {
+  const int ot = 1 - me;
+  const bool was_trial = k.trial == me;
+  k.trial = -1;
+  k.t[me] = dt;
+  k.at[me] = m;
+  if (k.at[ot] == 0) {
+    k.trial = ot;
+    return ot;
+  }
+  if (!(dt < 1e300) || !(k.t[ot] >= dt)) {
+    if (was_trial) k.loss[me] += 1;
+    return ot;
+  }
+  if (was_trial) k.loss[me] = 0;
+  const double r = k.t[ot] / dt;
+  double interval = 8.0 * r * r;
+  interval = interval < 8.0 ? 8.0 : (interval > 64.0 ? 64.0 : interval);
+  interval *= (double)(1 << (k.loss[ot] < 4 ? k.loss[ot] : 4));
+  if ((double)(m + 1 - k.at[ot]) >= interval) {
+    k.trial = ot;
+    return ot;
+  }
+  return me;
+}
+
 // Per-level choice of the Krylov method (TSFDE_KRYLOV_AUTO).  Every level
 // launches the BiCGSTAB and the PCG kernel; the one whose method is `choice`
 // for level `for_level` solves it, the other returns at once.  Block 0 of
 // the solving kernel then records the level's device time (globaltimer) for
-// its method and picks the method of the next level: the cheaper one by the
-// latest samples, or the other one as a probe once its sample is older than
-// an interval that grows with the ratio it lost by (8 r^2 levels, 8..64).
+// its method and picks the method of the next level by auto_rule_next.
 // Cleared by the host at every reset (choice BiCGSTAB for level 1).
 struct KrylovAuto {
   long long for_level;  // level the choice applies to
   int choice;           // 0 BiCGSTAB, 1 PCG
   int pad;
-  double t[2];          // device time (ns) of the latest level of each method
-  long long at[2];      // level of that sample (0: none yet)
+  AutoRule rule;
   long long used[2];    // levels solved by each method since the reset
 };
 
