@@ -7,8 +7,9 @@ FP32 inner solver) vs the plain FP64 path.
 
 One step = one time level of the scheme: SOE history update and
 right-hand side, Strang preconditioner for the level, Krylov solve (from
-u^{m-1}, stopping at ||r|| < 1e-12 ||b||; --cold-start: from x0 = 0, the
-paper's setting, with the same stopping rule).  A `batched` object adds the
+the quadratic extrapolation 3 u^{m-1} - 3 u^{m-2} + u^{m-3}, stopping at
+||r|| < 1e-12 ||b||; --start prev: from u^{m-1}; --cold-start: from x0 = 0,
+the paper's setting, with the same stopping rule).  A `batched` object adds the
 512-problem workload (first 128 of its 1024 levels), an `adjoint` object the
 gradient sweep of the adjoint workload (n = 4095, M = 1024).
 Steps are timed one by one with CUDA events on the solver's stream; L2 is
@@ -52,9 +53,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=2047)
+    ap.add_argument("--start", choices=["extrapolate", "prev", "zero"], default="extrapolate",
+                    help="initial guess of each level solve: quadratic extrapolation in the level "
+                         "index (default), u^{m-1}, or 0; same stopping rule ||r|| < tol ||b||")
     ap.add_argument("--cold-start", action="store_true",
-                    help="x0 = 0 for every level as in the paper's experiments (default: start "
-                         "from u^{m-1}, same stopping rule ||r|| < tol ||b||)")
+                    help="x0 = 0 for every level as in the paper's experiments (= --start zero)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
     ap.add_argument("--no-mid", action="store_true", help="skip the mid workload (n = 2^14 - 1, six pairs)")
     ap.add_argument("--dids-levels", type=int, default=None,
@@ -478,10 +481,12 @@ def mid_sample(torch, pkg, ti, stream, warm):
     each a whole march timed with CUDA events on the solver's stream (no L2
     flush: the SOE history, ~2 MB x E, exceeds L2), for the default path
     (double-single mixed solve, per-level Krylov choice), FP64 with the
-    same choice, and the paper's FP64 BiCGSTAB (x0 = 0)."""
+    same choice, both from the same start, and the paper's FP64 BiCGSTAB,
+    started from u^{m-1} as in the headline comparison (x0 = 0 when the
+    others start from 0)."""
     arms = {"mixed": dict(precision="mixed_ds", krylov="auto", warm_start=warm),
             "fp64": dict(precision="fp64", krylov="auto", warm_start=warm),
-            "paper_bicgstab": dict(precision="fp64", krylov="bicgstab", warm_start=False)}
+            "paper_bicgstab": dict(precision="fp64", krylov="bicgstab", warm_start=warm is not False)}
     rows = []
     tot = {k: [0.0, 0, 0] for k in arms}
     for g, a in MID_PAIRS:
@@ -559,6 +564,10 @@ def ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    # initial guess of every level solve (the stopping rule is the same)
+    start = "zero" if args.cold_start else args.start
+    warm = {"extrapolate": "extrapolate", "prev": True, "zero": False}[start]
+
     # ---- mixed arm: the reported value
     clocks = ClockSampler(torch.cuda.current_device())
     barrier()
@@ -567,7 +576,7 @@ def ours(args):
     prec_mx = "mixed_ds" if ds else "mixed"
     kry = args.krylov
     s_mx, ms_mx, tim_mx, st_mx = run_arm(torch, pkg, prob, prec_mx, W, K, flush, stream,
-                                         warm=(not args.cold_start), krylov=kry)
+                                         warm=warm, krylov=kry)
     barrier()
     clk = clocks.stop()
     t_mx = max_over_ranks([sum(ms_mx) / 1e3], "cuda")[0]
@@ -578,7 +587,7 @@ def ours(args):
     fp64 = None
     if not args.no_fp64:
         s64, ms64, tim64, st64 = run_arm(torch, pkg, prob, "fp64", W, K, flush, stream,
-                                         warm=(not args.cold_start), krylov=kry)
+                                         warm=warm, krylov=kry)
         u64 = current_u(torch, s64)
         rel = float(torch.max(torch.abs(u_mx - u64)) / torch.max(torch.abs(u64)))
         t64 = sum(ms64) / 1e3
@@ -592,9 +601,10 @@ def ours(args):
                 "krylov": kry}
         s64.close()
         if kry != "bicgstab":
-            # the paper's solver, FP64 right-preconditioned BiCGSTAB, on the same levels
+            # the paper's solver, FP64 right-preconditioned BiCGSTAB, on the same
+            # levels, started from u^{m-1} (x0 = 0 with --cold-start)
             sb, msb, timb, stb = run_arm(torch, pkg, prob, "fp64", W, K, flush, stream,
-                                         warm=(not args.cold_start), krylov="bicgstab")
+                                         warm=(start != "zero"), krylov="bicgstab")
             ub = current_u(torch, sb)
             tb = sum(msb) / 1e3
             fp64["paper_bicgstab"] = {
@@ -609,7 +619,7 @@ def ours(args):
     e2e = None
     if not args.no_e2e:
         se, ms_e2e, _, _ = run_arm(torch, pkg, prob, prec_mx, W, K, flush, stream, e2e=True,
-                                    warm=(not args.cold_start), krylov=kry)
+                                    warm=warm, krylov=kry)
         se.close()
         e2e = {"value": world * K / (sum(ms_e2e) / 1e3), "unit": "steps/s",
                "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n,
@@ -650,7 +660,7 @@ def ours(args):
     batched = None
     if args.batched_levels > 0:
         batched = batched_sample(torch, pkg, ti, args.batched_levels, rank, world, stream,
-                                 warm=not args.cold_start, full=not args.no_batched_full)
+                                 warm=(start != "zero"), full=not args.no_batched_full)
         if world > 1:
             keys = [k for k in ("mixed", "fp64", "mixed_full_M") if k in batched]
             tm = max_over_ranks([batched[k]["s"] for k in keys], "cuda")
@@ -662,7 +672,7 @@ def ours(args):
     dl = prob.M if args.dids_levels is None else min(args.dids_levels, prob.M)
     if rank == 0 and dl > 0:
         u_f = u_mx if s_mx.m == prob.M else None
-        dids = dids_sample(torch, pkg, prob, stream, dl, not args.cold_start, u_f, kry)
+        dids = dids_sample(torch, pkg, prob, stream, dl, warm, u_f, kry)
 
     adjoint = None
     if rank == 0 and not args.no_adjoint:
@@ -670,7 +680,7 @@ def ours(args):
 
     mid = None
     if rank == 0 and not args.no_mid:
-        mid = mid_sample(torch, pkg, ti, stream, not args.cold_start)
+        mid = mid_sample(torch, pkg, ti, stream, warm)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -690,7 +700,8 @@ def ours(args):
                                     + ", FP64 refinement/residual/SOE",
                        "krylov": kry,
                        "krylov_tol": 1e-12, "inner_tol": 1e-2,
-                       "initial_guess": "u^{m-1}" if (not args.cold_start) else "0 (Sec. 5)",
+                       "initial_guess": {"extrapolate": "3u^{m-1} - 3u^{m-2} + u^{m-3} (quadratic in the level index)",
+                                         "prev": "u^{m-1}", "zero": "0 (Sec. 5)"}[start],
                        "l2": f"flushed before every timed level ({args.flush_mb} MB write, then {args.flush_mb} MB read, outside the events)",
                        "parallelism": f"replicas x{world}"},
             "status": st_mx["status"],

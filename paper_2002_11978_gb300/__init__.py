@@ -222,7 +222,7 @@ class Solver:
         o.krylov = {"bicgstab": TSFDE_KRYLOV_BICGSTAB, "pcg": TSFDE_KRYLOV_PCG,
                     "auto": TSFDE_KRYLOV_AUTO}[krylov]
         o.history = {"soe": TSFDE_HISTORY_SOE, "direct": TSFDE_HISTORY_DIRECT}[history]
-        o.warm_start = 1 if warm_start else 0
+        o.warm_start = _warm(warm_start)
         o.ckpt_stride = int(ckpt_stride)
         o.engine = {"auto": TSFDE_ENGINE_AUTO, "grid": TSFDE_ENGINE_GRID,
                     "cluster": TSFDE_ENGINE_CLUSTER}[engine]
@@ -465,7 +465,7 @@ def _batch_args(instances, precision="mixed", precond="strang", krylov_tol=1e-12
     o = default_opts()
     o.krylov = {"bicgstab": TSFDE_KRYLOV_BICGSTAB, "pcg": TSFDE_KRYLOV_PCG, "auto": TSFDE_KRYLOV_AUTO}[krylov]
     o.cluster_size = cluster_size
-    o.warm_start = 1 if warm_start else 0
+    o.warm_start = _warm(warm_start)
     o.krylov_tol = krylov_tol
     o.max_it = max_it
     o.precision = {"fp64": TSFDE_FP64, "mixed": TSFDE_MIXED}[precision]
@@ -533,6 +533,15 @@ def probe_l2_read(buf, reps, stream=None):
         raise ValueError("buf must be a contiguous CUDA tensor")
     _check(lib.tsfde_probe_l2_read(ctypes.c_void_p(buf.data_ptr()), nbytes, int(reps),
                                    _stream_handle(stream)))
+
+
+def _warm(w):
+    """warm_start option: False/0 (x0 = 0), True/1 (u^{m-1}) or
+    "extrapolate"/2 (quadratic extrapolation in the level index from
+    u^{m-3}, u^{m-2}, u^{m-1})."""
+    if w in ("extrapolate", 2):
+        return 2
+    return 1 if w else 0
 
 
 def _prec(p):

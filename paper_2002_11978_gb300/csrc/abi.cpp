@@ -60,7 +60,7 @@ struct tsfde_ctx {
   // ld doubles; G^k = the E x ld history after level k's right-hand side),
   // everything needed to march on from level k
   int64_t ck_stride = 0, ck_slots = 0;
-  size_t ck_slot = 0;               // doubles per slot, (2 + E) ld
+  size_t ck_slot = 0;               // doubles per slot, (3 + E) ld
   double* ck = nullptr;
   double* ck_seg = nullptr;         // ck_stride recomputed levels, rows of n
   double* ck_save = nullptr;        // forward state kept across a sweep: u[3], G
@@ -68,6 +68,7 @@ struct tsfde_ctx {
   std::vector<char> ck_ok;          // slot recorded in the current march
   bool ck_override = false;         // a level took per-level kappa_m / f_m
   bool ck_recomputing = false;
+  std::vector<int> ck_kry;          // Krylov method of each level, replayed when recomputing
   // adjoint work buffers (allocated by the first tsfde_adjoint)
   double* adjY = nullptr;       // E x ld reversed SOE history
   double* adjLam[2] = {nullptr, nullptr};
@@ -114,16 +115,19 @@ double* ulev(tsfde_ctx* c, int64_t m) {
   return c->Uh ? c->Uh + (size_t)m * c->ld : c->u[m % 3];
 }
 
-// Checkpoint of level k (a multiple of ck_stride): u^{k-1}, u^k and the SOE
+// Checkpoint of level k (a multiple of ck_stride): u^{k-2}, u^{k-1}, u^k
+// (the levels an extrapolated start of level k + 1 reads) and the SOE
 // history after level k's right-hand side, copied on the context's stream.
 cudaError_t record_ckpt(tsfde_ctx* c, int64_t k) {
   const int64_t j = k / c->ck_stride;
   double* slot = c->ck + c->ck_slot * (size_t)j;
   const size_t nb = sizeof(double) * (size_t)c->n;
-  cudaError_t e = cudaMemcpyAsync(slot, ulev(c, k >= 1 ? k - 1 : 0), nb, cudaMemcpyDeviceToDevice, c->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(slot + c->ld, ulev(c, k), nb, cudaMemcpyDeviceToDevice, c->stream);
+  cudaError_t e = cudaSuccess;
+  for (int q = 0; q < 3 && e == cudaSuccess; ++q)  // u^{k-2}, u^{k-1}, u^k (those that exist)
+    if (k - 2 + q >= 0)
+      e = cudaMemcpyAsync(slot + q * (size_t)c->ld, ulev(c, k - 2 + q), nb, cudaMemcpyDeviceToDevice, c->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(slot + 2 * (size_t)c->ld, c->G, sizeof(double) * (size_t)std::max(c->E, 1) * c->ld,
+    e = cudaMemcpyAsync(slot + 3 * (size_t)c->ld, c->G, sizeof(double) * (size_t)std::max(c->E, 1) * c->ld,
                         cudaMemcpyDeviceToDevice, c->stream);
   if (e == cudaSuccess) c->ck_ok[j] = 1;
   return e;
@@ -134,10 +138,11 @@ cudaError_t restore_ckpt(tsfde_ctx* c, int64_t k) {
   const double* slot = c->ck + c->ck_slot * (size_t)(k / c->ck_stride);
   const size_t nb = sizeof(double) * (size_t)c->n;
   cudaError_t e = cudaSuccess;
-  if (k >= 1) e = cudaMemcpyAsync(ulev(c, k - 1), slot, nb, cudaMemcpyDeviceToDevice, c->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(ulev(c, k), slot + c->ld, nb, cudaMemcpyDeviceToDevice, c->stream);
+  for (int q = 0; q < 3 && e == cudaSuccess; ++q)
+    if (k - 2 + q >= 0)
+      e = cudaMemcpyAsync(ulev(c, k - 2 + q), slot + q * (size_t)c->ld, nb, cudaMemcpyDeviceToDevice, c->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->G, slot + 2 * (size_t)c->ld, sizeof(double) * (size_t)std::max(c->E, 1) * c->ld,
+    e = cudaMemcpyAsync(c->G, slot + 3 * (size_t)c->ld, sizeof(double) * (size_t)std::max(c->E, 1) * c->ld,
                         cudaMemcpyDeviceToDevice, c->stream);
   c->m = k;
   return e;
@@ -285,6 +290,7 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
     return fail(c, TSFDE_EINVAL, "history must be TSFDE_HISTORY_SOE or TSFDE_HISTORY_DIRECT");
   if (o.krylov != TSFDE_KRYLOV_BICGSTAB && o.krylov != TSFDE_KRYLOV_PCG && o.krylov != TSFDE_KRYLOV_AUTO)
     return fail(c, TSFDE_EINVAL, "krylov must be TSFDE_KRYLOV_BICGSTAB, _PCG or _AUTO");
+  if (o.warm_start < 0 || o.warm_start > 2) return fail(c, TSFDE_EINVAL, "warm_start must be 0, 1 or 2");
   if (o.ckpt_stride < -1) return fail(c, TSFDE_EINVAL, "ckpt_stride must be -1 (sqrt M), 0 (off) or positive");
   if (o.ckpt_stride != 0 && o.history != TSFDE_HISTORY_SOE)
     return fail(c, TSFDE_EINVAL, "checkpoints serve the FIDS adjoint (history = SOE)");
@@ -486,7 +492,7 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
     S = std::min<int64_t>(S, M);
     c->ck_stride = S;
     c->ck_slots = M / S + 1;
-    c->ck_slot = (size_t)(2 + std::max(E, 1)) * ld;
+    c->ck_slot = (size_t)(3 + std::max(E, 1)) * ld;
     c->ck_ok.assign(c->ck_slots, 0);
     ok &= dalloc(c, &c->ck, c->ck_slot * c->ck_slots) && dalloc(c, &c->ck_seg, (size_t)S * n) &&
           dalloc(c, &c->ck_save, (size_t)(3 + std::max(E, 1)) * ld);
@@ -752,10 +758,26 @@ static int enqueue_level(tsfde_ctx* c, const double* kappa_m, const double* f_m,
   if (e != cudaSuccess) return cuda_fail(c, e, "rhs kernel");
   LevelArgs A = level_args(c, c->ahat[m], c->b, ulev(c, m), c->stats + m);
   A.u_prev = c->opts.warm_start ? ulev(c, m - 1) : nullptr;
+  if (c->opts.warm_start == 2 && m >= 2) {
+    // extrapolation in the level index: quadratic through u^{m-3}, u^{m-2},
+    // u^{m-1} (x0 = 3 u^{m-1} - 3 u^{m-2} + u^{m-3}), linear at level 2.
+    // For the SOE history u^{m-3} shares its buffer with u^m.
+    A.u_prev2 = ulev(c, m - 2);
+    A.e1 = 1.0;
+    if (m >= 3) {
+      A.u_prev3 = ulev(c, m - 3);
+      A.e2 = 1.0;
+    }
+  }
   A.prev = (m >= 2) ? c->stats + (m - 1) : nullptr;
   A.retry_mixed = (m % 64 == 0) ? 1 : 0;
   A.kauto = c->kauto;
   A.m = m;
+  if (c->ck_recomputing && c->kauto) {
+    // a recomputed level takes the method the forward march took there
+    A.kauto = nullptr;
+    A.krylov = c->ck_kry[m];
+  }
   e = launch_level_ctx(c, A);
   if (e == cudaSuccess) e = record(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "level kernel");
@@ -1057,6 +1079,7 @@ int tsfde_adjoint(tsfde_ctx* c, const double* u_all, const double* dJ, double* g
     // in reverse.  The forward state is kept aside and brought back.
     const int64_t S = c->ck_stride;
     if ((e = keep_forward_state(c, true)) != cudaSuccess) return cuda_fail(c, e, "checkpoint copy");
+    c->ck_kry = kry;
     c->ck_recomputing = true;
     for (int64_t k0 = ((M - 1) / S) * S; k0 >= 0 && st0 == TSFDE_OK; k0 -= S) {
       const int64_t k1 = std::min(k0 + S, M);

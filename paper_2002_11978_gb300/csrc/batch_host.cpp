@@ -275,6 +275,7 @@ int tsfde_batch_setup_plan(tsfde_batch** out, int B, const tsfde_instance* inst,
   if (o.history == TSFDE_HISTORY_DIRECT) return TSFDE_ENOTSUP;  // FIDS only
   if (o.krylov != TSFDE_KRYLOV_BICGSTAB && o.krylov != TSFDE_KRYLOV_PCG && o.krylov != TSFDE_KRYLOV_AUTO)
     return TSFDE_EINVAL;
+  if (o.warm_start < 0 || o.warm_start > 2) return TSFDE_EINVAL;
   if (o.history != TSFDE_HISTORY_SOE) return TSFDE_EINVAL;
   if (o.precond != TSFDE_STRANG && o.precond != TSFDE_PRECOND_NONE) return TSFDE_EINVAL;
   if (!(o.krylov_tol > 0.0) || o.max_it < 1) return TSFDE_EINVAL;

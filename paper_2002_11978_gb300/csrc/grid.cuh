@@ -874,13 +874,22 @@ static __device__ void write_stat(StepStat* st, int status, int iters, int outer
 }
 
 
-// Warm start of a level solve: u = u_prev and r64 = b - (ahat I + K A) u_prev
-// (one FP64 product); returns b.b and r.r (grid-wide, in every CTA).
+// Warm start of a level solve: u = x0 and r64 = b - (ahat I + K A) x0, with
+// x0 = u_prev, or the extrapolation from u_prev, u_prev2 (and u_prev3) that
+// LevelArgs describes (one FP64 product); returns b.b and r.r (grid-wide, in
+// every CTA).
 template <int KP = kPre>
 __device__ bool warm_residual(const LevelArgs& A, SmemAll& S, double& bb, double& rr) {
   const DevPlan& P = A.P;
   auto pro = [&](int i) -> double {
-    const double x = A.u_prev[i];
+    double x = A.u_prev[i];
+    if (A.u_prev2) {
+      const double u2 = A.u_prev2[i];
+      const double d1 = x - u2;
+      double dx = A.e1 * d1;
+      if (A.e2 != 0.0) dx = fma(A.e2, d1 - (u2 - A.u_prev3[i]), dx);
+      x += dx;
+    }
     A.u[i] = x;
     return x;
   };
@@ -891,7 +900,7 @@ __device__ bool warm_residual(const LevelArgs& A, SmemAll& S, double& bb, double
   double bacc = 0.0, racc = 0.0;
   auto epi = [&](int i, double y) -> double {
     const double bi = A.b[i];
-    const double ri = bi - (A.ahat * A.u_prev[i] + A.kappa64[i] * y);
+    const double ri = bi - (A.ahat * A.u[i] + A.kappa64[i] * y);
     A.r64[i] = ri;
     bacc += bi * bi;
     racc += ri * ri;

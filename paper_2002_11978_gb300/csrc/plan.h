@@ -238,6 +238,13 @@ struct LevelArgs {
   StepStat* stat;
   int probe;          // cluster engine: return at once (launch check)
   const double* u_prev;   // warm start from u^{m-1} (NULL: x0 = 0)
+  // with u_prev, an extrapolated start (u_prev2 NULL: x0 = u^{m-1}):
+  // x0 = u^{m-1} + e1 d1 + e2 (d1 - d2), d1 = u^{m-1} - u^{m-2},
+  // d2 = u^{m-2} - u^{m-3} (u_prev3 is read only when e2 != 0; it may be
+  // the array u itself, each entry read before it is overwritten)
+  const double* u_prev2;
+  const double* u_prev3;
+  double e1, e2;
   const StepStat* prev;   // mixed: the previous level's stats (NULL: none)
   int retry_mixed;        // mixed: refine even after a level finished in FP64
   KrylovAuto* kauto;      // TSFDE_KRYLOV_AUTO: method choice state (NULL: fixed method)

@@ -141,6 +141,25 @@ def test_setup_validates_krylov(lib):
     assert not ctx
 
 
+def test_setup_validates_warm_start(lib):
+    """warm_start takes 0 (x0 = 0), 1 (u^{m-1}) or 2 (extrapolated); other
+    values are refused before any device work, single and batched."""
+    import paper_2002_11978_gb300 as pkg
+    ctx = ctypes.c_void_p()
+    for w in (-1, 3):
+        o = pkg.default_opts()
+        o.warm_start = w
+        assert lib.tsfde_setup(ctypes.byref(ctx), 1.5, 0.5, 1.0, 1.0, 7, 4, 3.0, 1e-12,
+                               ctypes.byref(o)) == pkg.TSFDE_EINVAL
+        inst = (pkg.tsfde_instance * 1)()
+        inst[0] = pkg.tsfde_instance(1.5, 0.5, 1.0, 1.0, 3.0, 63, 1e-12, None, None, None)
+        b = ctypes.c_void_p()
+        assert lib.tsfde_batch_setup(ctypes.byref(b), 1, inst, 8, ctypes.byref(o)) == pkg.TSFDE_EINVAL
+        assert not b
+    assert not ctx
+    assert pkg._warm("extrapolate") == 2 and pkg._warm(True) == 1 and pkg._warm(False) == 0
+
+
 def test_batch_krylov_option(lib):
     """The batched solve accepts BiCGSTAB, PCG and AUTO, and rejects other
     values; an instance with NULL data pointers is rejected before any

@@ -73,16 +73,20 @@ def test_adjoint_matches_dense_oracle(torch, n, M, krylov):
     assert ek < 1e-10 and ef < 1e-10, (ek, ef, info)
 
 
-@pytest.mark.parametrize("stride", [6, -1, 1, 32])
-def test_checkpointed_adjoint_equals_trajectory_adjoint(torch, stride):
+@pytest.mark.parametrize("stride,kw", [(6, {}), (-1, {}), (1, {}), (32, {}),
+                                       (6, dict(warm_start="extrapolate", krylov="auto")),
+                                       (1, dict(warm_start="extrapolate", krylov="auto"))])
+def test_checkpointed_adjoint_equals_trajectory_adjoint(torch, stride, kw):
     """u_all = NULL: the sweep marches each segment between checkpoints again
     (stride 6 leaves a ragged last segment of 2 levels at M = 32; -1 is
     ceil(sqrt(M)) = 6; 1 and M are the extremes).  The recomputed levels run
-    the same deterministic kernels from the same state, so the gradients
-    equal those of the sweep over the stored trajectory, and the forward
-    state is left where it was."""
+    the same deterministic kernels from the same state (with an extrapolated
+    start, the checkpoint's three levels feed it; with the per-level Krylov
+    choice, the method the forward march recorded for the level), so the
+    gradients equal those of the sweep over the stored trajectory, and the
+    forward state is left where it was."""
     n, M = 255, 32
-    _, prob, kobs, s = _setup(torch, n, M, ckpt_stride=stride)
+    _, prob, kobs, s = _setup(torch, n, M, ckpt_stride=stride, **kw)
     f0 = prob.F[0]
     u_obs = _forward(torch, s, prob, kobs, f0)[M].clone()
     U = _forward(torch, s, prob, prob.kappa0, f0)

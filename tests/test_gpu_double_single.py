@@ -147,7 +147,7 @@ def _march(torch, prob, precision, soe, **kw):
     return U.cpu().numpy(), info
 
 
-@pytest.mark.parametrize("warm", [False, True])
+@pytest.mark.parametrize("warm", [False, True, "extrapolate"])
 def test_smallest_config_march_matches_oracle(torch, warm):
     """n = 127, M = 64 with the oracle's SOE table: every level within 1e-10
     of the oracle's FIDS march (direct history sums, dense LU)."""

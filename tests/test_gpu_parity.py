@@ -281,25 +281,28 @@ def test_paper_tables_on_gpu(torch, row):
         assert abs(its / M - float(row[11])) <= 1.0, (its / M, row[11])
 
 
+@pytest.mark.parametrize("warm", [True, "extrapolate"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_warm_start_march_matches_oracle(torch, precision):
-    """Levels started from u^{m-1} (stopping at ||r|| < tol ||b||) reach the
-    same solutions as the oracle's dense-LU march."""
+def test_warm_start_march_matches_oracle(torch, precision, warm):
+    """Levels started from u^{m-1}, or from the extrapolation 3 u^{m-1} -
+    3 u^{m-2} + u^{m-3} (stopping at ||r|| < tol ||b||), reach the same
+    solutions as the oracle's dense-LU march."""
     prob = ti.config_smallest()
     tm, tau = oracle.graded_mesh(prob.T, prob.M, prob.r)
     soe = oracle.soe_build(prob.gamma, tau[1], prob.T, prob.soe_tol)
-    _, U, info = _gpu_solve(torch, prob, precision, soe=soe, warm_start=True)
+    _, U, info = _gpu_solve(torch, prob, precision, soe=soe, warm_start=warm)
     ref = _oracle_fids(prob, soe)
     assert np.max(np.abs(U - ref)) / np.max(np.abs(ref)) < 1e-10, info
 
 
 def test_warm_start_large_levels_agree(torch):
-    """n = 16383: 24 levels with and without warm start, FP64 and mixed."""
+    """n = 16383: 24 levels with and without warm start (u^{m-1} or the
+    extrapolated start), FP64 and mixed."""
     import paper_2002_11978_gb300 as pkg
     prob = ti.config_mid(0.3, 1.8, n=16383, M=64)
     out = {}
     for prec in ("fp64", "mixed"):
-        for warm in (False, True):
+        for warm in (False, True, "extrapolate"):
             s = pkg.Solver(prob.alpha, prob.gamma, prob.l, prob.T, prob.n, prob.M, prob.r, prob.soe_tol,
                            precision=prec, warm_start=warm)
             s.set_problem_from(prob)
