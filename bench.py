@@ -7,7 +7,7 @@ FP32 inner solver) vs the plain FP64 path.
 
 One step = one time level of the scheme: SOE history update and
 right-hand side, Strang preconditioner for the level, Krylov solve (from
-the quadratic extrapolation 3 u^{m-1} - 3 u^{m-2} + u^{m-3}, stopping at
+the cubic extrapolation 4 u^{m-1} - 6 u^{m-2} + 4 u^{m-3} - u^{m-4}, stopping at
 ||r|| < 1e-12 ||b||; --start prev: from u^{m-1}; --cold-start: from x0 = 0,
 the paper's setting, with the same stopping rule).  A `batched` object adds the
 512-problem workload (first 128 of its 1024 levels), an `adjoint` object the
@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=2047)
     ap.add_argument("--start", choices=["extrapolate", "prev", "zero"], default="extrapolate",
-                    help="initial guess of each level solve: quadratic extrapolation in the level "
+                    help="initial guess of each level solve: cubic extrapolation in the level "
                          "index (default), u^{m-1}, or 0; same stopping rule ||r|| < tol ||b||")
     ap.add_argument("--cold-start", action="store_true",
                     help="x0 = 0 for every level as in the paper's experiments (= --start zero)")
@@ -700,7 +700,7 @@ def ours(args):
                                     + ", FP64 refinement/residual/SOE",
                        "krylov": kry,
                        "krylov_tol": 1e-12, "inner_tol": 1e-2,
-                       "initial_guess": {"extrapolate": "3u^{m-1} - 3u^{m-2} + u^{m-3} (quadratic in the level index)",
+                       "initial_guess": {"extrapolate": "4u^{m-1} - 6u^{m-2} + 4u^{m-3} - u^{m-4} (cubic in the level index)",
                                          "prev": "u^{m-1}", "zero": "0 (Sec. 5)"}[start],
                        "l2": f"flushed before every timed level ({args.flush_mb} MB write, then {args.flush_mb} MB read, outside the events)",
                        "parallelism": f"replicas x{world}"},

@@ -158,9 +158,9 @@ typedef struct tsfde_opts {
   int warm_start;       /* 1: start every level's solve from u^{m-1} and stop
                            at ||r|| < krylov_tol ||b^m|| (mixed: same
                            refinement rules); 2: the same stopping rule from
-                           the quadratic extrapolation in the level index,
-                           x0 = 3 u^{m-1} - 3 u^{m-2} + u^{m-3} (linear at
-                           level 2, u^{m-1} at level 1; the batched solve
+                           the cubic extrapolation in the level index,
+                           x0 = 4 u^{m-1} - 6 u^{m-2} + 4 u^{m-3} - u^{m-4}
+                           (lower orders at levels 1-3; the batched solve
                            takes 2 as 1); 0 (default): x0 = 0 and the
                            residual relative to ||r_0|| = ||b^m|| (Sec. 5);
                            other values: TSFDE_EINVAL                       */
@@ -172,11 +172,11 @@ typedef struct tsfde_opts {
                            chooses per level within each instance's march */
   int ckpt_stride;      /* adjoint checkpoints: every ckpt_stride-th level of
                            the forward march (level 0 at each reset) keeps
-                           u^{k-2}, u^{k-1}, u^k and the SOE history, so
-                           that tsfde_adjoint can run with u_all = NULL by
+                           u^{k-3} .. u^k and the SOE history, so that
+                           tsfde_adjoint can run with u_all = NULL by
                            marching each segment again from its checkpoint.
                            -1: ceil(sqrt(M)); 0 (default): none.  Device
-                           memory (M/stride + 1) (E + 3) n + stride n
+                           memory (M/stride + 1) (E + 4) n + stride n
                            doubles; SOE history only                        */
 } tsfde_opts;
 

@@ -537,8 +537,8 @@ def probe_l2_read(buf, reps, stream=None):
 
 def _warm(w):
     """warm_start option: False/0 (x0 = 0), True/1 (u^{m-1}) or
-    "extrapolate"/2 (quadratic extrapolation in the level index from
-    u^{m-3}, u^{m-2}, u^{m-1})."""
+    "extrapolate"/2 (cubic extrapolation in the level index from
+    u^{m-4} .. u^{m-1})."""
     if w in ("extrapolate", 2):
         return 2
     return 1 if w else 0

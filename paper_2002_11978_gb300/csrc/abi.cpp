@@ -16,6 +16,15 @@
 
 using namespace tsfde;
 
+// Order of the extrapolated start (warm_start = 2): the level solve starts
+// from the polynomial in the level index through the last kStartOrder + 1
+// levels.  The SOE-history context rotates kRoll = kStartOrder + 1 level
+// buffers (at least 3: the right-hand side reads u^{m-1} and u^{m-2} while
+// u^m is written).
+constexpr int kStartOrder = 3;
+constexpr int kRoll = kStartOrder + 1 > 3 ? kStartOrder + 1 : 3;
+static_assert(kStartOrder <= kMaxStartOrder, "LevelArgs.up holds kMaxStartOrder + 1 levels");
+
 struct tsfde_ctx {
   double alpha = 0, gamma = 0, l = 0, T = 0, r = 0, soe_tol = 0, mu = 0;
   int kappa_mu = 1;
@@ -34,7 +43,7 @@ struct tsfde_ctx {
   DevPlan P{};
   std::vector<void*> allocs;
   double *G = nullptr, *eps = nullptr, *cw = nullptr;
-  double* u[3] = {nullptr, nullptr, nullptr};
+  double* u[kRoll] = {};  // rotating levels u^m, u^{m-1}, ... (SOE history)
   double *b = nullptr, *kappa64 = nullptr, *phi = nullptr, *kap0 = nullptr, *kap1d = nullptr;
   double* F = nullptr;
   float* kappa32 = nullptr;
@@ -60,10 +69,10 @@ struct tsfde_ctx {
   // ld doubles; G^k = the E x ld history after level k's right-hand side),
   // everything needed to march on from level k
   int64_t ck_stride = 0, ck_slots = 0;
-  size_t ck_slot = 0;               // doubles per slot, (3 + E) ld
+  size_t ck_slot = 0;               // doubles per slot, (kRoll + E) ld
   double* ck = nullptr;
   double* ck_seg = nullptr;         // ck_stride recomputed levels, rows of n
-  double* ck_save = nullptr;        // forward state kept across a sweep: u[3], G
+  double* ck_save = nullptr;        // forward state kept across a sweep: u[kRoll], G
   KrylovAuto* ck_kauto = nullptr;   // ... and the method-choice state
   std::vector<char> ck_ok;          // slot recorded in the current march
   bool ck_override = false;         // a level took per-level kappa_m / f_m
@@ -112,10 +121,10 @@ template <typename T> cudaError_t upload(T* dst, const std::vector<T>& src) {
 // Device vector of level m: a row of the stored levels with the direct
 // history, else one of three rotating buffers.
 double* ulev(tsfde_ctx* c, int64_t m) {
-  return c->Uh ? c->Uh + (size_t)m * c->ld : c->u[m % 3];
+  return c->Uh ? c->Uh + (size_t)m * c->ld : c->u[m % kRoll];
 }
 
-// Checkpoint of level k (a multiple of ck_stride): u^{k-2}, u^{k-1}, u^k
+// Checkpoint of level k (a multiple of ck_stride): u^{k-kStartOrder} .. u^k
 // (the levels an extrapolated start of level k + 1 reads) and the SOE
 // history after level k's right-hand side, copied on the context's stream.
 cudaError_t record_ckpt(tsfde_ctx* c, int64_t k) {
@@ -123,11 +132,12 @@ cudaError_t record_ckpt(tsfde_ctx* c, int64_t k) {
   double* slot = c->ck + c->ck_slot * (size_t)j;
   const size_t nb = sizeof(double) * (size_t)c->n;
   cudaError_t e = cudaSuccess;
-  for (int q = 0; q < 3 && e == cudaSuccess; ++q)  // u^{k-2}, u^{k-1}, u^k (those that exist)
-    if (k - 2 + q >= 0)
-      e = cudaMemcpyAsync(slot + q * (size_t)c->ld, ulev(c, k - 2 + q), nb, cudaMemcpyDeviceToDevice, c->stream);
+  for (int q = 0; q < kRoll && e == cudaSuccess; ++q)  // u^{k-kRoll+1} .. u^k (those that exist)
+    if (k - kRoll + 1 + q >= 0)
+      e = cudaMemcpyAsync(slot + q * (size_t)c->ld, ulev(c, k - kRoll + 1 + q), nb, cudaMemcpyDeviceToDevice,
+                          c->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(slot + 3 * (size_t)c->ld, c->G, sizeof(double) * (size_t)std::max(c->E, 1) * c->ld,
+    e = cudaMemcpyAsync(slot + kRoll * (size_t)c->ld, c->G, sizeof(double) * (size_t)std::max(c->E, 1) * c->ld,
                         cudaMemcpyDeviceToDevice, c->stream);
   if (e == cudaSuccess) c->ck_ok[j] = 1;
   return e;
@@ -138,28 +148,29 @@ cudaError_t restore_ckpt(tsfde_ctx* c, int64_t k) {
   const double* slot = c->ck + c->ck_slot * (size_t)(k / c->ck_stride);
   const size_t nb = sizeof(double) * (size_t)c->n;
   cudaError_t e = cudaSuccess;
-  for (int q = 0; q < 3 && e == cudaSuccess; ++q)
-    if (k - 2 + q >= 0)
-      e = cudaMemcpyAsync(ulev(c, k - 2 + q), slot + q * (size_t)c->ld, nb, cudaMemcpyDeviceToDevice, c->stream);
+  for (int q = 0; q < kRoll && e == cudaSuccess; ++q)
+    if (k - kRoll + 1 + q >= 0)
+      e = cudaMemcpyAsync(ulev(c, k - kRoll + 1 + q), slot + q * (size_t)c->ld, nb, cudaMemcpyDeviceToDevice,
+                          c->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->G, slot + 3 * (size_t)c->ld, sizeof(double) * (size_t)std::max(c->E, 1) * c->ld,
+    e = cudaMemcpyAsync(c->G, slot + kRoll * (size_t)c->ld, sizeof(double) * (size_t)std::max(c->E, 1) * c->ld,
                         cudaMemcpyDeviceToDevice, c->stream);
   c->m = k;
   return e;
 }
 
-// Keep (save = true) or bring back the forward state: the three rotating
-// levels, the SOE history and the method-choice state.
+// Keep (save = true) or bring back the forward state: the rotating levels,
+// the SOE history and the method-choice state.
 cudaError_t keep_forward_state(tsfde_ctx* c, bool save) {
   const size_t nb = sizeof(double) * (size_t)c->n;
   const size_t gb = sizeof(double) * (size_t)std::max(c->E, 1) * c->ld;
   cudaError_t e = cudaSuccess;
-  for (int q = 0; q < 3 && e == cudaSuccess; ++q) {
+  for (int q = 0; q < kRoll && e == cudaSuccess; ++q) {
     double* keep = c->ck_save + (size_t)q * c->ld;
     e = save ? cudaMemcpyAsync(keep, c->u[q], nb, cudaMemcpyDeviceToDevice, c->stream)
              : cudaMemcpyAsync(c->u[q], keep, nb, cudaMemcpyDeviceToDevice, c->stream);
   }
-  double* gkeep = c->ck_save + 3 * (size_t)c->ld;
+  double* gkeep = c->ck_save + kRoll * (size_t)c->ld;
   if (e == cudaSuccess)
     e = save ? cudaMemcpyAsync(gkeep, c->G, gb, cudaMemcpyDeviceToDevice, c->stream)
              : cudaMemcpyAsync(c->G, gkeep, gb, cudaMemcpyDeviceToDevice, c->stream);
@@ -456,7 +467,7 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
   if (use_cluster) ok &= dalloc(c, &dspT, Nc) && dalloc(c, &dspG, Nc);
   ok &= dalloc(c, &c->G, (size_t)std::max(E, 1) * ld);
   ok &= dalloc(c, &c->eps, c->eps_h.size()) && dalloc(c, &c->cw, c->cw_h.size());
-  for (int q = 0; q < 3; ++q) ok &= dalloc(c, &c->u[q], n);
+  for (int q = 0; q < kRoll; ++q) ok &= dalloc(c, &c->u[q], n);
   // FP32 vectors: length ld (even, zero-padded) -- the cluster engine moves
   // entries in aligned pairs
   ok &= dalloc(c, &c->b, n) && dalloc(c, &c->kappa64, n) && dalloc(c, &c->kappa32, ld);
@@ -492,10 +503,10 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
     S = std::min<int64_t>(S, M);
     c->ck_stride = S;
     c->ck_slots = M / S + 1;
-    c->ck_slot = (size_t)(3 + std::max(E, 1)) * ld;
+    c->ck_slot = (size_t)(kRoll + std::max(E, 1)) * ld;
     c->ck_ok.assign(c->ck_slots, 0);
     ok &= dalloc(c, &c->ck, c->ck_slot * c->ck_slots) && dalloc(c, &c->ck_seg, (size_t)S * n) &&
-          dalloc(c, &c->ck_save, (size_t)(3 + std::max(E, 1)) * ld);
+          dalloc(c, &c->ck_save, (size_t)(kRoll + std::max(E, 1)) * ld);
     if (c->kauto) ok &= dalloc(c, &c->ck_kauto, 1);
   }
   // direct history: all levels and the weights of Eq. (4.1),
@@ -758,16 +769,12 @@ static int enqueue_level(tsfde_ctx* c, const double* kappa_m, const double* f_m,
   if (e != cudaSuccess) return cuda_fail(c, e, "rhs kernel");
   LevelArgs A = level_args(c, c->ahat[m], c->b, ulev(c, m), c->stats + m);
   A.u_prev = c->opts.warm_start ? ulev(c, m - 1) : nullptr;
-  if (c->opts.warm_start == 2 && m >= 2) {
-    // extrapolation in the level index: quadratic through u^{m-3}, u^{m-2},
-    // u^{m-1} (x0 = 3 u^{m-1} - 3 u^{m-2} + u^{m-3}), linear at level 2.
-    // For the SOE history u^{m-3} shares its buffer with u^m.
-    A.u_prev2 = ulev(c, m - 2);
-    A.e1 = 1.0;
-    if (m >= 3) {
-      A.u_prev3 = ulev(c, m - 3);
-      A.e2 = 1.0;
-    }
+  if (c->opts.warm_start == 2) {
+    // polynomial extrapolation in the level index through the last
+    // kStartOrder + 1 levels (fewer at the first levels); with the SOE
+    // history the oldest of them shares its buffer with u^m
+    A.xorder = (int)std::min<int64_t>(kStartOrder, m - 1);
+    for (int j = 0; j <= A.xorder; ++j) A.up[j] = ulev(c, m - 1 - j);
   }
   A.prev = (m >= 2) ? c->stats + (m - 1) : nullptr;
   A.retry_mixed = (m % 64 == 0) ? 1 : 0;

@@ -429,7 +429,7 @@ __device__ LevelOut bt_level(BatchCtx* bx, const BatchArgs& A, int m, bool prev_
     if (nr == 0.0 || relres <= A.tol) break;
     // a zero correction cannot make progress: never read it as converged
     if (!(emax > 0.0)) { fallback = true; break; }
-    if (emax <= A.tol * xmax) break;
+    if (o.outer >= 2 && emax <= A.tol * xmax) break;  // as in mixed_level (grid.cuh)
     if (o.outer >= 2 && nr > 0.5 * nr_prev) {
       // the FP64 residual is at its rounding floor and u no longer moves at
       // the accuracy asked for

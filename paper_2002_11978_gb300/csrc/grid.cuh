@@ -875,20 +875,29 @@ static __device__ void write_stat(StepStat* st, int status, int iters, int outer
 
 
 // Warm start of a level solve: u = x0 and r64 = b - (ahat I + K A) x0, with
-// x0 = u_prev, or the extrapolation from u_prev, u_prev2 (and u_prev3) that
-// LevelArgs describes (one FP64 product); returns b.b and r.r (grid-wide, in
-// every CTA).
+// x0 = u_prev, or the extrapolation of order A.xorder from the earlier
+// levels A.up (one FP64 product); returns b.b and r.r (grid-wide, in every
+// CTA).
 template <int KP = kPre>
 __device__ bool warm_residual(const LevelArgs& A, SmemAll& S, double& bb, double& rr) {
   const DevPlan& P = A.P;
+  const int q = A.xorder;
   auto pro = [&](int i) -> double {
-    double x = A.u_prev[i];
-    if (A.u_prev2) {
-      const double u2 = A.u_prev2[i];
-      const double d1 = x - u2;
-      double dx = A.e1 * d1;
-      if (A.e2 != 0.0) dx = fma(A.e2, d1 - (u2 - A.u_prev3[i]), dx);
-      x += dx;
+    double v[kMaxStartOrder + 1];
+    v[0] = A.u_prev[i];
+    double x = v[0];
+#pragma unroll
+    for (int j = 1; j <= kMaxStartOrder; ++j)
+      if (j <= q) v[j] = A.up[j][i];
+    // after pass k, v[j] = nabla^k u^{m-1-j}; x collects nabla^k u^{m-1}
+#pragma unroll
+    for (int k = 1; k <= kMaxStartOrder; ++k) {
+      if (k <= q) {
+#pragma unroll
+        for (int j = 0; j + k <= kMaxStartOrder; ++j)
+          if (j + k <= q) v[j] -= v[j + 1];
+        x += v[0];
+      }
     }
     A.u[i] = x;
     return x;
@@ -924,7 +933,7 @@ __device__ bool warm_residual(const LevelArgs& A, SmemAll& S, double& bb, double
 // iterations), forms w = M e in FP64 and updates u += theta e,
 // r -= theta w with theta = 1, or the minimal-residual
 // theta = (r, w)/(w, w) when the full step would raise ||r||, so the FP64
-// residual never grows.  Stops when the last step satisfies
+// residual never grows.  Stops when a step after the first satisfies
 // max|theta e| <= tol max|u|, or ||r|| <= tol ||b|| (the FP64 path's
 // criterion, on the true residual), or when a sweep no longer halves ||r|| with
 // ||r||/||b|| <= 1e-9 (its rounding floor at large n) and the step is below
@@ -1048,7 +1057,10 @@ __device__ void mixed_level(const LevelArgs& A, SmemAll& S, Conv& conv, Inner& i
     if (nr == 0.0 || relres <= A.tol) break;
     // a zero correction cannot make progress: never read it as converged
     if (!(emax > 0.0)) { fallback = true; break; }
-    if (emax <= A.tol * xmax) break;
+    // a small step ends the refinement from the second sweep on; the first
+    // sweep's step only measures how good the starting point was (a warm or
+    // extrapolated start leaves it small while ||r|| is still above tol)
+    if (outer >= 2 && emax <= A.tol * xmax) break;
     if (outer >= 2 && nr > 0.5 * nr_prev) {
       // the FP64 residual is at its rounding floor and u no longer moves at
       // the accuracy asked for

@@ -144,8 +144,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_level_mixed(LevelArgs A) {
 // reduction), and every later sweep asks for the whole remaining reduction
 // (half the target), within max_it iterations and not below 1e-13.  A
 // level takes one long sweep and a short one that restarts from the true
-// FP64 residual.
+// FP64 residual.  That floor is relative to the sweep's own right-hand
+// side, so when the start is good enough that the whole reduction is at
+// most 1/kOneSweep (an extrapolated start), the first sweep asks for all of
+// it and the level usually ends after one sweep.
 constexpr double kFirstSweep = 100.0;
+constexpr double kOneSweep = 1e-6;
 
 template <int KP, bool PCG>
 __device__ void level_mixed_ds_run(const LevelArgs& A) {
@@ -168,8 +172,8 @@ __device__ void level_mixed_ds_run(const LevelArgs& A) {
   int sweep = 0;
   auto inner = [&](double sc, double target, SolveRes& ir) -> bool {
     auto binit = [&](int i) -> dsf { return dsf(A.r64[i] * sc); };
-    const double tin = sweep++ == 0 ? fmax(fmin(kFirstSweep * target, 0.1), 1e-13)
-                                    : fmax(0.5 * target, 1e-13);
+    const double tin = (sweep++ == 0 && target < kOneSweep) ? fmax(fmin(kFirstSweep * target, 0.1), 1e-13)
+                                                             : fmax(0.5 * target, 1e-13);
     ir = level_krylov<PCG, KP>(P, S.s, A.kds, A.kappads, A.hinvds, A.ahat, A.precond != 0, tin,
                                A.max_it, binit);
     return ir.status != TSFDE_ETIMEOUT;

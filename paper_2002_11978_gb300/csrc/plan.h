@@ -213,6 +213,9 @@ template <typename R> struct KVecs {
   R *x, *r, *rh, *p, *v, *s, *t, *ph, *sh;
 };
 
+// Highest order of the extrapolated start of a level solve (LevelArgs.up).
+constexpr int kMaxStartOrder = 4;
+
 struct LevelArgs {
   DevPlan P;
   double ahat;        // a_m / Gamma(1-gamma)
@@ -238,13 +241,13 @@ struct LevelArgs {
   StepStat* stat;
   int probe;          // cluster engine: return at once (launch check)
   const double* u_prev;   // warm start from u^{m-1} (NULL: x0 = 0)
-  // with u_prev, an extrapolated start (u_prev2 NULL: x0 = u^{m-1}):
-  // x0 = u^{m-1} + e1 d1 + e2 (d1 - d2), d1 = u^{m-1} - u^{m-2},
-  // d2 = u^{m-2} - u^{m-3} (u_prev3 is read only when e2 != 0; it may be
-  // the array u itself, each entry read before it is overwritten)
-  const double* u_prev2;
-  const double* u_prev3;
-  double e1, e2;
+  // with u_prev, an extrapolated start of order xorder (0: x0 = u^{m-1}):
+  // x0 = sum_{k=0..xorder} nabla^k u^{m-1}, Newton's backward form of the
+  // polynomial through u^{m-1-xorder}, ..., u^{m-1} evaluated one level on.
+  // up[j] = u^{m-1-j} (up[0] = u_prev); up[xorder] may be the array u
+  // itself, each entry read before it is overwritten.
+  const double* up[kMaxStartOrder + 1];
+  int xorder;
   const StepStat* prev;   // mixed: the previous level's stats (NULL: none)
   int retry_mixed;        // mixed: refine even after a level finished in FP64
   KrylovAuto* kauto;      // TSFDE_KRYLOV_AUTO: method choice state (NULL: fixed method)

@@ -284,8 +284,8 @@ def test_paper_tables_on_gpu(torch, row):
 @pytest.mark.parametrize("warm", [True, "extrapolate"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_warm_start_march_matches_oracle(torch, precision, warm):
-    """Levels started from u^{m-1}, or from the extrapolation 3 u^{m-1} -
-    3 u^{m-2} + u^{m-3} (stopping at ||r|| < tol ||b||), reach the same
+    """Levels started from u^{m-1}, or from the cubic extrapolation through
+    u^{m-4} .. u^{m-1} (stopping at ||r|| < tol ||b||), reach the same
     solutions as the oracle's dense-LU march."""
     prob = ti.config_smallest()
     tm, tau = oracle.graded_mesh(prob.T, prob.M, prob.r)
