@@ -184,15 +184,17 @@ def measured_l2_peak(torch, pkg, stream, mb=L2_PROBE_MB, reps=64, trials=5):
 
 
 # ---------------------------------------------------------------- our arm
-# DRAM bytes per launch from one ncu capture (profiles/k_level_mixed_ds_pcg_n131071_launches_traffic.md),
-# valid only for the kernel sources they were taken with: the digest of those sources is kept
-# beside the figure, and a changed source makes the figure null.
-TRAFFIC = {"k_level_mixed_ds/pcg": {
-    "bytes": 57.72e6,
-    "note": "dram read+write per launch at levels 9-11, ncu; those early levels (ahat ~1e6) take ~60 "
-            "PCG iterations against 22 on average over the march, so an average launch moves less",
-    "sources": ['grid.cuh', 'levels.cuh', 'levelds_pcg.cu', 'dev.cuh', 'dsf.cuh', 'plan.h'],
-    "sha1": "e8c601ddc538ccb76be6a86d1e1152ff88bceb06"}}
+# DRAM bytes per level of the double-single level kernels from one ncu capture
+# (profiles/k_level_mixed_ds_n131071_launches_traffic.md), valid only for the sources
+# they were taken with: the digest of those sources is kept beside the figure, and a
+# changed source makes the figure null.
+TRAFFIC = {"k_level_mixed_ds/auto": {
+    "bytes": 59.1e6,
+    "note": "dram read+write per level (both method kernels) at levels 6-11, ncu; BiCGSTAB "
+            "levels of 8-11 inner iterations; the PCG levels of the late march take ~5",
+    "sources": ['grid.cuh', 'levels.cuh', 'levelds.cu', 'levelds_pcg.cu', 'dev.cuh', 'dsf.cuh',
+                'plan.h', 'abi.cpp', 'kernels.cu'],
+    "sha1": "50e14bdb7ef9f742c33a8f14b70662e67b9a5c7e"}}
 
 
 def measured_traffic(kernel):
