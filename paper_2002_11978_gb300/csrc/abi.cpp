@@ -775,6 +775,14 @@ static int enqueue_level(tsfde_ctx* c, const double* kappa_m, const double* f_m,
     // history the oldest of them shares its buffer with u^m
     A.xorder = (int)std::min<int64_t>(kStartOrder, m - 1);
     for (int j = 0; j <= A.xorder; ++j) A.up[j] = ulev(c, m - 1 - j);
+    // Lagrange weights of the nodes m-1-j at m: (-1)^j C(q+1, j+1)
+    // (4, -6, 4, -1 for q = 3), exact in FP64
+    for (int j = 0; j <= A.xorder; ++j) {
+      double w = 1.0;
+      for (int k = 0; k <= A.xorder; ++k)
+        if (k != j) w *= (double)(1 + k) / (double)(k - j);
+      A.xw[j] = w;
+    }
   }
   A.prev = (m >= 2) ? c->stats + (m - 1) : nullptr;
   A.retry_mixed = (m % 64 == 0) ? 1 : 0;

@@ -883,21 +883,16 @@ __device__ bool warm_residual(const LevelArgs& A, SmemAll& S, double& bb, double
   const DevPlan& P = A.P;
   const int q = A.xorder;
   auto pro = [&](int i) -> double {
-    double v[kMaxStartOrder + 1];
-    v[0] = A.u_prev[i];
-    double x = v[0];
+    double x = A.u_prev[i];
+    if (q > 0) {
+      double v[kMaxStartOrder + 1];
 #pragma unroll
-    for (int j = 1; j <= kMaxStartOrder; ++j)
-      if (j <= q) v[j] = A.up[j][i];
-    // after pass k, v[j] = nabla^k u^{m-1-j}; x collects nabla^k u^{m-1}
+      for (int j = 1; j <= kMaxStartOrder; ++j)
+        if (j <= q) v[j] = A.up[j][i];
+      x *= A.xw[0];
 #pragma unroll
-    for (int k = 1; k <= kMaxStartOrder; ++k) {
-      if (k <= q) {
-#pragma unroll
-        for (int j = 0; j + k <= kMaxStartOrder; ++j)
-          if (j + k <= q) v[j] -= v[j + 1];
-        x += v[0];
-      }
+      for (int j = 1; j <= kMaxStartOrder; ++j)
+        if (j <= q) x = fma(A.xw[j], v[j], x);
     }
     A.u[i] = x;
     return x;

@@ -242,11 +242,12 @@ struct LevelArgs {
   int probe;          // cluster engine: return at once (launch check)
   const double* u_prev;   // warm start from u^{m-1} (NULL: x0 = 0)
   // with u_prev, an extrapolated start of order xorder (0: x0 = u^{m-1}):
-  // x0 = sum_{k=0..xorder} nabla^k u^{m-1}, Newton's backward form of the
-  // polynomial through u^{m-1-xorder}, ..., u^{m-1} evaluated one level on.
-  // up[j] = u^{m-1-j} (up[0] = u_prev); up[xorder] may be the array u
-  // itself, each entry read before it is overwritten.
+  // x0 = sum_{j=0..xorder} xw[j] up[j], the polynomial through up[0..xorder]
+  // evaluated at level m (Lagrange weights xw from the host).  up[j] =
+  // u^{m-1-j} (up[0] = u_prev); up[xorder] may be the array u itself, each
+  // entry read before it is overwritten.
   const double* up[kMaxStartOrder + 1];
+  double xw[kMaxStartOrder + 1];
   int xorder;
   const StepStat* prev;   // mixed: the previous level's stats (NULL: none)
   int retry_mixed;        // mixed: refine even after a level finished in FP64

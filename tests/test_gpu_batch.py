@@ -158,6 +158,12 @@ def test_batch_warm_start_matches_cold(torch, precision):
     assert iw["status"] == 0, iw
     for a, b in zip(Uw, Uc):
         assert np.max(np.abs(a - b)) / np.max(np.abs(b)) < 1e-10
+    # the batched solve takes the extrapolated start (warm_start = 2) as
+    # u^{m-1}: bitwise the same march
+    _, Ux, ix = _batch(torch, inst, M, precision=precision, warm_start="extrapolate")
+    assert ix["status"] == 0 and ix["iterations"] == iw["iterations"], (ix, iw)
+    for a, b in zip(Ux, Uw):
+        np.testing.assert_array_equal(a, b)
 
 
 def _mixed_specs():

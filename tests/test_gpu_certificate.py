@@ -84,10 +84,10 @@ def certify(prob, t, U, soe, tm, levels):
                                          (0.7, 0.8), (0.7, 1.2), (0.7, 1.8)])
 def test_mid_workload_certified(torch, gamma, alpha):
     """n = 2^14 - 1, M = 2048, the six (gamma, alpha) pairs, the default
-    path (double-single mixed solve, per-level Krylov choice, warm start);
-    levels 1, 2, 10, 100, 1000 and M certified."""
+    path (double-single mixed solve, per-level Krylov choice, extrapolated
+    start); levels 1, 2, 10, 100, 1000 and M certified."""
     prob = ti.config_mid(gamma, alpha, M=2048)
-    t, U, soe, tm = march(torch, prob, precision="mixed_ds", krylov="auto", warm_start=True)
+    t, U, soe, tm = march(torch, prob, precision="mixed_ds", krylov="auto", warm_start="extrapolate")
     bounds, lemma = certify(prob, t, U, soe, tm, [1, 2, 10, 100, 1000, prob.M])
     assert max(bounds.values()) <= 1e-10, (bounds, lemma)
 
@@ -105,6 +105,6 @@ def test_headline_workload_certified(torch):
     march; levels 1, 2, 16, 64, 2048 and M certified (each defect is an
     O(n^2) double-double sum)."""
     prob = ti.config_mixed()
-    t, U, soe, tm = march(torch, prob, precision="mixed_ds", krylov="auto", warm_start=True)
+    t, U, soe, tm = march(torch, prob, precision="mixed_ds", krylov="auto", warm_start="extrapolate")
     bounds, lemma = certify(prob, t, U, soe, tm, [1, 2, 16, 64, 2048, prob.M])
     assert max(bounds.values()) <= 1e-10, (bounds, lemma)
