@@ -62,6 +62,7 @@ struct tsfde_ctx {
   StepStat* stats = nullptr;
   int* status = nullptr;
   KrylovAuto* kauto = nullptr;  // TSFDE_KRYLOV_AUTO: per-level method choice
+  int* pre_status = nullptr;     // double-single: status of the separate preconditioner build
   KrylovAuto kauto_init{};       // host source of the reset copy (outlives it)
   int engine = TSFDE_ENGINE_GRID;  // engine of the mixed level solves
   // checkpoints of the forward march for the adjoint sweep (ckpt_stride):
@@ -484,10 +485,12 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
   // double-single tables and inner vectors
   const bool ds = o.precision == TSFDE_MIXED_DS;
   dsf2* dtwds = nullptr;
-  dsf *dsads = nullptr, *dsbds = nullptr, *dsaGds = nullptr, *dsbGds = nullptr;
+  dsf *dsads = nullptr, *dsbds = nullptr, *dsaGds = nullptr, *dsbGds = nullptr, *dgds = nullptr;
+  dsf2 *dchds = nullptr, *dBhds = nullptr;
   if (ds) {
     ok &= dalloc(c, &dtwds, L) && dalloc(c, &dsads, Nc) && dalloc(c, &dsbds, Nc) &&
           dalloc(c, &dsaGds, Nc) && dalloc(c, &dsbGds, Nc) && dalloc(c, &c->kappads, ld);
+    ok &= dalloc(c, &dchds, n) && dalloc(c, &dBhds, L) && dalloc(c, &dgds, n);
     dsf** vds[] = {&c->kds.x, &c->kds.r, &c->kds.rh, &c->kds.p, &c->kds.v, &c->kds.s, &c->kds.t,
                    &c->kds.ph, &c->kds.sh};
     for (dsf** p : vds) ok &= dalloc(c, p, ld);
@@ -497,6 +500,7 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
     if (ds) ok &= dalloc(c, &c->hinvds, ld);
   }
   if (o.krylov == TSFDE_KRYLOV_AUTO) ok &= dalloc(c, &c->kauto, 1);
+  if (ds) ok &= dalloc(c, &c->pre_status, 1);
   if (o.ckpt_stride != 0) {
     int64_t S = o.ckpt_stride;
     if (S < 0) S = std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)M)));
@@ -541,12 +545,23 @@ static int setup_impl(tsfde_ctx* c, double alpha, double gamma, double l, double
       sads[i] = dsf(sa[i]);
       sbds[i] = dsf(sb[i]);
     }
+    std::vector<dsf2> chds(n), Bhds(L);
+    for (int64_t j = 0; j < n; ++j) {
+      chds[j].x = dsf(ch64[j].x);
+      chds[j].y = dsf(ch64[j].y);
+    }
+    for (int64_t k = 0; k < L; ++k) {
+      Bhds[k].x = dsf(Bh64[k].x);
+      Bhds[k].y = dsf(Bh64[k].y);
+    }
     if ((e = upload(dtwds, twds)) != cudaSuccess || (e = upload(dsads, sads)) != cudaSuccess ||
-        (e = upload(dsbds, sbds)) != cudaSuccess)
+        (e = upload(dsbds, sbds)) != cudaSuccess || (e = upload(dchds, chds)) != cudaSuccess ||
+        (e = upload(dBhds, Bhds)) != cudaSuccess)
       return cuda_fail(c, e, "upload");
     P.twLds = dtwds;
     P.saTds = dsads; P.sbTds = dsbds;
     P.saGds = dsaGds; P.sbGds = dsbGds;
+    P.chirpds = dchds; P.Bhds = dBhds; P.gds = dgds;
   }
 
   if ((e = upload(dtw64, tw64)) != cudaSuccess || (e = upload(dtw32, tw32)) != cudaSuccess ||
@@ -700,6 +715,7 @@ static LevelArgs level_args(tsfde_ctx* c, double ahat, const double* b, double* 
   A.k64 = c->k64;
   A.k32 = c->k32;
   A.kds = c->kds;
+  A.pre_status = c->pre_status;
   A.kappads = c->kappads;
   A.krylov = c->opts.krylov;
   A.hinv64 = c->hinv64;

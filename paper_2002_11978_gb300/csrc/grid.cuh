@@ -37,9 +37,7 @@ template <typename R> struct Smem {
   double* red;  // 33 doubles
 };
 
-// Tables of each arithmetic type.  The Bluestein tables (chirp, Bh, gcol)
-// exist in FP64 and FP32 only: the preconditioner is never built in
-// double-single.
+// Tables of each arithmetic type.
 template <typename R> constexpr bool is_f64 = std::is_same_v<R, double>;
 template <typename R> constexpr bool is_ds = std::is_same_v<R, dsf>;
 
@@ -72,13 +70,19 @@ template <typename R> __device__ __forceinline__ R* sbG(const DevPlan& P) {
   else return P.sbG32;
 }
 template <typename R> __device__ __forceinline__ const cplx<R>* chirp(const DevPlan& P) {
-  if constexpr (is_f64<R>) return P.chirp64; else return P.chirp32;
+  if constexpr (is_f64<R>) return P.chirp64;
+  else if constexpr (is_ds<R>) return P.chirpds;
+  else return P.chirp32;
 }
 template <typename R> __device__ __forceinline__ const cplx<R>* Bh(const DevPlan& P) {
-  if constexpr (is_f64<R>) return P.Bh64; else return P.Bh32;
+  if constexpr (is_f64<R>) return P.Bh64;
+  else if constexpr (is_ds<R>) return P.Bhds;
+  else return P.Bh32;
 }
 template <typename R> __device__ __forceinline__ R* gcol(const DevPlan& P) {
-  if constexpr (is_f64<R>) return P.g64; else return P.g32;
+  if constexpr (is_f64<R>) return P.g64;
+  else if constexpr (is_ds<R>) return P.gds;
+  else return P.g32;
 }
 
 struct SmemAll {
@@ -937,20 +941,28 @@ __device__ bool warm_residual(const LevelArgs& A, SmemAll& S, double& bb, double
 // FP64 PBiCGSTAB on the remaining residual, so a level never returns an
 // unconverged answer.  PCG selects the Krylov method of that FP64 finish
 // (the inner solves choose their own).
-template <bool PCG = false, int KP = kPre, typename RI, class Conv, class Inner>
+// PRE: the caller's preconditioner is always built by a separate launch
+// (A.prebuilt; the in-kernel FP64 build is then not compiled in).
+template <bool PCG = false, int KP = kPre, bool PRE = false, typename RI, class Conv, class Inner>
 __device__ void mixed_level(const LevelArgs& A, SmemAll& S, Conv& conv, Inner& inner, const RI* e) {
   const DevPlan& P = A.P;
   const int n = P.n;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int gstr = gridDim.x * blockDim.x;
-  const double kbar = mean_kappa(P, A.kappa64, S.d.red);
-  if (kbar < 0.0) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
-  // The preconditioner is built in FP64 and rounded to FP32; building it in
-  // FP32 would bury its smallest eigenvalues (1/(ahat + kbar lambda_max),
-  // ~1e-8 of the largest at n = 2^17-1) under rounding.
-  if (A.precond && !build_precond<double, KP>(P, S.d, A.ahat, kbar)) {
-    write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0);
-    return;
+  if (PRE || A.prebuilt) {
+    // built by k_precond_ds before this launch
+    const int st = A.precond ? __ldcg(A.pre_status) : TSFDE_OK;
+    if (st != TSFDE_OK) { write_stat(A.stat, st, 0, 0, 0.0); return; }
+  } else if constexpr (!PRE) {
+    const double kbar = mean_kappa(P, A.kappa64, S.d.red);
+    if (kbar < 0.0) { write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0); return; }
+    // The preconditioner is built in FP64 and rounded to FP32; building it in
+    // FP32 would bury its smallest eigenvalues (1/(ahat + kbar lambda_max),
+    // ~1e-8 of the largest at n = 2^17-1) under rounding.
+    if (A.precond && !build_precond<double, KP>(P, S.d, A.ahat, kbar)) {
+      write_stat(A.stat, TSFDE_ETIMEOUT, 0, 0, 0.0);
+      return;
+    }
   }
   double bb, rr0;
   {

@@ -306,7 +306,7 @@ static cudaError_t set_attrs(size_t smem) {
                       level64_kernel(2, 1), level64_kernel(4, 1), level32_kernel(2, 1),
                       level32_kernel(4, 1), levelds_kernel(2, 1), levelds_kernel(4, 1),
                       (const void*)k_apply64, (const void*)k_apply32, (const void*)k_apply_ds,
-                      level_adj_kernel(0), level_adj_kernel(1)};
+                      level_adj_kernel(0), level_adj_kernel(1), precond_ds_kernel(2), precond_ds_kernel(4)};
   for (const void* k : ks) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -323,7 +323,7 @@ int coop_blocks_per_sm(size_t smem) {
                       level64_kernel(2, 1), level64_kernel(4, 1), level32_kernel(2, 1),
                       level32_kernel(4, 1), levelds_kernel(2, 1), levelds_kernel(4, 1),
                       (const void*)k_apply64, (const void*)k_apply32, (const void*)k_apply_ds,
-                      level_adj_kernel(0), level_adj_kernel(1)};
+                      level_adj_kernel(0), level_adj_kernel(1), precond_ds_kernel(2), precond_ds_kernel(4)};
   for (const void* k : ks) {
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, smem) != cudaSuccess) return 0;
@@ -358,12 +358,21 @@ cudaError_t launch_convert(const double* in, double* o64, float* o32, int n, cud
 }
 
 // With TSFDE_KRYLOV_AUTO (a.kauto set) both method kernels are launched;
-// the one not chosen for the level returns before any work.
-cudaError_t launch_level(const LevelArgs& a, int precision, cudaStream_t s) {
-  size_t smem = plan_smem_bytes(a.P);
-  void* args[] = {(void*)&a};
-  const bool kp2 = kp_fits(a.P, 2);
+// the one not chosen for the level returns before any work.  A
+// double-single level with a preconditioner first runs k_precond_ds.
+cudaError_t launch_level(const LevelArgs& a0, int precision, cudaStream_t s) {
+  size_t smem = plan_smem_bytes(a0.P);
+  const bool kp2 = kp_fits(a0.P, 2);
   const int kp = kp2 ? 2 : 4;
+  LevelArgs a = a0;
+  void* args[] = {(void*)&a};
+  if (precision == TSFDE_MIXED_DS && a.precond && a.pre_status) {
+    a.prebuilt = 1;
+    cudaError_t e = cudaMemsetAsync(a.P.bar, 0, sizeof(GridBarrier), s);
+    if (e == cudaSuccess)
+      e = cudaLaunchCooperativeKernel(precond_ds_kernel(kp), dim3(a.P.G), dim3(kThreads), args, smem, s);
+    if (e != cudaSuccess) return e;
+  }
   const bool autok = a.krylov == TSFDE_KRYLOV_AUTO && a.kauto;
   for (int pcg = 0; pcg < 2; ++pcg) {
     if (!autok && pcg != (a.krylov == TSFDE_KRYLOV_PCG ? 1 : 0)) continue;

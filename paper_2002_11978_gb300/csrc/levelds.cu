@@ -11,4 +11,8 @@ const void* levelds_kernel(int kp, int pcg) {
   return kp == 2 ? (const void*)k_level_mixed_ds<2, false> : (const void*)k_level_mixed_ds<4, false>;
 }
 
+const void* precond_ds_kernel(int kp) {
+  return kp == 2 ? (const void*)k_precond_ds<2> : (const void*)k_precond_ds<4>;
+}
+
 }  // namespace tsfde

@@ -165,9 +165,6 @@ __device__ void level_mixed_ds_run(const LevelArgs& A) {
         A.hinvds[k] = dsf(h);
       }
     }
-    if (!A.precond) return;
-    P.saGds[k] = dsf(P.saG64[k]);
-    P.sbGds[k] = dsf(P.sbG64[k]);
   };
   int sweep = 0;
   auto inner = [&](double sc, double target, SolveRes& ir) -> bool {
@@ -178,7 +175,37 @@ __device__ void level_mixed_ds_run(const LevelArgs& A) {
                                A.max_it, binit);
     return ir.status != TSFDE_ETIMEOUT;
   };
-  mixed_level<PCG, KP>(A, S, conv, inner, A.kds.x);
+  mixed_level<PCG, KP, true>(A, S, conv, inner, A.kds.x);
+}
+
+// The preconditioner of a double-single level, built in its own cooperative
+// launch before the level kernel(s): kbar = mean(kappa^m), then the
+// Bluestein build of P^{-1} (build_precond) in double-single arithmetic,
+// whose ~48 bits keep the spectrum to ~1e-14 of its largest entry (FP32
+// would bury the smallest eigenvalues, ~1e-8 of the largest at
+// n = 2^17 - 1), at a fraction of the FP64 pipe time of an FP64 build; the
+// FP64 tables (for an FP64 finish) are rounded from it.  Kept out of the
+// level kernel so that the level kernel's registers are not spent on it.
+template <int KP>
+__global__ void __launch_bounds__(kThreads, 2) k_precond_ds(LevelArgs A) {
+  const DevPlan& P = A.P;
+  int st = TSFDE_OK;
+  if (!kp_fits(P, KP)) {
+    st = TSFDE_EINVAL;
+  } else {
+    SmemAll S = smem_setup(P);
+    const double kbar = mean_kappa(P, A.kappa64, S.d.red);
+    if (kbar < 0.0 || !build_precond<dsf, KP>(P, S.s, A.ahat, kbar)) {
+      st = TSFDE_ETIMEOUT;
+    } else {
+      const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+      for (int k = gtid; k < P.Nc; k += gridDim.x * blockDim.x) {
+        P.saG64[k] = (double)P.saGds[k];
+        P.sbG64[k] = (double)P.sbGds[k];
+      }
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *A.pre_status = st;
 }
 
 template <int KP, bool PCG>

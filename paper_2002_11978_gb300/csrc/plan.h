@@ -112,10 +112,12 @@ struct DevPlan {
   double* g64; float* g32;  // first column of the circulant inverse (n)
   // double-single copies (mixed solves with the double-single inner solver;
   // NULL otherwise): twiddles, Toeplitz spectrum, per-level preconditioner
-  // spectrum (rounded from the FP64 build)
+  // spectrum (written by k_precond_ds), and the Bluestein tables and
+  // circulant-inverse column that build uses
   const dsf2* twLds;
   const dsf* saTds; const dsf* sbTds;
   dsf* saGds; dsf* sbGds;
+  const dsf2* chirpds; const dsf2* Bhds; dsf* gds;
   double2* S1;  // work: Nfft complex (double capacity, reused as float2 / dsf2)
   double2* S2;
   CGeo cl;
@@ -240,6 +242,11 @@ struct LevelArgs {
   double* r64;        // mixed: FP64 residual
   StepStat* stat;
   int probe;          // cluster engine: return at once (launch check)
+  // double-single mixed solve: the level's preconditioner was built by
+  // k_precond_ds just before (prebuilt = 1; tables in double-single and
+  // FP64), which wrote its status to *pre_status
+  int prebuilt;
+  int* pre_status;
   const double* u_prev;   // warm start from u^{m-1} (NULL: x0 = 0)
   // with u_prev, an extrapolated start of order xorder (0: x0 = u^{m-1}):
   // x0 = sum_{j=0..xorder} xw[j] up[j], the polynomial through up[0..xorder]
@@ -381,6 +388,7 @@ cudaError_t launch_level(const LevelArgs& a, int precision, cudaStream_t s);
 const void* level64_kernel(int kp, int pcg);
 const void* level32_kernel(int kp, int pcg);
 const void* levelds_kernel(int kp, int pcg);
+const void* precond_ds_kernel(int kp);
 const void* level_adj_kernel(int pcg);
 // cluster engine (cluster.cu): mixed level solve with the FP32 inner solves
 // on one thread-block cluster; a.P.G must equal a.P.cl.G.
