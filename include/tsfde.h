@@ -161,7 +161,7 @@ typedef struct tsfde_opts {
                            the cubic extrapolation in the level index,
                            x0 = 4 u^{m-1} - 6 u^{m-2} + 4 u^{m-3} - u^{m-4}
                            (lower orders at levels 1-3; the batched solve
-                           takes 2 as 1); 0 (default): x0 = 0 and the
+                           too); 0 (default): x0 = 0 and the
                            residual relative to ||r_0|| = ||b^m|| (Sec. 5);
                            other values: TSFDE_EINVAL                       */
   int history;          /* TSFDE_HISTORY_SOE (default, FIDS) or

@@ -45,6 +45,9 @@ struct BatchCtx {
   int method;  // Krylov method of the current level (TSFDE_KRYLOV_BICGSTAB / _PCG)
 };
 
+// rotating level buffers per instance
+constexpr int kBRoll = 4;
+
 size_t batch_smem_bytes(const CeLay& lay) { return ce_ctx_offset(lay) + sizeof(BatchCtx); }
 
 __device__ __forceinline__ CeGeo geo_q(const CeGeo& g0) {
@@ -69,8 +72,12 @@ __device__ __noinline__ void bt_init(const BatchCtx* bx) {
 }
 
 // History update and right-hand side of level m into r64; u^m = 0, or
-// u^{m-1} with warm; pushes the cluster partial of b.b into slot BS_BB.
-__device__ __noinline__ void bt_rhs(const BatchCtx* bx, int m, bool warm) {
+// u^{m-1} with warm = 1, or (warm = 2) the polynomial in the level index
+// through u^{m-1} .. u^{m-4} evaluated at m (x0 = 4 u^{m-1} - 6 u^{m-2} +
+// 4 u^{m-3} - u^{m-4}; lower orders at the first levels; u^{m-4} shares its
+// buffer with u^m and is read first); pushes the cluster partial of b.b
+// into slot BS_BB.
+__device__ __noinline__ void bt_rhs(const BatchCtx* bx, int m, int warm) {
   const BInst& I = bx->I;
   const CeGeo g = geo_q(I.gr);
   const CeSm<double> s = ce_sm<double>(bx->c64.lay);
@@ -83,10 +90,16 @@ __device__ __noinline__ void bt_rhs(const BatchCtx* bx, int m, bool warm) {
     s_cw[j] = I.cw[(size_t)m * I.E + j];
   }
   __syncthreads();
-  const double* u1 = I.u[(m - 1) % 3];
-  const double* u2 = I.u[(m >= 2 ? m - 2 : m - 1) % 3];
-  double* um = I.u[m % 3];
+  const double* u1 = I.u[(m - 1) % kBRoll];
+  const double* u2 = I.u[(m >= 2 ? m - 2 : m - 1) % kBRoll];
+  double* um = I.u[m % kBRoll];
   const double ah = I.ahat[m];
+  // extrapolated start: order q and the Lagrange weights (-1)^j C(q+1, j+1)
+  const int q = (warm == 2 && m >= 2) ? (m - 1 < 3 ? m - 1 : 3) : 0;
+  const double w0 = q + 1, w1 = -0.5 * (q + 1) * q, w2 = (q + 1) * q * (q - 1) / 6.0,
+               w3 = -(q + 1) * q * (q - 1) * (q - 2) / 24.0;
+  const double* u3 = q >= 2 ? I.u[(m - 3) % kBRoll] : nullptr;
+  const double* u4 = q >= 3 ? I.u[(m - 4) % kBRoll] : nullptr;
   double bb = 0.0;
   for (int pp = threadIdx.x; pp < npair; pp += blockDim.x) {
     const int i0 = pair_i0(g, pp);
@@ -108,7 +121,19 @@ __device__ __noinline__ void bt_rhs(const BatchCtx* bx, int m, bool warm) {
     double2 b = make_double2(ah * a1.x - sx + fv.x, ah * a1.y - sy + fv.y);
     if (i0 + 1 >= n) b.y = 0.0;
     st2(I.r64, i0, n, b);
-    st2(um, i0, n, warm ? a1 : make_double2(0.0, 0.0));
+    double2 x0 = warm ? a1 : make_double2(0.0, 0.0);
+    if (q > 0) {
+      x0 = make_double2(w0 * a1.x + w1 * a2.x, w0 * a1.y + w1 * a2.y);
+      if (q >= 2) {
+        const double2 a3 = ld2(u3, i0);
+        x0 = make_double2(fma(w2, a3.x, x0.x), fma(w2, a3.y, x0.y));
+      }
+      if (q >= 3) {
+        const double2 a4 = ld2(u4, i0);
+        x0 = make_double2(fma(w3, a4.x, x0.x), fma(w3, a4.y, x0.y));
+      }
+    }
+    st2(um, i0, n, x0);
     bb += b.x * b.x + b.y * b.y;
   }
   ce_put(s.part, g.Q, BS_BB, block_sum(bb, s.red));
@@ -241,7 +266,7 @@ __device__ __noinline__ void bt_warm_residual(const BatchCtx* bx, int m) {
   const CeGeo g = geo_q(I.gr);
   const CeSm<double> s = ce_sm<double>(bx->c64.lay);
   const int n = g.n, npair = (g.N1 >> 1) << g.lgcQ;
-  const double* um = I.u[m % 3];
+  const double* um = I.u[m % kBRoll];
   const double ah = I.ahat[m];
   Z* X = ce_io(g, s);
   for (int pp = threadIdx.x; pp < npair; pp += blockDim.x) {
@@ -285,7 +310,7 @@ __device__ __noinline__ void bt_update(const BatchCtx* bx, int m, double step, d
   const CeGeo g = geo_q(I.gr);
   const CeSm<double> s = ce_sm<double>(bx->c64.lay);
   const int n = g.n, npair = (g.N1 >> 1) << g.lgcQ;
-  double* um = I.u[m % 3];
+  double* um = I.u[m % kBRoll];
   double rr = 0.0, emax = 0.0, xmax = 0.0;
   for (int pp = threadIdx.x; pp < npair; pp += blockDim.x) {
     const int i0 = pair_i0(g, pp);
@@ -316,7 +341,7 @@ __device__ __noinline__ void bt_add_fp64(const BatchCtx* bx, int m) {
   const BInst& I = bx->I;
   const CeGeo g = geo_q(I.gr);
   const int n = g.n, npair = (g.N1 >> 1) << g.lgcQ;
-  double* um = I.u[m % 3];
+  double* um = I.u[m % kBRoll];
   for (int pp = threadIdx.x; pp < npair; pp += blockDim.x) {
     const int i0 = pair_i0(g, pp);
     if (i0 >= n) continue;
@@ -329,7 +354,7 @@ __device__ __noinline__ void bt_copy_out(const BatchCtx* bx, int m) {
   const BInst& I = bx->I;
   const CeGeo g = geo_q(I.gr);
   const int n = g.n, npair = (g.N1 >> 1) << g.lgcQ;
-  const double* um = I.u[m % 3];
+  const double* um = I.u[m % kBRoll];
   for (int pp = threadIdx.x; pp < npair; pp += blockDim.x) {
     const int i0 = pair_i0(g, pp);
     if (i0 < n) I.u_out[i0] = um[i0];
@@ -362,7 +387,7 @@ __device__ LevelOut bt_level(BatchCtx* bx, const BatchArgs& A, int m, bool prev_
   const int Q = I.gr.Q;
   const bool warm = A.warm != 0;
   LevelOut o{TSFDE_OK, 0, 0, false, 0.0};
-  bt_rhs(bx, m, warm);
+  bt_rhs(bx, m, A.warm);
   if (A.precond) bt_precond(bx, m);  // ends with a barrier
   else cl.sync();
   const double bb = ce_total(s.part, Q, BS_BB);
@@ -381,7 +406,7 @@ __device__ LevelOut bt_level(BatchCtx* bx, const BatchArgs& A, int m, bool prev_
   if (threadIdx.x == 0) {
     bx->c32.a = (float)I.ahat[m];
     bx->c64.a = I.ahat[m];
-    bx->c64.V.x = (A.precision == TSFDE_FP64 && !warm) ? I.u[m % 3] : I.v64.x;
+    bx->c64.V.x = (A.precision == TSFDE_FP64 && !warm) ? I.u[m % kBRoll] : I.v64.x;
   }
   __syncthreads();
   if (A.precision == TSFDE_FP64) {

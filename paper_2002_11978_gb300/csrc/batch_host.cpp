@@ -434,14 +434,14 @@ int tsfde_batch_setup_plan(tsfde_batch** out, int B, const tsfde_instance* inst,
     I.n = n; I.E = h.E; I.ld = ld;
     I.gr = h.gr; I.gc = h.gc;
     I.tstride = Lmax / h.L;
-    double *phi, *k64, *f, *Hh, *u0, *u1, *u2, *r64, *w, *ah, *eps, *cw, *lam, *h64;
+    double *phi, *k64, *f, *Hh, *u0, *u1, *u2, *u3, *r64, *w, *ah, *eps, *cw, *lam, *h64;
     float *k32, *h32;
     int* ea;
     double2 *ch, *bh, *t64, *g64;
     float2 *t32, *g32;
     ok = ok && balloc(b, &phi, ld) && balloc(b, &k64, ld) && balloc(b, &f, ld) &&
          balloc(b, &Hh, (size_t)E * ld) && balloc(b, &u0, ld) && balloc(b, &u1, ld) &&
-         balloc(b, &u2, ld) && balloc(b, &r64, ld) && balloc(b, &w, ld) && balloc(b, &k32, ld) &&
+         balloc(b, &u2, ld) && balloc(b, &u3, ld) && balloc(b, &r64, ld) && balloc(b, &w, ld) && balloc(b, &k32, ld) &&
          balloc(b, &h64, ld) && balloc(b, &h32, ld) &&
          balloc(b, &ah, M + 1) && balloc(b, &eps, h.eps.size()) && balloc(b, &cw, h.cw.size()) &&
          balloc(b, &ea, M + 1) && balloc(b, &lam, n) && balloc(b, &ch, n) && balloc(b, &bh, h.L) &&
@@ -451,7 +451,7 @@ int tsfde_batch_setup_plan(tsfde_batch** out, int B, const tsfde_instance* inst,
     for (int q = 0; q < 9 && ok; ++q) ok = balloc(b, &v64[q], ld) && balloc(b, &v32[q], ld);
     if (!ok) break;
     I.phi = phi; I.kap64 = k64; I.kap32 = k32; I.hinv64 = h64; I.hinv32 = h32; I.f = f; I.H = Hh;
-    I.u[0] = u0; I.u[1] = u1; I.u[2] = u2; I.r64 = r64; I.w = w;
+    I.u[0] = u0; I.u[1] = u1; I.u[2] = u2; I.u[3] = u3; I.r64 = r64; I.w = w;
     I.v64 = KVecs<double>{v64[0], v64[1], v64[2], v64[3], v64[4], v64[5], v64[6], v64[7], v64[8]};
     I.v32 = KVecs<float>{v32[0], v32[1], v32[2], v32[3], v32[4], v32[5], v32[6], v32[7], v32[8]};
     I.ahat = ah; I.eps = eps; I.cw = cw; I.Eact = ea; I.lam = lam; I.chirp = ch; I.Bh = bh;

@@ -277,7 +277,7 @@ struct BInst {
   const float* hinv32;
   const double* f;
   double* H;             // E x ld scaled SOE history
-  double* u[3];          // rotating levels
+  double* u[4];          // rotating levels (an extrapolated start reads u^{m-1} .. u^{m-4})
   double* r64;           // FP64 residual (holds b at the start of a level)
   double* w;             // FP64 scratch (M e, preconditioner column g)
   KVecs<float> v32;

@@ -148,7 +148,8 @@ def test_batch_partial_levels_and_cluster_sizes(torch):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_batch_warm_start_matches_cold(torch, precision):
-    """Levels started from u^{m-1} reach the cold-started FP64 solutions."""
+    """Levels started from u^{m-1}, or from the extrapolated start, reach the
+    cold-started FP64 solutions."""
     M = 24
     ns, al, ga = ti.batched_instance_params()
     specs = [(i, int(ns[i]), float(al[i]), float(ga[i])) for i in (3, 8, 64)]
@@ -158,12 +159,14 @@ def test_batch_warm_start_matches_cold(torch, precision):
     assert iw["status"] == 0, iw
     for a, b in zip(Uw, Uc):
         assert np.max(np.abs(a - b)) / np.max(np.abs(b)) < 1e-10
-    # the batched solve takes the extrapolated start (warm_start = 2) as
-    # u^{m-1}: bitwise the same march
+    # the extrapolated start (warm_start = 2: the cubic in the level index
+    # through u^{m-1} .. u^{m-4}) reaches the same solutions in fewer
+    # iterations
     _, Ux, ix = _batch(torch, inst, M, precision=precision, warm_start="extrapolate")
-    assert ix["status"] == 0 and ix["iterations"] == iw["iterations"], (ix, iw)
-    for a, b in zip(Ux, Uw):
-        np.testing.assert_array_equal(a, b)
+    assert ix["status"] == 0, ix
+    assert ix["iterations"] < iw["iterations"], (ix, iw)
+    for a, b in zip(Ux, Uc):
+        assert np.max(np.abs(a - b)) / np.max(np.abs(b)) < 1e-10
 
 
 def _mixed_specs():
