@@ -185,28 +185,38 @@ def measured_l2_peak(torch, pkg, stream, mb=L2_PROBE_MB, reps=64, trials=5):
 
 # ---------------------------------------------------------------- our arm
 # DRAM bytes per level of the double-single level kernels from one ncu capture
-# (profiles/k_level_mixed_ds_n131071_launches_traffic.md), valid only for the sources
-# they were taken with: the digest of those sources is kept beside the figure, and a
-# changed source makes the figure null.
+# (profiles/k_level_mixed_ds_n131071_launches_traffic.md), valid only for the code
+# they were taken with: the digest of that code (code_digest: comments and blank
+# space ignored) is kept beside the figure, and changed code makes the figure null.
 TRAFFIC = {"k_level_mixed_ds/auto": {
     "bytes": 62.8e6,
     "note": "dram read+write per level (k_precond_ds and both method kernels) at levels 6-11, ncu; "
             "BiCGSTAB levels of 8-11 inner iterations; the PCG levels of the late march take ~5",
     "sources": ['grid.cuh', 'levels.cuh', 'levelds.cu', 'levelds_pcg.cu', 'dev.cuh', 'dsf.cuh',
                 'plan.h', 'abi.cpp', 'kernels.cu'],
-    "sha1": "5e7a4f2c7f1e50d7b0ea8e7a173e5b6b09d7559f"}}
+    "sha1": "7b041ade0cfad06dd955660ce2f1bd65778f049d"}}
+
+
+def code_digest(files):
+    """SHA-1 of the code of the given csrc files with comments and blank
+    space removed: a change of code changes it, a change of comments does not."""
+    import hashlib
+    import re
+    h = hashlib.sha1()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2002_11978_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
+    return h.hexdigest()
 
 
 def measured_traffic(kernel):
-    import hashlib
     t = TRAFFIC.get(kernel)
     if t is None:
         return None
-    h = hashlib.sha1()
-    for f in t["sources"]:
-        with open(os.path.join(ROOT, "paper_2002_11978_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return t["bytes"] if h.hexdigest() == t["sha1"] else None
+    return t["bytes"] if code_digest(t["sources"]) == t["sha1"] else None
 
 
 def run_arm(torch, pkg, prob, precision, W, K, flush, stream, e2e=False, warm=False, krylov="bicgstab"):

@@ -120,7 +120,7 @@ template <typename T> cudaError_t upload(T* dst, const std::vector<T>& src) {
 }
 
 // Device vector of level m: a row of the stored levels with the direct
-// history, else one of three rotating buffers.
+// history, else one of kRoll rotating buffers.
 double* ulev(tsfde_ctx* c, int64_t m) {
   return c->Uh ? c->Uh + (size_t)m * c->ld : c->u[m % kRoll];
 }

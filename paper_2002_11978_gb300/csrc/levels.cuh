@@ -135,8 +135,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_level_mixed(LevelArgs A) {
 
 // Mixed level solve with the inner solve in double-single arithmetic
 // (dsf.cuh): the same refinement loop, every inner vector, product and
-// scalar update carried as FP32 pairs.  kappa^m (and 1/kappa^m for PCG) and
-// the preconditioner spectrum are rounded from FP64 once per level.  With
+// scalar update carried as FP32 pairs.  kappa^m (and 1/kappa^m for PCG) are
+// rounded from FP64 once per level; the preconditioner spectrum comes from
+// k_precond_ds, launched just before (mixed_level's PRE form).  With
 // ~48 bits the inner solve resolves the operator, but its true residual
 // cannot go below ~u_ds ||M|| ||u|| (u_ds ~ 2^-47), which at the late levels
 // of large problems is above tol ||b||.  So the first sweep stops near that
